@@ -1,0 +1,114 @@
+"""Closed forms and brute-force references used to pin the oracle.
+
+Nothing here shares code with the oracle or with the CUDA path.
+- Onsager's free energy of the square-lattice Ising model (Onsager 1944),
+  evaluated by Gauss-Legendre quadrature.
+- Onsager's internal energy (closed form with the complete elliptic integral
+  of the first kind, scipy.special.ellipk).
+- Yang's spontaneous magnetisation (Yang 1952).
+- Exact corner transfer matrices of a k x k quadrant of vertex tensors by
+  direct contraction of the network drawn from its geometry.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+K_CRIT = 0.5 * math.log(1.0 + math.sqrt(2.0))
+
+
+def onsager_minus_beta_f(K: float, n: int = 400) -> float:
+    """-beta f per spin = ln 2 + 1/(2 pi^2) int_0^pi int_0^pi ln[cosh^2 2K - sinh 2K (cos a + cos b)]."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    t = 0.5 * math.pi * (x + 1.0)
+    wt = 0.5 * math.pi * w
+    c = np.cos(t)
+    arg = math.cosh(2 * K) ** 2 - math.sinh(2 * K) * (c[:, None] + c[None, :])
+    integral = float(wt @ np.log(arg) @ wt)
+    return math.log(2.0) + integral / (2.0 * math.pi ** 2)
+
+
+def onsager_f(beta: float, K: float | None = None) -> float:
+    """Free energy per spin at inverse temperature beta and coupling K (default beta)."""
+    K = beta if K is None else K
+    return -onsager_minus_beta_f(K) / beta
+
+
+def onsager_u(K: float) -> float:
+    """Energy per spin (J = 1): -coth 2K [1 + (2/pi)(2 tanh^2 2K - 1) K1(k)], k = 2 sinh 2K / cosh^2 2K."""
+    k = 2.0 * math.sinh(2 * K) / math.cosh(2 * K) ** 2
+    K1 = special.ellipk(k * k)
+    return -1.0 / math.tanh(2 * K) * (1.0 + 2.0 / math.pi * (2.0 * math.tanh(2 * K) ** 2 - 1.0) * K1)
+
+
+def yang_m(K: float) -> float:
+    if K <= K_CRIT:
+        return 0.0
+    return (1.0 - math.sinh(2 * K) ** -4) ** 0.125
+
+
+def vertex_tensor(spins: np.ndarray, beta: float) -> np.ndarray:
+    """V[r, u, l, d]: one vertex (black plaquette) whose corner spins, in cyclic
+    order around the plaquette, are the right, up, left and down legs."""
+    B = np.exp(beta * spins @ spins.T)
+    return np.einsum("ru,ul,ld,dr->ruld", B, B, B, B)
+
+
+def brute_force_corner(spins: np.ndarray, beta: float, k: int, boundary: int = 0) -> np.ndarray:
+    """Exact corner transfer matrix of a k x k quadrant of vertices.
+
+    Vertex (i, j), 0 <= i, j < k, sits at column i, row j; its right leg
+    meets the left leg of (i+1, j) and its up leg the down leg of (i, j+1).
+    The right legs of column k-1 and the up legs of row k-1 are fixed to the
+    boundary spin.  Row index: the down legs of row 0 (i = 0..k-1); column
+    index: the left legs of column 0 (j = 0..k-1).  Contracted directly with
+    einsum over the whole network."""
+    q = spins.shape[0]
+    V = vertex_tensor(spins, beta)
+    letters = iter("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ")
+    # bond labels
+    h = {}  # horizontal bond between (i,j) and (i+1,j)
+    v = {}  # vertical bond between (i,j) and (i,j+1)
+    for j in range(k):
+        for i in range(k - 1):
+            h[(i, j)] = next(letters)
+    for i in range(k):
+        for j in range(k - 1):
+            v[(i, j)] = next(letters)
+    row = [next(letters) for _ in range(k)]
+    col = [next(letters) for _ in range(k)]
+    ops, subs = [], []
+    e = np.zeros(q)
+    e[boundary] = 1.0
+    for j in range(k):
+        for i in range(k):
+            r = h[(i, j)] if i < k - 1 else None
+            u = v[(i, j)] if j < k - 1 else None
+            l = h[(i - 1, j)] if i > 0 else col[j]
+            d = v[(i, j - 1)] if j > 0 else row[i]
+            T = V
+            idx = ""
+            # fix boundary legs by contracting with the unit vector
+            if r is None:
+                T = np.einsum("ruld,r->uld", T, e)
+            else:
+                idx += r
+            if u is None:
+                T = np.einsum(("uld,u->ld" if r is None else "ruld,u->rld"), T, e)
+            else:
+                idx += u
+            idx += l + d
+            ops.append(T)
+            subs.append(idx)
+    out = "".join(row) + "".join(col)
+    expr = ",".join(subs) + "->" + out
+    C = np.einsum(expr, *ops, optimize="greedy")
+    return C.reshape(q ** k, q ** k, order="F")
+
+
+def normalised_abs_spectrum(C: np.ndarray, n: int) -> np.ndarray:
+    ev = np.linalg.eigvalsh(0.5 * (C + C.T))
+    ev = ev[np.argsort(-np.abs(ev))][:n]
+    return ev / ev[0]
