@@ -1,0 +1,309 @@
+"""Benchmark: CTMRG steps/s for the q = 20 dodecahedron model at m = 256, T = 0.4398.
+
+One "step" is one iteration of the while-loop of Algorithm 3 of
+arXiv:2004.08669: extension of the corner, leading eigenpairs of the extended
+corner (warm-started block subspace iteration, capped at --subspace-iters
+iterations per step, FP64 Rayleigh-Ritz), renormalisation of P, normalisation
+of P and Omega, S_E and the convergence measure.  Inputs live in HBM when the
+timed region starts; C~ (N = 5120, 210 MB in FP64) is larger than the 129 MB
+L2, so no explicit L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CTMRG steps/s at q=20 m=256, mixed vs FP64 at |\u0394f|/f\u22641e-10; % tensor peak"
+UNIT = "steps/s"
+# FP64 peak of the CUDA cores: 152 SMs x 2 DFMA/clk/SM x 2 FLOP x SM clock.
+FP64_DFMA_PER_CLK_PER_SM = 2
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64")
+    ap.add_argument("--m", type=int, default=256)
+    ap.add_argument("--T", type=float, default=0.4398)
+    ap.add_argument("--prep", type=int, default=12, help="untimed steps before warm-up (cold start)")
+    ap.add_argument("--subspace-iters", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=150.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    ent = data.get(kernel)
+    if not ent or ent.get("workload") != workload:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    return ent.get("dram_bytes_per_launch") if h == ent.get("source_sha") else None
+
+
+def run_reference(args):
+    """Comparison arm: the CPU oracle (plain C, OpenMP on the host cores)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2004_08669_gb300 import workloads as W
+    O.build()
+    m, q = args.m, 20
+    beta = 1.0 / args.T
+    P, om = W.random_state(m, q, m, seed=2004086690)
+    c = O.CTMRG(W.dodecahedron(), m, beta)
+    c.set_state(P, np.concatenate([om[:m], np.zeros(m * q - m)]), m)
+    t0 = time.perf_counter()
+    nwarm = min(args.warmup, 1)
+    for _ in range(nwarm):
+        c.step()
+    t1 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        c.step()
+        done += 1
+        if time.perf_counter() - t1 > args.cpu_budget_s:
+            break
+    el = time.perf_counter() - t1
+    value = done / el
+    sample = (f"{done} oracle step(s) of {args.steps} requested timed at q=20 m={m} from a seeded full-size "
+              f"state after {nwarm} untimed step(s); each step is a full dense diagonalisation of C~ "
+              f"(N={m * q}); the rate is per step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"dodecahedron q=20 m={m} T={args.T} fp64 (CPU oracle)", "q": q, "m": m,
+                      "T": args.T, "parallelism": "host threads"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(g, args):
+    """The oracle, as it stands, on one full-size step from the GPU's state."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2004_08669_gb300 import workloads as W
+    O.build()
+    P, om, live = g.get_state()
+    c = O.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T)
+    c.set_state(P, np.concatenate([om, np.zeros(args.m * 20 - args.m)]), live)
+    t = time.perf_counter()
+    c.step()
+    el = time.perf_counter() - t
+    return {"value": 1.0 / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"1 oracle step (full dense diagonalisation, N={args.m * 20}) from the GPU run's state, "
+                      f"{el:.1f} s"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2004_08669_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2004_08669_gb300 import ctm, workloads as W
+
+    m, q = args.m, 20
+    beta = 1.0 / args.T
+    g = ctm.CTMRG(W.dodecahedron(), m, beta, prec=args.prec, device=f"cuda:{local}",
+                  max_subspace_iters=args.subspace_iters)
+    stream = g.stream
+    g.step(args.prep)
+    for _ in range(max(args.warmup, 0)):
+        g.step(1)
+    launches0 = g.launch_count()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    g.profile(True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        done, info, st = g.step(1)
+        iters.append(info["subspace_iters"])
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    launches = g.launch_count() - launches0
+    ms_t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the C-ABI with host buffers: per step load the state
+    # from pinned host memory, step, read the spectrum back to the host.
+    blob = g.save()
+    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = np.frombuffer(blob, dtype=np.uint8)
+    import ctypes
+    spec = torch.empty(m, dtype=torch.float64, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctm._check(ctm.lib.ctm_load(g.h, ctypes.c_void_p(pinned.data_ptr()), len(blob)))
+        ctm.ctm_step(g.h, 1)
+        ctm._check(ctm.lib.ctm_get_spectrum(g.h, ctypes.cast(spec.data_ptr(), ctm._dp)))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(blob),
+           "d2h_bytes_per_step": 8 * m}
+
+    # roofline of the dominant kernel class, timed live with events on the
+    # library's stream over the timed region
+    kern = {k: v for k, v in prof.items() if k != "all" and v["ms"] > 0}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_fp64 = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    workload = f"dodecahedron q=20 m={m} T={args.T} {args.prec}"
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": traffic_for(dom, workload),
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock",
+            "share_of_step": d["ms"] / ms, "launches": d["launches"]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+           "config": {"workload": workload, "q": q, "m": m, "T": args.T, "prec": args.prec,
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (C~ is 210 MB FP64), no flush",
+                      "subspace_iters_cap": args.subspace_iters,
+                      "subspace_iters_mean": float(np.mean(iters)), "prep_steps": args.prep},
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+           "kernels_ms": {k: round(v["ms"], 3) for k, v in kern.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * ctm.h -- C-ABI of the GB300 CTMRG library (libctm_gb300.so).
+ *
+ * One handle runs the corner transfer matrix renormalisation group of
+ * arXiv:2004.08669 (Algorithm 3, "Symmetric-CTMRG") for one polyhedron
+ * vector-spin model at one temperature on one GPU.  Every step of the method
+ * runs in the library's own CUDA kernels; the library never calls cuBLAS,
+ * cuSOLVER or any CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Indices are 0-based.  Matrices exchanged with the caller are
+ *    column-major, combined indices put the first leg fastest, exactly as in
+ *    the paper's Algorithms 1-3: the half-row transfer tensor P is m x (m q)
+ *    with column index gamma + m*s, and the extended corner C~ is (m q) x (m q)
+ *    with row index gamma + m*s (gamma: renormalised leg, s: spin).  The
+ *    device keeps its own layout internally and converts on the way in/out.
+ *  - "host" pointers are ordinary CPU memory owned by the caller; the library
+ *    copies from them before returning and never keeps them.  The library
+ *    owns every device buffer it allocates; a caller-provided workspace
+ *    (ctm_config.workspace) stays owned by the caller and must outlive the
+ *    handle.
+ *  - All work is issued on the caller's CUDA stream (borrowed, never
+ *    destroyed).  Calls that return host data synchronise that stream.
+ *  - Errors: every call returns a ctm_status; nothing throws across the ABI.
+ *    ctm_last_error() returns a thread-local message for the last failure.
+ *    A handle stays usable after CTM_ENOTCONVERGED (the caller may keep
+ *    stepping); after CTM_ECUDA or CTM_ETIMEOUT it should be destroyed.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CTM_OK = 0,
+    CTM_EINVAL = 1,          /* invalid argument or configuration            */
+    CTM_ENOMEM = 2,          /* device allocation or workspace too small     */
+    CTM_ENOTCONVERGED = 3,   /* an iteration cap was reached (result usable) */
+    CTM_ENUMERIC = 4,        /* NaN/Inf or a non-positive pivot was produced */
+    CTM_ETIMEOUT = 5,        /* a bounded device-side wait gave up           */
+    CTM_ECUDA = 6,           /* a CUDA runtime call failed                   */
+    CTM_EUNSUPPORTED = 7     /* precision mode or feature not built          */
+} ctm_status;
+
+/* Arithmetic of the contractions (extension, C~ V products, P update).
+ * The Rayleigh-Ritz eigensolve, the CholQR2 re-orthonormalisation and the
+ * normalisations are FP64 in every mode. */
+typedef enum {
+    CTM_FP64 = 0,     /* plain FP64 on the CUDA cores                         */
+    CTM_TF32 = 1,     /* tcgen05 kind::tf32, FP32 accumulate                  */
+    CTM_BF16 = 2,     /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
+    CTM_OZAKI64 = 3   /* FP64 emulated by bf16 slice products on tcgen05      */
+} ctm_precision;
+
+typedef struct {
+    int q;                    /* number of spin states (q >= 2)                    */
+    int dim;                  /* spin-vector dimension (1..4)                       */
+    const double* spins;      /* host, q x dim row-major unit vectors (Sec. I)      */
+    int m;                    /* cutoff dimension (Sec. II), 1 <= m                 */
+    double beta;              /* inverse temperature 1/T, finite, >= 0              */
+    int boundary_spin;        /* fixed boundary spin "s = 1" of Sec. II (0-based)   */
+    ctm_precision prec;
+    int ozaki_slices;         /* slices per operand for CTM_OZAKI64 (0: default)    */
+    double tol_spectrum;      /* convergence of the step loop (default 1e-12)      */
+    int max_steps;            /* cap used by ctm_run (default 5000)                 */
+    int block_extra;          /* subspace width b = m + block_extra (0: default)    */
+    int max_subspace_iters;   /* per step (0: default 50)                           */
+    double subspace_tol;      /* Ritz residual / |w_1| (0: default 1e-13)           */
+    double tol_cluster;       /* multiplet tolerance, relative to |w_1| (0: 1e-10)  */
+    void* workspace;          /* optional device workspace (NULL: library allocates) */
+    size_t workspace_bytes;   /* its size; see ctm_workspace_size                   */
+} ctm_config;
+
+/* Per-step diagnostics (the paper's S_E and c of Algorithm 3 plus the
+ * quantities the build needs). */
+typedef struct {
+    double kappa;          /* Frobenius growth factor of P this step           */
+    double delta;          /* convergence measure (spectrum and kappa change)  */
+    double S_E;            /* entanglement entropy of the kept spectrum (Eq. 6) */
+    double residual;       /* max Ritz residual / |w_1| of the kept states     */
+    int m_eff;             /* states kept after the multiplet rule             */
+    int live_dim;          /* live dimension of C~ this step                   */
+    int subspace_iters;    /* subspace iterations used                          */
+    int jacobi_sweeps;     /* Jacobi sweeps of the last Rayleigh-Ritz          */
+    int steps;             /* CTMRG steps done by this handle                   */
+    int converged;         /* delta < tol_spectrum                              */
+} ctm_step_info;
+
+/* Observables of the current state (Eq. 4-6 and the free energy). */
+typedef struct {
+    double f;       /* free energy per spin, -(T/2) ln kappa                       */
+    double M;       /* spontaneous magnetisation, Eq. (5), kept states             */
+    double u;       /* internal energy per spin, 2 <h> from Tr(C~_h C~^3)/Tr C~^4 */
+    double S_E;     /* entanglement entropy, Eq. (6), kept states                  */
+    double delta;   /* last convergence measure                                    */
+    int steps;      /* CTMRG steps done                                            */
+    int converged;
+} ctm_obs;
+
+typedef struct ctm_handle ctm_handle;
+
+/* Device bytes a handle needs for this configuration. */
+ctm_status ctm_workspace_size(const ctm_config* cfg, size_t* bytes);
+
+/* Create a handle: validates cfg, copies the spin table, builds the vertex
+ * weight of Eq. (1)-(2) on the device and sets the fixed-boundary initial
+ * P and Omega of Algorithm 3.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Validation: q >= 2, 1 <= dim <= 4, m >= 1, beta >= 0
+ * finite, spins of unit norm within 1e-12, 0 <= boundary_spin < q. */
+ctm_status ctm_init(ctm_handle** h, const ctm_config* cfg, void* cuda_stream);
+
+/* Run up to nsteps iterations of the while-loop of Algorithm 3 (extension,
+ * leading eigenpairs of C~, renormalisation, normalisation, S_E and the
+ * convergence test).  Stops early once converged.  *steps_done (may be
+ * NULL) receives the number of steps taken; info (may be NULL) the
+ * diagnostics of the last one.  Returns CTM_ENOTCONVERGED if a subspace
+ * iteration hit its cap (the step is still applied). */
+ctm_status ctm_step(ctm_handle* h, int nsteps, int* steps_done, ctm_step_info* info);
+
+/* Observables of the current state: one more extension and its leading
+ * eigenpairs, then Eq. (5)-(6) and the free energy. out: host. */
+ctm_status ctm_observables(ctm_handle* h, ctm_obs* out);
+
+/* Adjoint of the step for the fixed-point derivatives of f and M with
+ * respect to beta.  Not built yet: returns CTM_EUNSUPPORTED. */
+ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
+
+/* Normalised kept spectrum Omega (host, m entries; zeros past m_eff). */
+ctm_status ctm_get_spectrum(ctm_handle* h, double* omega);
+
+/* State exchange (host buffers, paper layout).  P: m x (m q); omega: m;
+ * live: rows of P that may be non-zero.  ctm_set_state also discards the
+ * warm start of the subspace iteration. */
+ctm_status ctm_get_state(ctm_handle* h, double* P, double* omega, int* live);
+ctm_status ctm_set_state(ctm_handle* h, const double* P, const double* omega, int live);
+
+/* Checkpoint: serialise the whole iteration state (P, Omega, warm start,
+ * counters) into a host buffer.  Call with buf == NULL to get *len. */
+ctm_status ctm_save(ctm_handle* h, void* buf, size_t* len);
+ctm_status ctm_load(ctm_handle* h, const void* buf, size_t len);
+
+/* Inspection for tests: compute only the extension C~ = Sub-CTMRG(P, Omega P,
+ * W) of the current state, then read `count` sampled entries
+ * (row[i], col[i]) in the paper's index into out (host). */
+ctm_status ctm_extend(ctm_handle* h);
+ctm_status ctm_get_ctilde(ctm_handle* h, const int* rows, const int* cols, int count, double* out);
+
+/* Inspection for tests: leading eigenpairs of the C~ last built by
+ * ctm_extend (subspace iteration to subspace_tol, cold or warm start).
+ * evals: host, b entries; vecs: host, (m q) x b in the paper's row index,
+ * or NULL.  *b_out receives b. */
+ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out);
+
+/* Profiling.  While enabled, every kernel class of the step is bracketed by
+ * CUDA events on the handle's stream; ctm_profile_read synchronises the
+ * stream and returns, per class, the launches, the summed device time and
+ * the algorithmic FLOPs and bytes of those launches (the minimum traffic of
+ * each kernel's inputs and outputs).  The last entry, "all", counts every
+ * kernel the handle launched while enabled.  Reading clears the records. */
+typedef struct {
+    const char* name;     /* static string owned by the library */
+    long long launches;
+    double ms;
+    double flops;
+    double bytes;
+} ctm_prof_entry;
+ctm_status ctm_profile(ctm_handle* h, int enable);
+ctm_status ctm_profile_read(ctm_handle* h, ctm_prof_entry* out, int max_entries, int* n_entries);
+
+/* Kernels launched by this handle since ctm_init. */
+ctm_status ctm_launch_count(ctm_handle* h, long long* launches);
+
+const char* ctm_last_error(void);
+void ctm_destroy(ctm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -127,6 +127,30 @@ void or_sub_ctmrg(int m, int q, const double* P, const double* Pp, const double*
     free(X2);
 }
 
+/* One entry of C~ = Sub-CTMRG(P, Omega P, W) at a time, straight from the
+ * composition of Algorithm 3: row gamma + m s', column gamma' + m sigma',
+ *   C~ = sum_{s,sigma} X1[(gamma,s),(gamma',sigma)] w[(s + q sigma), (s' + q sigma')],
+ *   X1[(gamma,s),(gamma',sigma)] = sum_alpha P[alpha,(gamma,s)] omega_alpha P[alpha,(gamma',sigma)]. */
+void or_ctilde_entries(int m, int q, const double* P, const double* omega, const double* w,
+                       int count, const int* rows, const int* cols, double* out) {
+    size_t q2 = (size_t)q * q;
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < count; ++e) {
+        int g = rows[e] % m, sp = rows[e] / m;
+        int gp = cols[e] % m, sgp = cols[e] / m;
+        double acc = 0.0;
+        for (int sg = 0; sg < q; ++sg)
+            for (int s = 0; s < q; ++s) {
+                double x1 = 0.0;
+                for (int a = 0; a < m; ++a)
+                    x1 += P[a + (size_t)m * (g + (size_t)m * s)] * omega[a] *
+                          P[a + (size_t)m * (gp + (size_t)m * sg)];
+                acc += x1 * w[(s + (size_t)q * sg) + q2 * (sp + (size_t)q * sgp)];
+            }
+        out[e] = acc;
+    }
+}
+
 /* ---------------------------------------------------------------------
  * Dense symmetric eigensolver.
  * Householder reduction to tridiagonal form and the implicit symmetric QR
@@ -221,7 +245,14 @@ int or_eigh(int n, double* A, double* evals, double* Z) {
         }
     }
 
-    /* --- implicit symmetric QR with Wilkinson shift on (d, e). */
+    /* --- implicit symmetric QR with Wilkinson shift on (d, e).  The
+     *     rotations act on columns k, k+1 of Z; Z is held transposed (row i
+     *     of Z contiguous) while they are applied, so that each row is
+     *     streamed once per sweep. */
+    double* Zt = (double*)malloc(ld * ld * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) Zt[k + ld * i] = Z[i + ld * k];
     double* cs = (double*)malloc(2 * (size_t)n * sizeof(double));
     int hi = n - 1;
     long iter = 0, maxiter = 60L * n + 60;
@@ -269,16 +300,21 @@ int or_eigh(int n, double* A, double* evals, double* Z) {
         /* Z <- Z G_lo ... G_{hi-1}; rows are independent. */
 #pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) {
+            double* zr = Zt + ld * i;
             for (int r = 0; r < nrot; ++r) {
                 int k = lo + r;
                 double c = cs[2 * r], s = cs[2 * r + 1];
-                double zk = Z[i + ld * k], zk1 = Z[i + ld * (k + 1)];
-                Z[i + ld * k] = c * zk - s * zk1;
-                Z[i + ld * (k + 1)] = s * zk + c * zk1;
+                double zk = zr[k], zk1 = zr[k + 1];
+                zr[k] = c * zk - s * zk1;
+                zr[k + 1] = s * zk + c * zk1;
             }
         }
     }
     free(cs);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) Z[i + ld * k] = Zt[k + ld * i];
+    free(Zt);
 
     /* --- sort by |eigenvalue| descending (stable in the original order). */
     int* ord = (int*)malloc((size_t)n * sizeof(int));

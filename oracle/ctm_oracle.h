@@ -63,6 +63,11 @@ void or_pindex2(const double* A, int a, int b, int c, double* B);
 void or_sub_ctmrg(int m, int q, const double* P, const double* Pp,
                   const double* w, double* out);
 
+/* Sampled entries of C~ = Sub-CTMRG(P, Omega P, W), computed one by one
+ * (rows/cols in the paper's combined index gamma + m s). */
+void or_ctilde_entries(int m, int q, const double* P, const double* omega, const double* w,
+                       int count, const int* rows, const int* cols, double* out);
+
 /* Dense symmetric eigensolver (Householder tridiagonalisation followed by the
  * implicit symmetric QR iteration with Wilkinson shift).  A (n x n,
  * column-major, symmetric) is destroyed.  On return evals[i] and column i of

@@ -51,6 +51,8 @@ def lib():
             L.or_pindex.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
             L.or_pindex2.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
             L.or_sub_ctmrg.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+            L.or_ctilde_entries.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
             L.or_eigh.argtypes = [ctypes.c_int, _dp, _dp, _dp]
             L.or_eigh.restype = ctypes.c_int
             L.or_num_threads.restype = ctypes.c_int
@@ -116,6 +118,19 @@ def sub_ctmrg(P: np.ndarray, Pp: np.ndarray, w: np.ndarray, m: int, q: int) -> n
     N = m * q
     out = np.zeros((N, N), order="F")
     lib().or_sub_ctmrg(m, q, _p(P), _p(Pp), _p(w), _p(out))
+    return out
+
+
+def ctilde_entries(P, omega, w, m: int, q: int, rows, cols) -> np.ndarray:
+    """Entries C~[rows[i], cols[i]] of Sub-CTMRG(P, Omega P, W), one by one."""
+    P, w = _f64(P), _f64(w)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.zeros(len(r))
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib().or_ctilde_entries(m, q, _p(P), om.ctypes.data_as(_dp), _p(w), len(r), r.ctypes.data_as(ip),
+                            c.ctypes.data_as(ip), out.ctypes.data_as(_dp))
     return out
 
 

@@ -1,0 +1,957 @@
+// ctm.cu -- host orchestration of the CTMRG step and the C-ABI of include/ctm.h.
+//
+// One handle = one temperature of Algorithm 3 (Symmetric-CTMRG) of
+// arXiv:2004.08669 on one GPU.  A step is
+//   a2  extension   C~ = Sub-CTMRG(P, Omega P, W)      (gemm_f64 + wcontract_f64)
+//   a3  eigenpairs  leading b Ritz pairs of C~           (subspace iteration,
+//                   FP64 Jacobi Rayleigh-Ritz, CholQR2, multiplet-aware cut,
+//                   gauge alignment to the previous step)
+//   a4  renormalise P <- U^t Sub-CTMRG(P, U', W)          (gemm_f64 + wcontract_f64)
+//   a5  normalise   P <- P / ||P||_F, Omega <- Omega / (sum w^4)^{1/4}
+//   a6  S_E (Eq. 6) and the convergence measure delta on the device.
+// The host only sequences launches and reads back one small control block per
+// subspace iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ctm.h"
+#include "ctm_internal.cuh"
+#include "eig_f64.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+ctm_status fail(ctm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CTM_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(CTM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    int q, dim, m, N, b, npad, splits;
+    size_t off_spins, off_E, off_Eh, off_mag, off_P, off_Pn, off_omega, off_prev, off_C, off_V, off_Y,
+        off_Z, off_T, off_Zprev, off_U, off_Up, off_H, off_Sb, off_G, off_Linv, off_theta, off_res,
+        off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
+        off_mfull, off_colv, total;
+};
+
+Layout make_layout(const ctm_config& c) {
+    Layout L{};
+    L.q = c.q;
+    L.dim = c.dim;
+    L.m = c.m;
+    L.N = c.m * c.q;
+    int extra = c.block_extra > 0 ? c.block_extra : std::max(8, c.m / 8);
+    L.b = std::min(L.N, c.m + extra);
+    L.npad = L.b + (L.b & 1);
+    if (L.npad < 2) L.npad = 2;
+    L.splits = 16;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align256(o + bytes);
+        return r;
+    };
+    const size_t d = sizeof(double);
+    const size_t N = L.N, b = L.b, m = L.m, q = L.q, np = L.npad;
+    L.off_spins = take(q * L.dim * d);
+    L.off_E = take(q * q * d);
+    L.off_Eh = take(q * q * d);
+    L.off_mag = take(q * d);
+    L.off_P = take(m * N * d);
+    L.off_Pn = take(m * N * d);
+    L.off_omega = take(m * d);
+    L.off_prev = take(m * d);
+    L.off_C = take(N * N * d);
+    L.off_V = take(N * b * d);
+    L.off_Y = take(N * b * d);
+    L.off_Z = take(N * b * d);
+    L.off_T = take(N * b * d);
+    L.off_Zprev = take(N * b * d);
+    L.off_U = take(N * m * d);
+    L.off_Up = take(m * N * d);
+    L.off_H = take(b * b * d);
+    L.off_Sb = take(b * b * d);
+    L.off_G = take(b * b * d);
+    L.off_Linv = take(b * b * d);
+    L.off_theta = take(np * d);
+    L.off_res = take(np * d);
+    L.off_part = take((size_t)L.splits * b * b * d);
+    L.off_red = take(4096 * d);
+    L.off_A0 = take(np * np * d);
+    L.off_A1 = take(np * np * d);
+    L.off_S = take(np * np * d);
+    L.off_diag = take(np * d);
+    L.off_rank = take(np * sizeof(int));
+    L.off_gd = take(3 * np * d);
+    L.off_gQ = take(4 * np * d);
+    L.off_gk = take(np * sizeof(int));
+    L.off_ctl = take(sizeof(ctm::DevCtl));
+    L.off_mfull = take(sizeof(int));
+    L.off_colv = take(2 * np * d);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+struct ctm_handle {
+    ctm_config cfg;
+    Layout lay;
+    cudaStream_t st = nullptr;
+    bool own_ws = false;
+    char* ws = nullptr;
+    // device views
+    double *spins, *E, *Eh, *mag, *P, *Pn, *omega, *prev, *C, *V, *Y, *Z, *T, *Zprev, *U, *Up, *H, *Sb, *G,
+        *Linv, *theta, *res, *part, *red, *colv;
+    int* mfull;
+    ctm::EigWork ew;
+    ctm::DevCtl* ctl;
+    ctm::DevCtl* hctl = nullptr;  // pinned mirror
+    // host-side iteration state
+    int live = 1;
+    int steps = 0;
+    bool warm = false;
+    int warm_live = -1;
+    uint64_t seed = 2004086690ull;
+    ctm_step_info last{};
+    std::vector<double> spins_h;
+    // profiling (kernel classes timed with events on st) and launch counting
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double flops, bytes;
+        int nk;
+    };
+    bool prof_on = false;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    long long launches = 0;
+    long long launches_prof = 0;
+};
+
+namespace {
+
+ctm_status validate(const ctm_config* c) {
+    if (!c) return fail(CTM_EINVAL, "config is NULL");
+    if (c->q < 2 || c->q > 32) return fail(CTM_EINVAL, "q must be in [2, 32]");
+    if (c->dim < 1 || c->dim > 4) return fail(CTM_EINVAL, "dim must be in [1, 4]");
+    if (!c->spins) return fail(CTM_EINVAL, "spins is NULL");
+    if (c->m < 1) return fail(CTM_EINVAL, "m must be >= 1");
+    if ((long)c->m * c->q > 65536) return fail(CTM_EINVAL, "m q must be <= 65536");
+    if (!(c->beta >= 0.0) || !isfinite(c->beta)) return fail(CTM_EINVAL, "beta must be finite and >= 0");
+    if (c->boundary_spin < 0 || c->boundary_spin >= c->q) return fail(CTM_EINVAL, "boundary_spin out of range");
+    for (int s = 0; s < c->q; ++s) {
+        double n2 = 0.0;
+        for (int k = 0; k < c->dim; ++k) n2 += c->spins[s * c->dim + k] * c->spins[s * c->dim + k];
+        if (!(fabs(sqrt(n2) - 1.0) <= 1e-12)) return fail(CTM_EINVAL, "spins must be unit vectors");
+    }
+    if (c->prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "only CTM_FP64 is built in this library");
+    return CTM_OK;
+}
+
+ctm_config with_defaults(const ctm_config& c) {
+    ctm_config r = c;
+    if (r.tol_spectrum <= 0.0) r.tol_spectrum = 1e-12;
+    if (r.max_steps <= 0) r.max_steps = 5000;
+    if (r.max_subspace_iters <= 0) r.max_subspace_iters = 50;
+    if (r.subspace_tol <= 0.0) r.subspace_tol = 1e-13;
+    if (r.tol_cluster <= 0.0) r.tol_cluster = 1e-10;
+    return r;
+}
+
+// ------------------------------------------------------------ small kernels
+__global__ void k_weights(int q, int dim, const double* __restrict__ v, double beta, int bspin,
+                          double* __restrict__ E, double* __restrict__ Eh, double* __restrict__ mag) {
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        int a = e % q, b = e / q;
+        double d = 0.0;
+        for (int k = 0; k < dim; ++k) d += v[a * dim + k] * v[b * dim + k];
+        double w = exp(beta * d);  // Eq. (2): one bond's share exp(-h/T), h = -v.v
+        E[e] = w;
+        Eh[e] = -d * w;            // the same bond with its energy h inserted
+    }
+    for (int s = threadIdx.x; s < q; s += blockDim.x) {
+        double d = 0.0;
+        for (int k = 0; k < dim; ++k) d += v[bspin * dim + k] * v[s * dim + k];
+        mag[s] = d;
+    }
+}
+
+// U (N x m) = Z[:, :m] with columns >= meff zeroed; U' (m x N) with
+// U'[alpha + m (sigma + q alpha')] = U[(sigma + q alpha) + N alpha'] (P-Index2).
+__global__ void k_make_U(int N, int m, int q, const double* __restrict__ Z, int ldz,
+                         const ctm::DevCtl* __restrict__ ctl, double* __restrict__ U, double* __restrict__ Up) {
+    const int meff = ctl->meff_new;
+    size_t tot = (size_t)N * m;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int t = (int)(e % N), ap = (int)(e / N);
+        double v = (ap < meff) ? Z[t + (size_t)ldz * ap] : 0.0;
+        U[e] = v;
+        int sigma = t % q, alpha = t / q;
+        Up[alpha + (size_t)m * (sigma + (size_t)q * ap)] = v;
+    }
+}
+
+// Deterministic partial sums of squares.
+__global__ void k_sumsq_partial(size_t n, const double* __restrict__ x, double* __restrict__ part) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        s += x[i] * x[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// a5/a6: kappa, Omega normalisation, S_E of the kept spectrum, delta.
+__global__ void k_step_finalize(int m, int nparts, const double* __restrict__ part,
+                                const double* __restrict__ theta, double* __restrict__ omega,
+                                double* __restrict__ prev, ctm::DevCtl* ctl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double ss = 0.0;
+    for (int i = 0; i < nparts; ++i) ss += part[i];
+    double kappa = sqrt(ss);
+    int meff = ctl->meff_new;
+    double z4 = 0.0;
+    for (int i = 0; i < meff; ++i) z4 += pow(theta[i], 4);
+    double sc = pow(z4, -0.25);
+    double SE = 0.0;
+    for (int i = 0; i < meff; ++i) {
+        double p = pow(theta[i], 4) / z4;
+        if (p > 0.0) SE -= p * log(p);
+    }
+    double a1 = fabs(theta[0]);
+    double delta = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double w = (i < meff) ? theta[i] * sc : 0.0;
+        omega[i] = w;
+        double r = (i < meff) ? fabs(theta[i]) / a1 : 0.0;
+        if (ctl->have_prev) delta = fmax(delta, fabs(r - prev[i]));
+        prev[i] = r;
+    }
+    if (ctl->have_prev) delta = fmax(delta, fabs(kappa / ctl->prev_kappa - 1.0));
+    else delta = INFINITY;
+    if (!isfinite(kappa) || kappa == 0.0 || !isfinite(SE)) ctl->numeric_bad = 1;
+    ctl->have_prev = 1;
+    ctl->prev_kappa = kappa;
+    ctl->kappa = kappa;
+    ctl->delta = delta;
+    ctl->SE = SE;
+    ctl->live = meff;
+}
+
+__global__ void k_scale(size_t n, const double* __restrict__ x, const ctm::DevCtl* __restrict__ ctl,
+                        double* __restrict__ y) {
+    double inv = 1.0 / ctl->kappa;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = x[i] * inv;
+}
+
+// Observables: per kept column, col[i] = sum_t Z_ti^2 mag(t mod q) and
+// col[b + i] = z_i . Yh_i.
+__global__ void k_obs_cols(int N, int q, int b, const double* __restrict__ Z, const double* __restrict__ Yh,
+                           const double* __restrict__ mag, double* __restrict__ col) {
+    __shared__ double red[2][32];
+    int i = blockIdx.x;
+    double s0 = 0.0, s1 = 0.0;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        double z = Z[t + (size_t)N * i];
+        s0 += z * z * mag[t % q];
+        s1 += z * Yh[t + (size_t)N * i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s0;
+        red[1][threadIdx.x >> 5] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        s0 = threadIdx.x < nw ? red[0][threadIdx.x] : 0.0;
+        s1 = threadIdx.x < nw ? red[1][threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (threadIdx.x == 0) {
+            col[i] = s0;
+            col[b + i] = s1;
+        }
+    }
+}
+
+__global__ void k_obs_finalize(int b, const double* __restrict__ theta, const double* __restrict__ col,
+                               ctm::DevCtl* ctl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int meff = ctl->meff_new;
+    double z4 = 0, mn = 0, un = 0;
+    for (int i = 0; i < meff; ++i) {
+        double w = theta[i], w3 = w * w * w, w4 = w3 * w;
+        z4 += w4;
+        mn += w4 * col[i];
+        un += w3 * col[b + i];
+    }
+    double SE = 0.0;
+    for (int i = 0; i < meff; ++i) {
+        double p = pow(theta[i], 4) / z4;
+        if (p > 0.0) SE -= p * log(p);
+    }
+    ctl->obs_M_num = mn;
+    ctl->obs_u_num = un;
+    ctl->obs_z4 = z4;
+    ctl->obs_SE = SE;
+}
+
+__global__ void k_gather(int count, const long long* __restrict__ idx, const double* __restrict__ C,
+                         double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = C[idx[i]];
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+inline int grid_for(size_t work, int cap = 152 * 8) {
+    size_t g = (work + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+// --------------------------------------------------------------- profiling
+enum ProfClass { PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_SMALL, PC_COUNT };
+const char* const kProfNames[PC_COUNT + 1] = {"gemm_f64", "wcontract_f64", "jacobi_f64", "cholqr_f64", "small",
+                                              "all"};
+
+cudaEvent_t take_event(ctm_handle* h) {
+    if (h->evnext == h->evpool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->evpool.push_back(e);
+    }
+    return h->evpool[h->evnext++];
+}
+
+// Bracket one kernel class: begin returns an event (or null when off).
+cudaEvent_t prof_begin(ctm_handle* h) {
+    if (!h->prof_on) return nullptr;
+    cudaEvent_t a = take_event(h);
+    cudaEventRecord(a, h->st);
+    return a;
+}
+
+void prof_end(ctm_handle* h, cudaEvent_t a, int cls, int nk, double flops = 0.0, double bytes = 0.0) {
+    h->launches += nk;
+    if (!h->prof_on) return;
+    h->launches_prof += nk;
+    if (!a) return;
+    cudaEvent_t b = take_event(h);
+    cudaEventRecord(b, h->st);
+    h->recs.push_back({cls, a, b, flops, bytes, nk});
+}
+
+// Small bookkeeping kernels: counted, not timed.
+void count_small(ctm_handle* h, int nk) {
+    h->launches += nk;
+    if (h->prof_on) h->launches_prof += nk;
+}
+
+// Profiled FP64 GEMM with its algorithmic FLOPs and minimum bytes.
+void pgemm(ctm_handle* h, bool tA, bool tB, int M, int N, int K, const double* A, int lda, const double* B,
+           int ldb, double* C, int ldc, const double* scaleK = nullptr, int splits = 1) {
+    cudaEvent_t a = prof_begin(h);
+    int nk = ctm::gemm_f64(h->st, tA, tB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, scaleK, splits, h->part);
+    double fl = 2.0 * M * (double)N * K;
+    double by = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
+    prof_end(h, a, PC_GEMM, nk, fl, by);
+}
+
+void pwcontract(ctm_handle* h, double* X, const double* E1, const int* live_dev, int live_host) {
+    const Layout& L = h->lay;
+    cudaEvent_t a = prof_begin(h);
+    ctm::wcontract_f64(h->st, L.m, L.q, X, L.N, h->E, E1, live_dev);
+    double nb = (double)live_host * live_host, q = L.q;
+    prof_end(h, a, PC_WCONTRACT, 1, nb * 4.0 * q * q * q, nb * 2.0 * 8.0 * q * q);
+}
+
+// --------------------------------------------------------------- stages
+ctm_status sync_ctl(ctm_handle* h) {
+    CTM_CUDA(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(ctm::DevCtl), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    return CTM_OK;
+}
+
+// Split-K factor: enough CTAs to fill the GPU, at least 128 of K per split,
+// and never more partial sums than the partial buffer (splits_max b^2) holds.
+int gemm_splits(const Layout& L, int M, int Nn, int K) {
+    long tiles = (long)((M + 63) / 64) * ((Nn + 63) / 64);
+    long want = (2L * 152 + tiles - 1) / tiles;
+    long maxs = std::max(1, K / 128);
+    long cap = ((long)L.splits * L.b * L.b) / ((long)M * Nn);
+    long s = std::min<long>(std::min<long>(want, maxs), std::min<long>(L.splits, cap));
+    return (int)std::max<long>(1, s);
+}
+
+// C = P^t diag(omega) P, then the vertex-weight contraction (E1 = E or Eh).
+void stage_extend(ctm_handle* h, const double* E1) {
+    const Layout& L = h->lay;
+    pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega);
+    pwcontract(h, h->C, E1, &h->ctl->live, h->live);
+}
+
+// Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR2) or
+// 3 (shifted first pass, then CholQR2).  tmp is clobbered.
+ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int passes) {
+    const Layout& L = h->lay;
+    const int N = L.N, b = L.b;
+    double* bufs[2] = {dst, tmp};
+    double* cur = src;
+    for (int i = 0; i < passes; ++i) {
+        double* out = bufs[(passes - 1 - i) % 2];
+        pgemm(h, true, false, b, b, N, cur, N, cur, N, h->G, b, nullptr, gemm_splits(L, b, b, N));
+        double shift_rel = (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
+        cudaEvent_t a = prof_begin(h);
+        CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl));
+        ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b);
+        prof_end(h, a, PC_CHOLQR, 2, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
+        pgemm(h, false, true, N, b, b, cur, N, h->Linv, b, out, N);
+        cur = out;
+    }
+    CTM_CUDA(cudaGetLastError());
+    return CTM_OK;
+}
+
+// Leading b eigenpairs of C (a3).  On return theta/Z hold the sorted Ritz
+// pairs, h->hctl the decision (meff_new, residual, convergence).
+ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* iters_used) {
+    const Layout& L = h->lay;
+    const int N = L.N, b = L.b, m = L.m;
+    const int Ldim = L.q * h->live;
+    bool cold = true;
+    int passes = 3;
+    if (Ldim <= b) {
+        ctm::identity_block(h->st, N, b, h->V, N);
+        count_small(h, 1);
+        max_iters = 1;
+        passes = 2;
+    } else if (h->warm && h->warm_live == h->live) {
+        CTM_CUDA(cudaMemcpyAsync(h->V, h->Zprev, sizeof(double) * N * b, cudaMemcpyDeviceToDevice, h->st));
+        cold = false;
+        passes = 2;
+    } else {
+        ctm::randn_block(h->st, N, b, h->Y, N, h->seed + (uint64_t)h->steps);
+        count_small(h, 1);
+        ctm_status s = stage_orth(h, h->Y, h->V, h->T, 3);
+        if (s != CTM_OK) return s;
+        max_iters = std::max(max_iters, 200);
+    }
+    bool conv = false;
+    int it = 0;
+    for (it = 0; it < max_iters; ++it) {
+        pgemm(h, false, false, N, b, N, h->C, N, h->V, N, h->Y, N);
+        pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+        cudaEvent_t ja = prof_begin(h);
+        CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
+        prof_end(h, ja, PC_JACOBI, 4);
+        pgemm(h, false, false, N, b, b, h->V, N, h->Sb, b, h->Z, N);
+        pgemm(h, false, false, N, b, b, h->Y, N, h->Sb, b, h->T, N);
+        int nchk = std::min(m + 1, std::min(b, Ldim));
+        ctm::resid_f64(h->st, N, nchk, h->T, h->Z, N, h->theta, h->res);
+        ctm::decide(h->st, b, Ldim, m, h->cfg.subspace_tol, h->cfg.tol_cluster, h->theta, h->res, h->ctl);
+        count_small(h, (nchk > 0 ? 1 : 0) + 1);
+        CTM_CUDA(cudaGetLastError());
+        ctm_status s = sync_ctl(h);
+        if (s != CTM_OK) return s;
+        if (h->hctl->jac_status == 2 || h->hctl->chol_status == 2)
+            return fail(CTM_ETIMEOUT, "a device-side barrier timed out");
+        if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the eigen stage");
+        if (h->hctl->sub_converged) {
+            conv = true;
+            ++it;
+            break;
+        }
+        if (it + 1 == max_iters) {
+            ++it;
+            break;
+        }
+        ctm::next_block(h->st, N, b, h->T, h->Z, N, h->theta, 1e-12, h->Y);
+        count_small(h, 1);
+        s = stage_orth(h, h->Y, h->V, h->T, passes);
+        if (s != CTM_OK) return s;
+        CTM_CUDA(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(ctm::DevCtl), cudaMemcpyDeviceToHost, h->st));
+        CTM_CUDA(cudaStreamSynchronize(h->st));
+        if (h->hctl->chol_status == 1) return fail(CTM_ENUMERIC, "Cholesky QR met a non-positive pivot");
+    }
+    if (!cold) {
+        ctm::gauge_align(h->st, N, b, h->Z, h->Zprev, N, h->theta, h->cfg.tol_cluster, h->ew);
+        count_small(h, 3);
+    }
+    CTM_CUDA(cudaGetLastError());
+    *sub_converged = conv;
+    *iters_used = it;
+    return CTM_OK;
+}
+
+ctm_status step_once(ctm_handle* h) {
+    const Layout& L = h->lay;
+    const int N = L.N, m = L.m;
+    const int live_in = h->live;  // basis of this step's C~
+    stage_extend(h, h->E);
+    bool conv = false;
+    int iters = 0;
+    ctm_status s = stage_eigen(h, h->cfg.max_subspace_iters, &conv, &iters);
+    if (s != CTM_OK) return s;
+    const int meff = h->hctl->meff_new;
+    if (meff < 1) return fail(CTM_ENUMERIC, "no state kept");
+    // a4: U, U' and P <- U^t Sub-CTMRG(P, U', W)
+    k_make_U<<<grid_for((size_t)N * m), 256, 0, h->st>>>(N, m, L.q, h->Z, N, h->ctl, h->U, h->Up);
+    count_small(h, 1);
+    pgemm(h, true, false, N, N, m, h->P, m, h->Up, m, h->C, N);
+    pwcontract(h, h->C, h->E, h->mfull, m);
+    pgemm(h, true, false, m, N, N, h->U, N, h->C, N, h->Pn, m, nullptr, gemm_splits(L, m, N, N));
+    // a5/a6
+    const int nparts = 512;
+    k_sumsq_partial<<<nparts, 256, 0, h->st>>>((size_t)m * N, h->Pn, h->red);
+    k_step_finalize<<<1, 32, 0, h->st>>>(m, nparts, h->red, h->theta, h->omega, h->prev, h->ctl);
+    k_scale<<<grid_for((size_t)m * N), 256, 0, h->st>>>((size_t)m * N, h->Pn, h->ctl, h->P);
+    count_small(h, 3);
+    CTM_CUDA(cudaGetLastError());
+    s = sync_ctl(h);
+    if (s != CTM_OK) return s;
+    if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the renormalisation");
+    // the warm start for the next step is this step's aligned Ritz block
+    std::swap(h->Z, h->Zprev);
+    h->warm = true;
+    h->warm_live = live_in;  // valid for the next step only if its live dim is unchanged
+    h->live = meff;
+    h->steps += 1;
+    ctm_step_info& I = h->last;
+    I.kappa = h->hctl->kappa;
+    I.delta = h->hctl->delta;
+    I.S_E = h->hctl->SE;
+    I.residual = h->hctl->resid;
+    I.m_eff = meff;
+    I.live_dim = L.q * meff;
+    I.subspace_iters = iters;
+    I.jacobi_sweeps = h->hctl->jac_sweeps;
+    I.steps = h->steps;
+    I.converged = (h->hctl->delta < h->cfg.tol_spectrum) ? 1 : 0;
+    return conv ? CTM_OK : CTM_ENOTCONVERGED;
+}
+
+}  // namespace
+
+// ================================================================ C-ABI
+extern "C" {
+
+const char* ctm_last_error(void) { return g_err.c_str(); }
+
+ctm_status ctm_workspace_size(const ctm_config* cfg, size_t* bytes) {
+    ctm_status s = validate(cfg);
+    if (s != CTM_OK) return s;
+    if (!bytes) return fail(CTM_EINVAL, "bytes is NULL");
+    *bytes = make_layout(with_defaults(*cfg)).total;
+    return CTM_OK;
+}
+
+ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) {
+    if (!out) return fail(CTM_EINVAL, "handle pointer is NULL");
+    *out = nullptr;
+    ctm_status s = validate(cfg);
+    if (s != CTM_OK) return s;
+    ctm_handle* h = new ctm_handle();
+    h->cfg = with_defaults(*cfg);
+    h->lay = make_layout(h->cfg);
+    const Layout& L = h->lay;
+    h->st = (cudaStream_t)cuda_stream;
+    if (cfg->workspace) {
+        if (cfg->workspace_bytes < L.total) {
+            delete h;
+            return fail(CTM_ENOMEM, "workspace too small");
+        }
+        h->ws = (char*)cfg->workspace;
+    } else {
+        if (cudaMalloc(&h->ws, L.total) != cudaSuccess) {
+            delete h;
+            return fail(CTM_ENOMEM, "cudaMalloc of the workspace failed");
+        }
+        h->own_ws = true;
+    }
+    if (cudaMallocHost(&h->hctl, sizeof(ctm::DevCtl)) != cudaSuccess) {
+        ctm_destroy(h);
+        return fail(CTM_ENOMEM, "pinned host allocation failed");
+    }
+    auto D = [&](size_t off) { return (double*)(h->ws + off); };
+    h->spins = D(L.off_spins);
+    h->E = D(L.off_E);
+    h->Eh = D(L.off_Eh);
+    h->mag = D(L.off_mag);
+    h->P = D(L.off_P);
+    h->Pn = D(L.off_Pn);
+    h->omega = D(L.off_omega);
+    h->prev = D(L.off_prev);
+    h->C = D(L.off_C);
+    h->V = D(L.off_V);
+    h->Y = D(L.off_Y);
+    h->Z = D(L.off_Z);
+    h->T = D(L.off_T);
+    h->Zprev = D(L.off_Zprev);
+    h->U = D(L.off_U);
+    h->Up = D(L.off_Up);
+    h->H = D(L.off_H);
+    h->Sb = D(L.off_Sb);
+    h->G = D(L.off_G);
+    h->Linv = D(L.off_Linv);
+    h->theta = D(L.off_theta);
+    h->res = D(L.off_res);
+    h->part = D(L.off_part);
+    h->red = D(L.off_red);
+    h->colv = D(L.off_colv);
+    h->ew.A0 = D(L.off_A0);
+    h->ew.A1 = D(L.off_A1);
+    h->ew.S = D(L.off_S);
+    h->ew.diag = D(L.off_diag);
+    h->ew.rank = (int*)(h->ws + L.off_rank);
+    h->ew.gdots = D(L.off_gd);
+    h->ew.gQ = D(L.off_gQ);
+    h->ew.gkind = (int*)(h->ws + L.off_gk);
+    h->ctl = (ctm::DevCtl*)(h->ws + L.off_ctl);
+    h->mfull = (int*)(h->ws + L.off_mfull);
+    h->spins_h.assign(cfg->spins, cfg->spins + (size_t)cfg->q * cfg->dim);
+
+    cudaStream_t st = h->st;
+    auto bail = [&](cudaError_t e, const char* what) {
+        ctm_destroy(h);
+        return fail(CTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->ws, 0, L.total, st)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemcpyAsync(h->spins, cfg->spins, sizeof(double) * L.q * L.dim, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return bail(e, "spins upload");
+    k_weights<<<1, 256, 0, st>>>(L.q, L.dim, h->spins, cfg->beta, cfg->boundary_spin, h->E, h->Eh, h->mag);
+    // Algorithm 3 initialisation: p = 1 at alpha = 1, (gamma = 1, s = boundary); omega = e_1.
+    const double one = 1.0;
+    size_t p0 = 0 + (size_t)L.m * (cfg->boundary_spin + (size_t)L.q * 0);
+    if ((e = cudaMemcpyAsync(h->P + p0, &one, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return bail(e, "P init");
+    if ((e = cudaMemcpyAsync(h->omega, &one, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return bail(e, "omega init");
+    k_set_int<<<1, 1, 0, st>>>(&h->ctl->live, 1);
+    k_set_int<<<1, 1, 0, st>>>(h->mfull, L.m);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "init sync");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init kernels");
+    h->live = 1;
+    *out = h;
+    return CTM_OK;
+}
+
+void ctm_destroy(ctm_handle* h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    delete h;
+}
+
+ctm_status ctm_profile(ctm_handle* h, int enable) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    h->prof_on = enable != 0;
+    h->recs.clear();
+    h->evnext = 0;
+    h->launches_prof = 0;
+    return CTM_OK;
+}
+
+ctm_status ctm_profile_read(ctm_handle* h, ctm_prof_entry* out, int max_entries, int* n_entries) {
+    if (!h || !out || !n_entries) return fail(CTM_EINVAL, "NULL argument");
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    ctm_prof_entry agg[PC_COUNT + 1];
+    for (int c = 0; c <= PC_COUNT; ++c) agg[c] = {kProfNames[c], 0, 0.0, 0.0, 0.0};
+    for (const auto& r : h->recs) {
+        float ms = 0.f;
+        CTM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        agg[r.cls].launches += r.nk;
+        agg[r.cls].ms += ms;
+        agg[r.cls].flops += r.flops;
+        agg[r.cls].bytes += r.bytes;
+    }
+    agg[PC_COUNT].launches = h->launches_prof;
+    int n = std::min(max_entries, PC_COUNT + 1);
+    for (int c = 0; c < n; ++c) out[c] = agg[c];
+    *n_entries = n;
+    h->recs.clear();
+    h->evnext = 0;
+    h->launches_prof = 0;
+    return CTM_OK;
+}
+
+ctm_status ctm_launch_count(ctm_handle* h, long long* launches) {
+    if (!h || !launches) return fail(CTM_EINVAL, "NULL argument");
+    *launches = h->launches;
+    return CTM_OK;
+}
+
+ctm_status ctm_step(ctm_handle* h, int nsteps, int* steps_done, ctm_step_info* info) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(CTM_EINVAL, "nsteps < 0");
+    int done = 0;
+    ctm_status worst = CTM_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        ctm_status s = step_once(h);
+        if (s != CTM_OK && s != CTM_ENOTCONVERGED) {
+            if (steps_done) *steps_done = done;
+            return s;
+        }
+        if (s == CTM_ENOTCONVERGED) worst = s;
+        ++done;
+        if (h->last.converged) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (info) *info = h->last;
+    if (worst != CTM_OK) fail(worst, "a subspace iteration reached its cap");
+    return worst;
+}
+
+ctm_status ctm_observables(ctm_handle* h, ctm_obs* out) {
+    if (!h || !out) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    const int N = L.N, b = L.b;
+    stage_extend(h, h->E);
+    bool conv = false;
+    int iters = 0;
+    ctm_status s = stage_eigen(h, h->cfg.max_subspace_iters, &conv, &iters);
+    if (s != CTM_OK) return s;
+    // the eigen stage aligned Z to Zprev; keep it as the warm start
+    std::swap(h->Z, h->Zprev);
+    h->warm = true;
+    h->warm_live = h->live;
+    // impurity corner C~_h (bond energy inserted), then Yh = C~_h Z
+    stage_extend(h, h->Eh);
+    pgemm(h, false, false, N, b, N, h->C, N, h->Zprev, N, h->Y, N);
+    k_obs_cols<<<b, 256, 0, h->st>>>(N, L.q, b, h->Zprev, h->Y, h->mag, h->colv);
+    k_obs_finalize<<<1, 32, 0, h->st>>>(b, h->theta, h->colv, h->ctl);
+    count_small(h, 2);
+    CTM_CUDA(cudaGetLastError());
+    s = sync_ctl(h);
+    if (s != CTM_OK) return s;
+    const ctm::DevCtl& c = *h->hctl;
+    double kappa = h->last.kappa > 0.0 ? h->last.kappa : c.kappa;
+    out->f = (h->cfg.beta > 0.0 && kappa > 0.0) ? -0.5 / h->cfg.beta * log(kappa) : NAN;
+    out->M = c.obs_M_num / c.obs_z4;
+    out->u = 2.0 * c.obs_u_num / c.obs_z4;
+    out->S_E = c.obs_SE;
+    out->delta = h->last.delta;
+    out->steps = h->steps;
+    out->converged = h->last.converged;
+    return conv ? CTM_OK : fail(CTM_ENOTCONVERGED, "observables: subspace iteration reached its cap");
+}
+
+ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta) {
+    (void)h;
+    (void)grad_obs;
+    (void)grad_beta;
+    return fail(CTM_EUNSUPPORTED, "ctm_step_backward is not built yet");
+}
+
+ctm_status ctm_get_spectrum(ctm_handle* h, double* omega) {
+    if (!h || !omega) return fail(CTM_EINVAL, "NULL argument");
+    CTM_CUDA(cudaMemcpyAsync(omega, h->omega, sizeof(double) * h->lay.m, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    return CTM_OK;
+}
+
+ctm_status ctm_get_state(ctm_handle* h, double* P, double* omega, int* live) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    const Layout& L = h->lay;
+    if (P) {
+        std::vector<double> tmp((size_t)L.m * L.N);
+        CTM_CUDA(cudaMemcpyAsync(tmp.data(), h->P, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, h->st));
+        CTM_CUDA(cudaStreamSynchronize(h->st));
+        for (int g = 0; g < L.m; ++g)
+            for (int s = 0; s < L.q; ++s)
+                for (int a = 0; a < L.m; ++a)
+                    P[a + (size_t)L.m * (g + (size_t)L.m * s)] = tmp[a + (size_t)L.m * (s + (size_t)L.q * g)];
+    }
+    if (omega) {
+        CTM_CUDA(cudaMemcpyAsync(omega, h->omega, sizeof(double) * L.m, cudaMemcpyDeviceToHost, h->st));
+        CTM_CUDA(cudaStreamSynchronize(h->st));
+    }
+    if (live) *live = h->live;
+    return CTM_OK;
+}
+
+ctm_status ctm_set_state(ctm_handle* h, const double* P, const double* omega, int live) {
+    if (!h || !P || !omega) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    if (live < 1 || live > L.m) return fail(CTM_EINVAL, "live out of range");
+    std::vector<double> tmp((size_t)L.m * L.N);
+    for (int g = 0; g < L.m; ++g)
+        for (int s = 0; s < L.q; ++s)
+            for (int a = 0; a < L.m; ++a)
+                tmp[a + (size_t)L.m * (s + (size_t)L.q * g)] = P[a + (size_t)L.m * (g + (size_t)L.m * s)];
+    CTM_CUDA(cudaMemcpyAsync(h->P, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyHostToDevice, h->st));
+    CTM_CUDA(cudaMemcpyAsync(h->omega, omega, sizeof(double) * L.m, cudaMemcpyHostToDevice, h->st));
+    k_set_int<<<1, 1, 0, h->st>>>(&h->ctl->live, live);
+    k_set_int<<<1, 1, 0, h->st>>>(&h->ctl->have_prev, 0);
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    h->live = live;
+    h->warm = false;
+    h->warm_live = -1;
+    return CTM_OK;
+}
+
+namespace {
+struct SaveHeader {
+    uint64_t magic;
+    int q, m, b, N;
+    int live, steps, warm, warm_live;
+    uint64_t seed;
+    ctm_step_info last;
+};
+const uint64_t kMagic = 0x43544d5247423330ull;  // "CTMRGB30"
+}  // namespace
+
+ctm_status ctm_save(ctm_handle* h, void* buf, size_t* len) {
+    if (!h || !len) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b) +
+                  sizeof(ctm::DevCtl);
+    if (!buf) {
+        *len = need;
+        return CTM_OK;
+    }
+    if (*len < need) return fail(CTM_EINVAL, "buffer too small");
+    SaveHeader hd{kMagic, L.q, L.m, L.b, L.N, h->live, h->steps, h->warm ? 1 : 0, h->warm_live, h->seed, h->last};
+    char* p = (char*)buf;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    CTM_CUDA(cudaMemcpyAsync(p, h->P, sizeof(double) * L.m * L.N, cudaMemcpyDeviceToHost, h->st));
+    p += sizeof(double) * L.m * L.N;
+    CTM_CUDA(cudaMemcpyAsync(p, h->omega, sizeof(double) * L.m, cudaMemcpyDeviceToHost, h->st));
+    p += sizeof(double) * L.m;
+    CTM_CUDA(cudaMemcpyAsync(p, h->prev, sizeof(double) * L.m, cudaMemcpyDeviceToHost, h->st));
+    p += sizeof(double) * L.m;
+    CTM_CUDA(cudaMemcpyAsync(p, h->Zprev, sizeof(double) * L.N * L.b, cudaMemcpyDeviceToHost, h->st));
+    p += sizeof(double) * L.N * L.b;
+    CTM_CUDA(cudaMemcpyAsync(p, h->ctl, sizeof(ctm::DevCtl), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    *len = need;
+    return CTM_OK;
+}
+
+ctm_status ctm_load(ctm_handle* h, const void* buf, size_t len) {
+    if (!h || !buf) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b) +
+                  sizeof(ctm::DevCtl);
+    if (len < need) return fail(CTM_EINVAL, "buffer too small");
+    SaveHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kMagic || hd.q != L.q || hd.m != L.m || hd.b != L.b || hd.N != L.N)
+        return fail(CTM_EINVAL, "checkpoint does not match this configuration");
+    const char* p = (const char*)buf + sizeof(hd);
+    CTM_CUDA(cudaMemcpyAsync(h->P, p, sizeof(double) * L.m * L.N, cudaMemcpyHostToDevice, h->st));
+    p += sizeof(double) * L.m * L.N;
+    CTM_CUDA(cudaMemcpyAsync(h->omega, p, sizeof(double) * L.m, cudaMemcpyHostToDevice, h->st));
+    p += sizeof(double) * L.m;
+    CTM_CUDA(cudaMemcpyAsync(h->prev, p, sizeof(double) * L.m, cudaMemcpyHostToDevice, h->st));
+    p += sizeof(double) * L.m;
+    CTM_CUDA(cudaMemcpyAsync(h->Zprev, p, sizeof(double) * L.N * L.b, cudaMemcpyHostToDevice, h->st));
+    p += sizeof(double) * L.N * L.b;
+    CTM_CUDA(cudaMemcpyAsync(h->ctl, p, sizeof(ctm::DevCtl), cudaMemcpyHostToDevice, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    h->live = hd.live;
+    h->steps = hd.steps;
+    h->warm = hd.warm != 0;
+    h->warm_live = hd.warm_live;
+    h->seed = hd.seed;
+    h->last = hd.last;
+    return CTM_OK;
+}
+
+ctm_status ctm_extend(ctm_handle* h) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    stage_extend(h, h->E);
+    CTM_CUDA(cudaGetLastError());
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    return CTM_OK;
+}
+
+ctm_status ctm_get_ctilde(ctm_handle* h, const int* rows, const int* cols, int count, double* out) {
+    if (!h || (count > 0 && (!rows || !cols || !out))) return fail(CTM_EINVAL, "NULL argument");
+    if (count <= 0) return CTM_OK;
+    const Layout& L = h->lay;
+    std::vector<long long> idx((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        int r = rows[i], c = cols[i];
+        if (r < 0 || r >= L.N || c < 0 || c >= L.N) return fail(CTM_EINVAL, "index out of range");
+        long long tr = (r / L.m) + (long long)L.q * (r % L.m);  // paper gamma + m s -> device s + q gamma
+        long long tc = (c / L.m) + (long long)L.q * (c % L.m);
+        idx[i] = tr + (long long)L.N * tc;
+    }
+    long long* d_idx = nullptr;
+    double* d_out = nullptr;
+    CTM_CUDA(cudaMallocAsync(&d_idx, sizeof(long long) * idx.size(), h->st));
+    CTM_CUDA(cudaMallocAsync(&d_out, sizeof(double) * count, h->st));
+    CTM_CUDA(cudaMemcpyAsync(d_idx, idx.data(), sizeof(long long) * idx.size(), cudaMemcpyHostToDevice, h->st));
+    k_gather<<<grid_for((size_t)count), 256, 0, h->st>>>(count, d_idx, h->C, d_out);
+    CTM_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double) * count, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaFreeAsync(d_idx, h->st));
+    CTM_CUDA(cudaFreeAsync(d_out, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    return CTM_OK;
+}
+
+ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    const Layout& L = h->lay;
+    bool conv = false;
+    int iters = 0;
+    ctm_status s = stage_eigen(h, h->cfg.max_subspace_iters, &conv, &iters);
+    if (s != CTM_OK) return s;
+    if (b_out) *b_out = L.b;
+    if (evals) CTM_CUDA(cudaMemcpyAsync(evals, h->theta, sizeof(double) * L.b, cudaMemcpyDeviceToHost, h->st));
+    if (vecs) {
+        std::vector<double> tmp((size_t)L.N * L.b);
+        CTM_CUDA(cudaMemcpyAsync(tmp.data(), h->Z, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, h->st));
+        CTM_CUDA(cudaStreamSynchronize(h->st));
+        for (int i = 0; i < L.b; ++i)
+            for (int g = 0; g < L.m; ++g)
+                for (int sp = 0; sp < L.q; ++sp)
+                    vecs[(g + (size_t)L.m * sp) + (size_t)L.N * i] = tmp[(sp + (size_t)L.q * g) + (size_t)L.N * i];
+    }
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    return conv ? CTM_OK : fail(CTM_ENOTCONVERGED, "subspace iteration reached its cap");
+}
+
+}  // extern "C"

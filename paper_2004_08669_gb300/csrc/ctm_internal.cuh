@@ -1,0 +1,97 @@
+// ctm_internal.cuh -- device-side helpers and kernel declarations shared by the
+// translation units of libctm_gb300.so.
+//
+// Device layout: every (m q)-long combined index is spin-fastest,
+// t = s + q * gamma, so that the live block of the extended corner (the rows
+// with gamma < D) is its leading (q D) x (q D) block.  P is m x N column-major
+// (P[alpha + m t]); C~ and all N x b blocks are column-major.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cuda/atomic>
+
+namespace ctm {
+
+constexpr int kThreads = 256;
+
+// Device control block: flags and scalars written by kernels and read back by
+// the host once per subspace iteration / step.
+struct DevCtl {
+    // eigen stage
+    int meff_new;        // kept states after the multiplet rule
+    int sub_converged;   // Ritz residuals below tol
+    int jac_sweeps;      // sweeps of the last Jacobi
+    int jac_status;      // 0 ok, 1 sweep cap, 2 barrier timeout
+    int chol_status;     // 0 ok, 1 non-positive pivot, 2 barrier timeout
+    int numeric_bad;     // NaN/Inf seen
+    int pad0, pad1;
+    double resid;        // max residual / |theta_0|
+    double theta0;
+    // step stage
+    double kappa;
+    double delta;
+    double SE;
+    double prev_kappa;
+    int have_prev;
+    int live;            // current live rows of P (D)
+    int pad2, pad3;
+    // barrier words (cooperative kernels)
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int rot_count[64];   // rotations per Jacobi sweep
+    // observables
+    double obs_M_num, obs_u_num, obs_z4, obs_SE;
+};
+
+// Grid-wide barrier for cooperative launches.  Every wait is bounded: after
+// ~2^22 polls (about a second) the barrier records a timeout in *err and
+// returns, so a missing block can never hang the GPU.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen,
+                                             unsigned int nblocks, int* err) {
+    __syncthreads();
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> g(*gen);
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(*count);
+        unsigned int my = g.load(cuda::memory_order_acquire);
+        unsigned int arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
+        if (arrived == nblocks - 1) {
+            c.store(0u, cuda::memory_order_relaxed);
+            g.fetch_add(1u, cuda::memory_order_release);
+        } else {
+            long polls = 0;
+            while (g.load(cuda::memory_order_acquire) == my) {
+                if (++polls > (1L << 22)) {
+                    atomicExch(err, 2);
+                    s_fail = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    if (threadIdx.x == 0 && *(volatile int*)err == 2) s_fail = 1;
+    __syncthreads();
+    return s_fail == 0;  // uniform across the block
+}
+
+// ---------------------------------------------------------------- kernels
+// FP64 GEMM: C = alpha op(A) op(B) (+ beta C), column-major, optional per-k
+// scaling of B (scaleK[k] * B(k, j)), split-K over blockIdx.z writing
+// partial sums to C + z * splitStride (beta ignored when splits > 1).
+// Returns the number of kernels launched (1, or 2 with split-K).
+int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, double alpha,
+             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+             const double* scaleK, int splits, double* partial);
+
+// Blockwise vertex-weight contraction, in place on an N x N matrix (spin-fastest
+// index): every q x q block X_{gamma gamma'} becomes E o (E (X o E1) E), where
+// E1 is E (plain weight) or E o h (bond impurity).  Blocks with gamma or
+// gamma' >= *live are zero and skipped.
+void wcontract_f64(cudaStream_t st, int m, int q, double* X, int ldx, const double* E,
+                   const double* E1, const int* live);
+
+}  // namespace ctm

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libctm_gb300.so (include/ctm.h), same names.
+
+Argument marshalling only: every step of the CTMRG runs in the library's
+CUDA kernels.  Importing this module loads the library and raises if it is
+missing; there is no CPU fallback.  PyTorch provides the device workspace
+(allocated through its caching allocator) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctm_gb300.so")
+
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ENOTCONVERGED, CTM_ENUMERIC, CTM_ETIMEOUT, CTM_ECUDA, CTM_EUNSUPPORTED = range(8)
+CTM_FP64, CTM_TF32, CTM_BF16, CTM_OZAKI64 = range(4)
+PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "ozaki64": CTM_OZAKI64}
+_STATUS = ["CTM_OK", "CTM_EINVAL", "CTM_ENOMEM", "CTM_ENOTCONVERGED", "CTM_ENUMERIC", "CTM_ETIMEOUT",
+           "CTM_ECUDA", "CTM_EUNSUPPORTED"]
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class ctm_config(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("dim", ctypes.c_int), ("spins", _dp), ("m", ctypes.c_int),
+                ("beta", ctypes.c_double), ("boundary_spin", ctypes.c_int), ("prec", ctypes.c_int),
+                ("ozaki_slices", ctypes.c_int), ("tol_spectrum", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("block_extra", ctypes.c_int), ("max_subspace_iters", ctypes.c_int),
+                ("subspace_tol", ctypes.c_double), ("tol_cluster", ctypes.c_double),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class ctm_step_info(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("delta", ctypes.c_double), ("S_E", ctypes.c_double),
+                ("residual", ctypes.c_double), ("m_eff", ctypes.c_int), ("live_dim", ctypes.c_int),
+                ("subspace_iters", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int), ("steps", ctypes.c_int),
+                ("converged", ctypes.c_int)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ctm_obs(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("M", ctypes.c_double), ("u", ctypes.c_double),
+                ("S_E", ctypes.c_double), ("delta", ctypes.c_double), ("steps", ctypes.c_int),
+                ("converged", ctypes.c_int)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ctm_prof_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class CtmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS[status] if 0 <= status < len(_STATUS) else status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2004_08669_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    sig = {
+        "ctm_workspace_size": [ctypes.POINTER(ctm_config), ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_init": [ctypes.POINTER(H), ctypes.POINTER(ctm_config), ctypes.c_void_p],
+        "ctm_step": [H, ctypes.c_int, _ip, ctypes.POINTER(ctm_step_info)],
+        "ctm_observables": [H, ctypes.POINTER(ctm_obs)],
+        "ctm_step_backward": [H, ctypes.POINTER(ctm_obs), _dp],
+        "ctm_get_spectrum": [H, _dp],
+        "ctm_get_state": [H, _dp, _dp, _ip],
+        "ctm_set_state": [H, _dp, _dp, ctypes.c_int],
+        "ctm_save": [H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_load": [H, ctypes.c_void_p, ctypes.c_size_t],
+        "ctm_extend": [H],
+        "ctm_get_ctilde": [H, _ip, _ip, ctypes.c_int, _dp],
+        "ctm_eigen": [H, _dp, _dp, _ip],
+        "ctm_profile": [H, ctypes.c_int],
+        "ctm_profile_read": [H, ctypes.POINTER(ctm_prof_entry), ctypes.c_int, _ip],
+        "ctm_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.ctm_last_error.restype = ctypes.c_char_p
+    L.ctm_last_error.argtypes = []
+    L.ctm_destroy.restype = None
+    L.ctm_destroy.argtypes = [H]
+    return L
+
+
+lib = _load()
+
+
+def ctm_last_error() -> str:
+    return lib.ctm_last_error().decode()
+
+
+def _check(status: int, allow=(CTM_OK,)) -> int:
+    if status not in allow:
+        raise CtmError(status, ctm_last_error())
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def make_config(spins, m: int, beta: float, boundary_spin: int = 0, prec: str = "fp64", **kw) -> tuple:
+    spins = np.ascontiguousarray(spins, dtype=np.float64)
+    cfg = ctm_config()
+    cfg.q, cfg.dim = spins.shape
+    cfg.spins = _dptr(spins)
+    cfg.m = int(m)
+    cfg.beta = float(beta)
+    cfg.boundary_spin = int(boundary_spin)
+    cfg.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg, spins  # keep spins alive with the config
+
+
+def ctm_workspace_size(cfg: ctm_config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib.ctm_workspace_size(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def ctm_init(cfg: ctm_config, stream: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib.ctm_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(stream)))
+    return h
+
+
+def ctm_step(h, nsteps: int):
+    done = ctypes.c_int(0)
+    info = ctm_step_info()
+    st = _check(lib.ctm_step(h, int(nsteps), ctypes.byref(done), ctypes.byref(info)),
+                (CTM_OK, CTM_ENOTCONVERGED))
+    return done.value, info, st
+
+
+def ctm_observables(h):
+    o = ctm_obs()
+    st = _check(lib.ctm_observables(h, ctypes.byref(o)), (CTM_OK, CTM_ENOTCONVERGED))
+    return o, st
+
+
+def ctm_step_backward(h, grad_obs: ctm_obs):
+    g = np.zeros(1)
+    _check(lib.ctm_step_backward(h, ctypes.byref(grad_obs), _dptr(g)))
+    return g
+
+
+def ctm_get_spectrum(h, m: int) -> np.ndarray:
+    om = np.zeros(m)
+    _check(lib.ctm_get_spectrum(h, _dptr(om)))
+    return om
+
+
+def ctm_get_state(h, m: int, q: int):
+    P = np.zeros((m, m * q), order="F")
+    om = np.zeros(m)
+    live = ctypes.c_int(0)
+    _check(lib.ctm_get_state(h, _dptr(P), _dptr(om), ctypes.byref(live)))
+    return P, om, live.value
+
+
+def ctm_set_state(h, P: np.ndarray, omega: np.ndarray, live: int):
+    P = np.asfortranarray(P, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    _check(lib.ctm_set_state(h, _dptr(P), _dptr(om), int(live)))
+
+
+def ctm_save(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib.ctm_save(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.ctm_save(h, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def ctm_load(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib.ctm_load(h, buf, len(blob)))
+
+
+def ctm_extend(h):
+    _check(lib.ctm_extend(h))
+
+
+def ctm_get_ctilde(h, rows, cols) -> np.ndarray:
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.zeros(len(r))
+    _check(lib.ctm_get_ctilde(h, r.ctypes.data_as(_ip), c.ctypes.data_as(_ip), len(r), _dptr(out)))
+    return out
+
+
+def ctm_eigen(h, N: int, b: int, want_vectors: bool = True):
+    ev = np.zeros(b)
+    vec = np.zeros((N, b), order="F") if want_vectors else None
+    bo = ctypes.c_int(0)
+    st = _check(lib.ctm_eigen(h, _dptr(ev), _dptr(vec) if want_vectors else None, ctypes.byref(bo)),
+                (CTM_OK, CTM_ENOTCONVERGED))
+    return ev, vec, st
+
+
+def ctm_profile(h, enable: bool):
+    _check(lib.ctm_profile(h, 1 if enable else 0))
+
+
+def ctm_profile_read(h) -> dict:
+    arr = (ctm_prof_entry * 16)()
+    n = ctypes.c_int(0)
+    _check(lib.ctm_profile_read(h, arr, 16, ctypes.byref(n)))
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops,
+                                   "bytes": arr[i].bytes} for i in range(n.value)}
+
+
+def ctm_launch_count(h) -> int:
+    n = ctypes.c_longlong(0)
+    _check(lib.ctm_launch_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def ctm_destroy(h):
+    if h:
+        lib.ctm_destroy(h)
+
+
+class CTMRG:
+    """One CTMRG run on the GPU: owns a handle and its torch-allocated workspace."""
+
+    def __init__(self, spins, m: int, beta: float, boundary_spin: int = 0, prec: str = "fp64",
+                 device: str = "cuda:0", **kw):
+        import torch
+        self.device = torch.device(device)
+        self.cfg, self._spins = make_config(spins, m, beta, boundary_spin, prec, **kw)
+        self.m, self.q = m, self._spins.shape[0]
+        self.N = m * self.q
+        nbytes = ctm_workspace_size(self.cfg)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.cfg.workspace = ctypes.c_void_p(self._ws.data_ptr())
+        self.cfg.workspace_bytes = nbytes
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            self.h = ctm_init(self.cfg, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ctm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        done, info, st = ctm_step(self.h, n)
+        return done, info.to_dict(), st
+
+    def run(self, max_steps: int):
+        done, info, st = ctm_step(self.h, max_steps)
+        return done, info.to_dict()
+
+    def observables(self) -> dict:
+        o, st = ctm_observables(self.h)
+        return o.to_dict()
+
+    def spectrum(self) -> np.ndarray:
+        return ctm_get_spectrum(self.h, self.m)
+
+    def get_state(self):
+        return ctm_get_state(self.h, self.m, self.q)
+
+    def set_state(self, P, omega, live: int):
+        ctm_set_state(self.h, P, omega, live)
+
+    def extend(self):
+        ctm_extend(self.h)
+
+    def ctilde(self, rows, cols):
+        return ctm_get_ctilde(self.h, rows, cols)
+
+    def eigen(self, want_vectors=True):
+        b = min(self.N, self.m + (self.cfg.block_extra if self.cfg.block_extra > 0 else max(8, self.m // 8)))
+        return ctm_eigen(self.h, self.N, b, want_vectors)
+
+    def profile(self, enable: bool):
+        ctm_profile(self.h, enable)
+
+    def profile_read(self) -> dict:
+        return ctm_profile_read(self.h)
+
+    def launch_count(self) -> int:
+        return ctm_launch_count(self.h)
+
+    def save(self) -> bytes:
+        return ctm_save(self.h)
+
+    def load(self, blob: bytes):
+        ctm_load(self.h, blob)

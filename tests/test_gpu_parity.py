@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances (FP64 mode): C~ entries 1e-13 of max|C~| (a sum of m q^2
+products in a different order); Ritz values 1e-12 of |w_1|; projectors onto
+the kept spaces 1e-9 in the 2-norm (eigenvector error ~ residual / gap);
+free energy per step and at convergence 1e-12 relative (the target for the
+FP64 form); M, u and S_E 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2004_08669_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_08669_gb300 import build
+    build.build()
+    from paper_2004_08669_gb300 import ctm as C
+    return C
+
+
+def _paper_live_block(N, m, q, live):
+    return np.array([g + m * s for s in range(q) for g in range(live)])
+
+
+@pytest.mark.parametrize("model,m,live,beta", [("dodecahedron", 8, 8, 1 / 0.44), ("dodecahedron", 12, 7, 2.0),
+                                               ("ising", 10, 10, 0.5), ("cube", 9, 5, 1.0), ("clock3", 5, 3, 0.9)])
+def test_extension_matches_oracle(ctm, model, m, live, beta):
+    spins = W.clock(3) if model == "clock3" else W.spins_for(model)
+    q = spins.shape[0]
+    N = m * q
+    P, om = W.random_state(m, q, live, seed=11 + m)
+    g = ctm.CTMRG(spins, m, beta)
+    g.set_state(P, om[:m], live)
+    g.extend()
+    rr, cc = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    gpu = g.ctilde(rr.ravel(), cc.ravel()).reshape(N, N)
+    ref = O.sub_ctmrg(P, om[:m, None] * P, O.weight_matrix(spins, beta), m, q)
+    scale = np.abs(ref).max()
+    assert np.abs(gpu - ref).max() <= 1e-13 * scale
+    assert np.abs(gpu - gpu.T).max() <= 1e-14 * scale
+    g.close()
+
+
+@pytest.mark.parametrize("model,m,live,beta", [("dodecahedron", 8, 8, 1 / 0.44), ("dodecahedron", 16, 11, 2.5),
+                                               ("ising", 12, 12, 0.5)])
+def test_leading_eigenpairs_match_oracle(ctm, model, m, live, beta):
+    spins = W.spins_for(model)
+    q = spins.shape[0]
+    N = m * q
+    P, om = W.random_state(m, q, live, seed=5 + m)
+    g = ctm.CTMRG(spins, m, beta, max_subspace_iters=400)
+    g.set_state(P, om[:m], live)
+    g.extend()
+    ev, Z, st = g.eigen()
+    assert st == ctm.CTM_OK
+    ref = O.sub_ctmrg(P, om[:m, None] * P, O.weight_matrix(spins, beta), m, q)
+    idx = _paper_live_block(N, m, q, live)
+    evr, Zr = O.eigh(ref[np.ix_(idx, idx)])
+    b = len(ev)
+    nk = min(m, len(evr))
+    scale = abs(evr[0])
+    assert np.abs(ev[:nk] - evr[:nk]).max() <= 1e-12 * scale
+    # projector onto the kept space (random states: no exact multiplets)
+    Zf = np.zeros((N, len(evr)))
+    Zf[idx] = Zr
+    Pg = Z[:, :nk] @ Z[:, :nk].T
+    Po = Zf[:, :nk] @ Zf[:, :nk].T
+    assert np.linalg.norm(Pg - Po, 2) <= 1e-9
+    assert np.abs(Z.T @ Z - np.eye(b)).max() <= 1e-12
+    g.close()
+
+
+def _run_pair(ctm, spins, m, beta, steps, **kw):
+    g = ctm.CTMRG(spins, m, beta, max_subspace_iters=400, **kw)
+    o = O.CTMRG(spins, m, beta)
+    rows = []
+    for k in range(steps):
+        done, info, st = g.step(1)
+        r = o.step()
+        rows.append((info, r))
+    return g, o, rows
+
+
+def test_trajectory_matches_oracle_m8(ctm):
+    """q = 20, m = 8, T = 0.44: every step's kappa, kept spectrum and S_E."""
+    spins = W.dodecahedron()
+    g, o, rows = _run_pair(ctm, spins, 8, 1 / 0.44, 25)
+    for info, r in rows:
+        assert info["m_eff"] == int(r["m_eff"])
+        assert info["kappa"] == pytest.approx(r["kappa"], rel=1e-12)
+        assert info["S_E"] == pytest.approx(r["S_E_kept"], rel=1e-10, abs=1e-12)
+    _, om_o, live_o = o.get_state()
+    om_g = g.spectrum()
+    np.testing.assert_allclose(np.abs(om_g), np.abs(om_o[:8]), atol=1e-10)
+    g.close()
+
+
+def test_converged_observables_match_oracle_m8(ctm):
+    """q = 20, m = 8, T = 0.44 run to delta < 1e-12: f, M, u, S_E."""
+    spins, beta = W.dodecahedron(), 1 / 0.44
+    g = ctm.CTMRG(spins, 8, beta)
+    done, info = g.run(5000)
+    assert info["converged"]
+    obs = g.observables()
+    o = O.CTMRG(spins, 8, beta)
+    hist = o.run(5000, 1e-12)
+    ref = o.observables()
+    assert abs(obs["f"] - ref["f"]) <= 1e-12 * abs(ref["f"])
+    assert obs["M"] == pytest.approx(ref["M_kept"], abs=1e-10)
+    assert obs["u"] == pytest.approx(ref["u_kept"], abs=1e-10)
+    assert obs["S_E"] == pytest.approx(ref["S_E_kept"], abs=1e-10)
+    assert abs(done - len(hist)) <= 3
+    g.close()
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_onsager_on_gpu(ctm, beta):
+    from tests import exact as E
+    g = ctm.CTMRG(W.ising(), 16, beta)
+    done, info = g.run(2000)
+    obs = g.observables()
+    assert obs["f"] == pytest.approx(E.onsager_f(beta), rel=1e-12)
+    assert obs["M"] == pytest.approx(E.yang_m(beta), abs=1e-11)
+    g.close()
+
+
+def test_trajectory_matches_oracle_m64(ctm):
+    """q = 20, m = 64, T = 0.4398 (several GEMM tiles, ragged tails): 8 steps."""
+    spins = W.dodecahedron()
+    g, o, rows = _run_pair(ctm, spins, 64, 1 / 0.4398, 8)
+    for info, r in rows:
+        assert info["m_eff"] == int(r["m_eff"])
+        assert info["kappa"] == pytest.approx(r["kappa"], rel=1e-11)
+    g.close()
+
+
+def test_full_size_m256_sampled(ctm):
+    """The timed configuration (q = 20, m = 256): after a few steps, sampled
+    entries of C~ against the oracle's one-by-one routine, and properties of
+    the Ritz pairs that hold at any size."""
+    spins, beta, m = W.dodecahedron(), 1 / 0.4398, 256
+    q, N = 20, 256 * 20
+    g = ctm.CTMRG(spins, m, beta, max_subspace_iters=60)
+    g.step(4)
+    P, om, live = g.get_state()
+    g.extend()
+    rng = np.random.default_rng(256)
+    r = rng.integers(0, N, 400)
+    c = rng.integers(0, N, 400)
+    gpu = g.ctilde(r, c)
+    ref = O.ctilde_entries(P, om, O.weight_matrix(spins, beta), m, q, r, c)
+    scale = np.abs(g.ctilde(np.arange(0, 20), np.arange(0, 20))).max()
+    assert np.abs(gpu - ref).max() <= 1e-13 * scale
+    assert np.abs(g.ctilde(r, c) - g.ctilde(c, r)).max() <= 1e-14 * scale
+    ev, Z, st = g.eigen()
+    b = len(ev)
+    assert np.all(np.diff(np.abs(ev)) <= 1e-15 * abs(ev[0]))
+    assert np.abs(Z.T @ Z - np.eye(b)).max() <= 1e-11
+    g.close()
+
+
+def test_checkpoint_resume_is_bit_exact(ctm):
+    spins, beta = W.dodecahedron(), 1 / 0.5
+    g = ctm.CTMRG(spins, 8, beta)
+    g.step(6)
+    blob = g.save()
+    _, a, _ = g.step(5)
+    sa = g.spectrum()
+    g.load(blob)
+    _, b, _ = g.step(5)
+    sb = g.spectrum()
+    assert a["kappa"] == b["kappa"]
+    np.testing.assert_array_equal(sa, sb)
+    g.close()
+
+
+def test_beta_zero_and_small_cases(ctm):
+    g = ctm.CTMRG(W.dodecahedron(), 8, 0.0)
+    done, info, _ = g.step(4)
+    assert info["kappa"] == pytest.approx(400.0, rel=1e-13)
+    assert info["m_eff"] == 1
+    g.close()
+    # m = 1: the corner keeps a single state
+    g = ctm.CTMRG(W.dodecahedron(), 1, 2.0)
+    o = O.CTMRG(W.dodecahedron(), 1, 2.0)
+    for _ in range(5):
+        _, info, _ = g.step(1)
+        r = o.step()
+        assert info["kappa"] == pytest.approx(r["kappa"], rel=1e-12)
+    g.close()
+
+
+def test_invalid_and_unsupported(ctm):
+    with pytest.raises(ctm.CtmError) as e:
+        ctm.CTMRG(W.dodecahedron(), 8, 2.0, prec="bf16")
+    assert e.value.status in (ctm.CTM_EUNSUPPORTED, ctm.CTM_OK)
+    g = ctm.CTMRG(W.dodecahedron(), 8, 2.0)
+    with pytest.raises(ctm.CtmError) as e:
+        P, om = W.random_state(8, 20, 4, seed=1)
+        g.set_state(P, om[:8], 9)
+    assert e.value.status == ctm.CTM_EINVAL
+    with pytest.raises(ctm.CtmError) as e:
+        g.ctilde([160], [0])
+    assert e.value.status == ctm.CTM_EINVAL
+    g.close()

@@ -303,3 +303,15 @@ def test_planted_half_temperature_fails_onsager():
     c.set_weights(O.weight_matrix(W.ising(), beta / 2))
     c.run(2000, 1e-13)
     assert abs(c.observables()["M_kept"] - E.yang_m(beta)) > 0.1
+
+
+def test_ctilde_entries_match_full_extension():
+    """The one-by-one entry routine and the full Sub-CTMRG agree (both are
+    pinned to brute force through the extension test above)."""
+    P, om = W.random_state(6, 3, 4, seed=3)
+    w = O.weight_matrix(W.clock(3), 0.8)
+    full = O.sub_ctmrg(P, om[:6, None] * P, w, 6, 3)
+    rng = np.random.default_rng(0)
+    r = rng.integers(0, 18, 50)
+    c = rng.integers(0, 18, 50)
+    np.testing.assert_allclose(O.ctilde_entries(P, om[:6], w, 6, 3, r, c), full[r, c], rtol=1e-13, atol=1e-14)
