@@ -157,6 +157,35 @@ ctm_status ctm_get_ctilde(ctm_handle* h, const int* rows, const int* cols, int c
  * or NULL.  *b_out receives b. */
 ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out);
 
+/* Dense symmetric FP64 eigensolver on device memory: the cyclic Jacobi
+ * solver (round-robin parallel order) that the step uses for its
+ * Rayleigh-Ritz problem, exposed on its own.  A: n x n symmetric, device,
+ * column-major with leading dimension lda (only read; (A + A^t)/2 is
+ * diagonalised).  evals: device, n entries; vecs: device, n x n with
+ * leading dimension ldv; on return column i of vecs and evals[i] are the
+ * i-th eigenpair, sorted by |eigenvalue| descending (ties by index).
+ * workspace: device scratch of at least ctm_symeig_workspace_size(n) bytes,
+ * owned by the caller.  max_sweeps <= 0 selects 40 (cap 64).  Synchronises
+ * the stream.  Returns CTM_ENOTCONVERGED if the sweep cap was reached
+ * (the result is still written), CTM_ETIMEOUT if a device-side barrier
+ * gave up, CTM_EINVAL for n < 1, n > 4096 or a short workspace. */
+ctm_status ctm_symeig_workspace_size(int n, size_t* bytes);
+ctm_status ctm_symeig(int n, const double* A, int lda, double* evals, double* vecs, int ldv, int max_sweeps,
+                      void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* One contraction of the step's shape on device memory:
+ *   D (M x N) = A^t B,  A: K x M (lda), B: K x N (ldb), D: M x N (ldd),
+ * all column-major FP64 (both operands contiguous along K, as every GEMM of
+ * Algorithm 3 is here).  prec: CTM_FP64 runs the FP64 CUDA-core kernel;
+ * CTM_TF32 / CTM_BF16 round A and B to that type (nearest, ties away for
+ * TF32, ties to even for BF16) and run the tcgen05 tensor-core kernel with
+ * FP32 accumulation; D is written in FP64.  workspace: device scratch of at
+ * least ctm_contract_workspace_size(...) bytes, owned by the caller.
+ * Synchronises the stream; CTM_ETIMEOUT if a bounded device wait gave up. */
+ctm_status ctm_contract_workspace_size(ctm_precision prec, int M, int N, int K, size_t* bytes);
+ctm_status ctm_contract(ctm_precision prec, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                        double* D, int ldd, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
 /* Profiling.  While enabled, every kernel class of the step is bracketed by
  * CUDA events on the handle's stream; ctm_profile_read synchronises the
  * stream and returns, per class, the launches, the summed device time and

@@ -24,6 +24,7 @@
 #include "../../include/ctm.h"
 #include "ctm_internal.cuh"
 #include "eig_f64.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -712,6 +713,115 @@ ctm_status ctm_profile_read(ctm_handle* h, ctm_prof_entry* out, int max_entries,
     h->recs.clear();
     h->evnext = 0;
     h->launches_prof = 0;
+    return CTM_OK;
+}
+
+// ---- standalone dense symmetric eigensolver
+namespace {
+struct SymeigLayout {
+    size_t A0, A1, S, diag, rank, ctl, total;
+};
+SymeigLayout symeig_layout(int n) {
+    const size_t np = (size_t)(n + (n & 1) < 2 ? 2 : n + (n & 1));
+    SymeigLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align256(o + bytes);
+        return r;
+    };
+    L.A0 = take(np * np * sizeof(double));
+    L.A1 = take(np * np * sizeof(double));
+    L.S = take(np * np * sizeof(double));
+    L.diag = take(np * sizeof(double));
+    L.rank = take(np * sizeof(int));
+    L.ctl = take(sizeof(ctm::DevCtl));
+    L.total = o;
+    return L;
+}
+}  // namespace
+
+ctm_status ctm_symeig_workspace_size(int n, size_t* bytes) {
+    if (n < 1 || n > 4096 || !bytes) return fail(CTM_EINVAL, "n must be in [1, 4096] and bytes non-NULL");
+    *bytes = symeig_layout(n).total;
+    return CTM_OK;
+}
+
+ctm_status ctm_symeig(int n, const double* A, int lda, double* evals, double* vecs, int ldv, int max_sweeps,
+                      void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    if (n < 1 || n > 4096) return fail(CTM_EINVAL, "n must be in [1, 4096]");
+    if (!A || !evals || !vecs || !workspace) return fail(CTM_EINVAL, "NULL argument");
+    if (lda < n || ldv < n) return fail(CTM_EINVAL, "leading dimension smaller than n");
+    SymeigLayout L = symeig_layout(n);
+    if (workspace_bytes < L.total) return fail(CTM_EINVAL, "workspace too small");
+    if (max_sweeps <= 0) max_sweeps = 40;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    char* ws = (char*)workspace;
+    ctm::EigWork w{};
+    w.A0 = (double*)(ws + L.A0);
+    w.A1 = (double*)(ws + L.A1);
+    w.S = (double*)(ws + L.S);
+    w.diag = (double*)(ws + L.diag);
+    w.rank = (int*)(ws + L.rank);
+    ctm::DevCtl* ctl = (ctm::DevCtl*)(ws + L.ctl);
+    CTM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(ctm::DevCtl), st));
+    CTM_CUDA(ctm::jacobi_f64(st, n, A, lda, w, evals, vecs, ldv, max_sweeps, ctl));
+    int jst = 0;
+    CTM_CUDA(cudaMemcpyAsync(&jst, &ctl->jac_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    if (jst == 2) return fail(CTM_ETIMEOUT, "a device-side barrier of the Jacobi solver gave up");
+    if (jst == 1) return fail(CTM_ENOTCONVERGED, "Jacobi reached its sweep cap");
+    return CTM_OK;
+}
+
+// ---- one contraction in a chosen precision
+namespace {
+size_t contract_ws(ctm_precision prec, int M, int N, int K) {
+    if (prec == CTM_FP64) return 256;
+    size_t esz = (prec == CTM_BF16) ? 2 : 4;
+    size_t ld = (size_t)ctm::tc_ld(K);
+    return align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz) + 256;
+}
+}  // namespace
+
+ctm_status ctm_contract_workspace_size(ctm_precision prec, int M, int N, int K, size_t* bytes) {
+    if (!bytes || M < 1 || N < 1 || K < 1) return fail(CTM_EINVAL, "bad sizes");
+    if (prec != CTM_FP64 && prec != CTM_TF32 && prec != CTM_BF16)
+        return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
+    *bytes = contract_ws(prec, M, N, K);
+    return CTM_OK;
+}
+
+ctm_status ctm_contract(ctm_precision prec, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                        double* D, int ldd, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    if (M < 1 || N < 1 || K < 1) return fail(CTM_EINVAL, "bad sizes");
+    if (!A || !B || !D || !workspace) return fail(CTM_EINVAL, "NULL argument");
+    if (lda < K || ldb < K || ldd < M) return fail(CTM_EINVAL, "leading dimension too small");
+    if (prec != CTM_FP64 && prec != CTM_TF32 && prec != CTM_BF16)
+        return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
+    if (workspace_bytes < contract_ws(prec, M, N, K)) return fail(CTM_EINVAL, "workspace too small");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    char* ws = (char*)workspace;
+    if (prec == CTM_FP64) {
+        ctm::gemm_f64(st, true, false, M, N, K, 1.0, A, lda, B, ldb, 0.0, D, ldd, nullptr, 1, nullptr);
+        CTM_CUDA(cudaGetLastError());
+        CTM_CUDA(cudaStreamSynchronize(st));
+        return CTM_OK;
+    }
+    const bool bf16 = prec == CTM_BF16;
+    const size_t esz = bf16 ? 2 : 4;
+    const int ld = ctm::tc_ld(K);
+    void* Aop = ws;
+    void* Bop = ws + align256((size_t)M * ld * esz);
+    int* err = (int*)(ws + align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz));
+    CTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    ctm::to_operand(st, bf16, M, K, A, lda, nullptr, Aop, ld);
+    ctm::to_operand(st, bf16, N, K, B, ldb, nullptr, Bop, ld);
+    CTM_CUDA(ctm::tc_gemm(st, bf16, M, N, K, 1.0, Aop, ld, Bop, ld, 0.0, D, ldd, err));
+    int herr = 0;
+    CTM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
     return CTM_OK;
 }
 

@@ -1,0 +1,24 @@
+// tc_gemm.cuh -- host entry points of the tcgen05 GEMM (tc_gemm.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ctm {
+
+// Leading dimension (elements) of a K-major operand copy: K rounded up to 64.
+int tc_ld(int K);
+
+// Copy rows of a column-major FP64 matrix into a K-major operand (bf16 or
+// fp32): dst[r * ldo + k] = src[k + lds * r] * (scale ? scale[k] : 1), zero
+// for K <= k < ldo.
+void to_operand(cudaStream_t st, bool bf16, int R, int K, const double* src, int lds, const double* scale,
+                void* dst, int ldo);
+
+// D (M x N, column-major FP64, ldd) = alpha * A . B^t + beta * D with A (M x K)
+// and B (N x K) K-major operands of leading dimension lda, ldb (multiples of
+// 64).  bf16: kind::f16 with bf16 operands; else kind::tf32 on fp32 storage.
+// *err (device int) is set to 1 if a bounded wait gave up.
+cudaError_t tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, double alpha, const void* A, int lda,
+                    const void* B, int ldb, double beta, double* D, int ldd, int* err);
+
+}  // namespace ctm

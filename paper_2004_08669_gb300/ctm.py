@@ -86,6 +86,14 @@ def _load():
         "ctm_profile": [H, ctypes.c_int],
         "ctm_profile_read": [H, ctypes.POINTER(ctm_prof_entry), ctypes.c_int, _ip],
         "ctm_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
+        "ctm_symeig_workspace_size": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_contract_workspace_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_contract": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                         ctypes.c_size_t, ctypes.c_void_p],
+        "ctm_symeig": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                       ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -231,6 +239,48 @@ def ctm_launch_count(h) -> int:
     n = ctypes.c_longlong(0)
     _check(lib.ctm_launch_count(h, ctypes.byref(n)))
     return n.value
+
+
+def ctm_symeig_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib.ctm_symeig_workspace_size(int(n), ctypes.byref(b)))
+    return b.value
+
+
+def ctm_symeig(A, max_sweeps: int = 0):
+    """Eigenpairs of a symmetric FP64 torch CUDA tensor A (n x n) with the
+    library's Jacobi solver; the workspace comes from torch.  Returns
+    (evals, vecs, status) as torch tensors, sorted by |eigenvalue| desc."""
+    import torch
+    n = A.shape[0]
+    Ac = A.t().contiguous()  # column-major storage of A
+    ev = torch.empty(n, dtype=torch.float64, device=A.device)
+    vt = torch.empty(n, n, dtype=torch.float64, device=A.device)  # rows of vt = columns of vecs
+    ws = torch.empty(ctm_symeig_workspace_size(n), dtype=torch.uint8, device=A.device)
+    st = torch.cuda.current_stream(A.device).cuda_stream
+    status = _check(lib.ctm_symeig(n, Ac.data_ptr(), n, ev.data_ptr(), vt.data_ptr(), n, int(max_sweeps),
+                                   ws.data_ptr(), ws.numel(), ctypes.c_void_p(st)), (CTM_OK, CTM_ENOTCONVERGED))
+    return ev, vt.t(), status
+
+
+def ctm_contract(A, B, prec: str = "fp64"):
+    """D = A^t B for FP64 torch CUDA tensors A (K x M) and B (K x N) through
+    the library's contraction kernel in the given precision."""
+    import torch
+    K, M = A.shape
+    K2, N = B.shape
+    assert K == K2
+    p = PRECISIONS[prec]
+    Ac = A.t().contiguous()  # column-major K x M
+    Bc = B.t().contiguous()
+    Dt = torch.empty(N, M, dtype=torch.float64, device=A.device)  # column-major M x N
+    nb = ctypes.c_size_t(0)
+    _check(lib.ctm_contract_workspace_size(p, M, N, K, ctypes.byref(nb)))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=A.device)
+    st = torch.cuda.current_stream(A.device).cuda_stream
+    _check(lib.ctm_contract(p, M, N, K, Ac.data_ptr(), K, Bc.data_ptr(), K, Dt.data_ptr(), M, ws.data_ptr(),
+                            ws.numel(), ctypes.c_void_p(st)))
+    return Dt.t()
 
 
 def ctm_destroy(h):

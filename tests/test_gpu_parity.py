@@ -211,3 +211,21 @@ def test_invalid_and_unsupported(ctm):
         g.ctilde([160], [0])
     assert e.value.status == ctm.CTM_EINVAL
     g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 301])
+def test_symeig_matches_lapack(ctm, n):
+    """The standalone Jacobi solver against numpy's LAPACK eigh."""
+    import torch
+    rng = np.random.default_rng(100 + n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    ev, vec, st = ctm.ctm_symeig(torch.tensor(A, device="cuda:0"))
+    assert st == ctm.CTM_OK
+    ev, vec = ev.cpu().numpy(), vec.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(np.sort(ev), np.sort(ref), atol=1e-13 * n * scale)
+    assert np.all(np.diff(np.abs(ev)) <= 0)
+    assert np.abs(A @ vec - vec * ev).max() <= 1e-13 * n * scale
+    assert np.abs(vec.T @ vec - np.eye(n)).max() <= 1e-13 * n
