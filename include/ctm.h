@@ -173,6 +173,28 @@ ctm_status ctm_symeig_workspace_size(int n, size_t* bytes);
 ctm_status ctm_symeig(int n, const double* A, int lda, double* evals, double* vecs, int ldv, int max_sweeps,
                       void* workspace, size_t workspace_bytes, void* cuda_stream);
 
+/* No-allocation variant of ctm_symeig.  The paper has no counterpart; this
+ * exists for callers that cannot allocate device memory themselves -- code
+ * running inside a fixed memory pool that must not grow, or a host program
+ * that only holds device pointers handed to it by another framework.  The
+ * caller still passes A, evals and vecs (device, same layout and results as
+ * ctm_symeig); the solver's scratch is a file-scope device array of
+ * CTM_SYMEIG_NOALLOC_MAX_N-sized buffers (about 6.3 MB), which every GPU that
+ * loads this library keeps reserved until the process exits.  No call
+ * allocates or frees anything.
+ *  - n > CTM_SYMEIG_NOALLOC_MAX_N (or n < 1) returns CTM_EINVAL with a message.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and each call clears the parts that must
+ *    start at zero.  Calls whose work overlaps on the GPU (concurrent streams
+ *    or host threads) race on the array and give wrong results: serialise
+ *    them.
+ *  - Synchronises the stream; statuses as for ctm_symeig. */
+#define CTM_SYMEIG_NOALLOC_MAX_N 512
+ctm_status ctm_symeig_noalloc(int n, const double* A, int lda, double* evals, double* vecs, int ldv, int max_sweeps,
+                              void* cuda_stream);
+
 /* One contraction of the step's shape on device memory:
  *   D (M x N) = A^t B,  A: K x M (lda), B: K x N (ldb), D: M x N (ldd),
  * all column-major FP64 (both operands contiguous along K, as every GEMM of

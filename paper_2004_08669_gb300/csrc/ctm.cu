@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1065,3 +1066,79 @@ ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out) {
 }
 
 }  // extern "C"
+
+// ================================================================ no-allocation variant
+// ctm_symeig_noalloc: the same Jacobi solver as ctm_symeig for callers that
+// cannot allocate device memory themselves -- for example code running inside
+// a memory pool that must not grow, or a host process that only receives
+// device pointers from another framework and has no allocator of its own.
+// Its scratch is a file-scope device array (every GPU that loads this library
+// reserves it until the process exits), so nothing is allocated per call.
+namespace {
+constexpr int kNoAllocMaxN = CTM_SYMEIG_NOALLOC_MAX_N;
+constexpr size_t kNoAllocPad = (size_t)kNoAllocMaxN + (kNoAllocMaxN & 1);
+constexpr size_t kNoAllocBytes = 3 * ((kNoAllocPad * kNoAllocPad * sizeof(double) + 255) / 256 * 256) +
+                                 (kNoAllocPad * sizeof(double) + 255) / 256 * 256 +
+                                 (kNoAllocPad * sizeof(int) + 255) / 256 * 256 +
+                                 (sizeof(ctm::DevCtl) + 255) / 256 * 256;
+__device__ __align__(256) unsigned char g_symeig_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" ctm_status ctm_symeig_noalloc(int n, const double* A, int lda, double* evals, double* vecs, int ldv,
+                                         int max_sweeps, void* cuda_stream) {
+    if (n < 1 || n > kNoAllocMaxN)
+        return fail(CTM_EINVAL, "ctm_symeig_noalloc: n must be in [1, CTM_SYMEIG_NOALLOC_MAX_N = " +
+                                    std::to_string(kNoAllocMaxN) + "]");
+    if (!A || !evals || !vecs) return fail(CTM_EINVAL, "NULL argument");
+    if (lda < n || ldv < n) return fail(CTM_EINVAL, "leading dimension smaller than n");
+    if (max_sweeps <= 0) max_sweeps = 40;
+    int dev = 0;
+    CTM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(CTM_EINVAL, "device index out of range");
+    void* base = nullptr;
+    {
+        // One-time set-up per device (with that device current): the host-side
+        // name of the array is not a device address, so ask the runtime for it.
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_symeig_scratch);
+            if (e != cudaSuccess)
+                return fail(CTM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_scratch_ptr[dev] = p;
+        }
+        base = g_scratch_ptr[dev];
+    }
+    // Carve the scratch exactly as the workspace of ctm_symeig is carved.
+    const size_t np = (size_t)(n + (n & 1) < 2 ? 2 : n + (n & 1));
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align256(o + bytes);
+        return r;
+    };
+    char* ws = (char*)base;
+    ctm::EigWork w{};
+    w.A0 = (double*)(ws + take(np * np * sizeof(double)));
+    w.A1 = (double*)(ws + take(np * np * sizeof(double)));
+    w.S = (double*)(ws + take(np * np * sizeof(double)));
+    w.diag = (double*)(ws + take(np * sizeof(double)));
+    w.rank = (int*)(ws + take(np * sizeof(int)));
+    ctm::DevCtl* ctl = (ctm::DevCtl*)(ws + take(sizeof(ctm::DevCtl)));
+    if (o > kNoAllocBytes) return fail(CTM_EINVAL, "ctm_symeig_noalloc: scratch layout exceeds its array");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The array keeps the previous call's contents: the control block (barrier
+    // words, counters, status) must start at zero.
+    CTM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(ctm::DevCtl), st));
+    CTM_CUDA(ctm::jacobi_f64(st, n, A, lda, w, evals, vecs, ldv, max_sweeps, ctl));
+    int jst = 0;
+    CTM_CUDA(cudaMemcpyAsync(&jst, &ctl->jac_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    if (jst == 2) return fail(CTM_ETIMEOUT, "a device-side barrier of the Jacobi solver gave up");
+    if (jst == 1) return fail(CTM_ENOTCONVERGED, "Jacobi reached its sweep cap");
+    return CTM_OK;
+}

@@ -87,6 +87,8 @@ def _load():
         "ctm_profile_read": [H, ctypes.POINTER(ctm_prof_entry), ctypes.c_int, _ip],
         "ctm_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
         "ctm_symeig_workspace_size": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_symeig_noalloc": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
         "ctm_contract_workspace_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_size_t)],
         "ctm_contract": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -260,6 +262,22 @@ def ctm_symeig(A, max_sweeps: int = 0):
     st = torch.cuda.current_stream(A.device).cuda_stream
     status = _check(lib.ctm_symeig(n, Ac.data_ptr(), n, ev.data_ptr(), vt.data_ptr(), n, int(max_sweeps),
                                    ws.data_ptr(), ws.numel(), ctypes.c_void_p(st)), (CTM_OK, CTM_ENOTCONVERGED))
+    return ev, vt.t(), status
+
+
+def ctm_symeig_noalloc(A, max_sweeps: int = 0):
+    """ctm_symeig through the no-allocation entry point: the library's
+    scratch is its own static device array; the caller passes A (torch FP64
+    CUDA tensor, n <= CTM_SYMEIG_NOALLOC_MAX_N) and receives the outputs in
+    tensors allocated here."""
+    import torch
+    n = A.shape[0]
+    Ac = A.t().contiguous()
+    ev = torch.empty(n, dtype=torch.float64, device=A.device)
+    vt = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    st = torch.cuda.current_stream(A.device).cuda_stream
+    status = _check(lib.ctm_symeig_noalloc(n, Ac.data_ptr(), n, ev.data_ptr(), vt.data_ptr(), n, int(max_sweeps),
+                                           ctypes.c_void_p(st)), (CTM_OK, CTM_ENOTCONVERGED))
     return ev, vt.t(), status
 
 
