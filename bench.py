@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64")
+    ap.add_argument("--modes", default="fp64,tf32,bf16",
+                    help="precision forms to time; the first one gives the headline value")
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--T", type=float, default=0.4398)
     ap.add_argument("--prep", type=int, default=12, help="untimed steps before warm-up (cold start)")
@@ -190,6 +191,97 @@ def cpu_baseline(g, args):
                       f"{el:.1f} s"}
 
 
+def tensor_peak(prec: str):
+    """Dense tensor peak for the operand type: MEASURED_PEAKS.json when the
+    driver wrote it (bf16 burst), else the profiling recipe's fallback
+    1.9 PFLOP/s; TF32 scaled by the nominal ratio 1.1 / 2.25."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    src = "fallback"
+    bf16 = 1900.0
+    try:
+        d = json.load(open(path))
+        for k in ("bf16_tflops", "bf16_dense_tflops"):
+            if k in d:
+                bf16 = float(d[k])
+                src = "measured"
+                break
+    except Exception:
+        pass
+    if prec == "tf32":
+        return bf16 * 1.1 / 2.25, f"{src} bf16 x nominal tf32/bf16 ratio 1.1/2.25"
+    return bf16, f"{src} bf16"
+
+
+def run_mode(args, prec, local, world, barrier, timed_steps):
+    import numpy as np
+    import torch
+
+    from paper_2004_08669_gb300 import ctm, workloads as W
+    m = args.m
+    beta = 1.0 / args.T
+    g = ctm.CTMRG(W.dodecahedron(), m, beta, prec=prec, device=f"cuda:{local}",
+                  max_subspace_iters=args.subspace_iters)
+    stream = g.stream
+    g.step(args.prep)
+    for _ in range(max(args.warmup, 0)):
+        g.step(1)
+    launches0 = g.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    g.profile(True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    iters, sweeps = [], []
+    rr0 = None
+    for _ in range(timed_steps):
+        done, info, st = g.step(1)
+        if rr0 is None:
+            rr0 = (info["rr_refined"], info["rr_jacobi"])
+        iters.append(info["subspace_iters"])
+        sweeps.append(info["jacobi_sweeps"])
+    rr_paths = {"refined": info["rr_refined"] - rr0[0], "jacobi": info["rr_jacobi"] - rr0[1]}
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    launches = g.launch_count() - launches0
+    ms_t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    kern = {k: v for k, v in prof.items() if k != "all" and v["ms"] > 0}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    # roofline of the contraction kernel of this mode (the dominant one in the
+    # FP64 form): algorithmic FLOPs of its launches / their event-timed duration
+    ck = "gemm_f64" if prec == "fp64" else "tc_gemm"
+    d = kern[ck]
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    workload = f"dodecahedron q=20 m={m} T={args.T} {prec}"
+    if prec == "fp64":
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+        roof = {"kernel": ck, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(ck, workload),
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock"}
+    else:
+        peak, src = tensor_peak(prec)
+        roof = {"kernel": ck, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(ck, workload), "peak_source": src}
+    roof.update({"share_of_step": d["ms"] / ms, "launches": d["launches"], "dominant_kernel": dom})
+    res = {"prec": prec, "value": world * timed_steps / (ms_max / 1e3), "ms_per_step": ms_max / timed_steps,
+           "roofline": roof, "gpu_launches": launches, "clocks": clk,
+           "subspace_iters_mean": float(np.mean(iters)), "jacobi_sweeps_mean": float(np.mean(sweeps)),
+           "rayleigh_ritz_paths": rr_paths,
+           "kernels_ms_per_step": {k: round(v["ms"] / timed_steps, 3) for k, v in kern.items()},
+           "workload": workload}
+    return g, res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -204,17 +296,7 @@ def run_ours(args):
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    from paper_2004_08669_gb300 import ctm, workloads as W
-
-    m, q = args.m, 20
-    beta = 1.0 / args.T
-    g = ctm.CTMRG(W.dodecahedron(), m, beta, prec=args.prec, device=f"cuda:{local}",
-                  max_subspace_iters=args.subspace_iters)
-    stream = g.stream
-    g.step(args.prep)
-    for _ in range(max(args.warmup, 0)):
-        g.step(1)
-    launches0 = g.launch_count()
+    from paper_2004_08669_gb300 import ctm
 
     def barrier():
         torch.cuda.synchronize()
@@ -222,30 +304,10 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    g.profile(True)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
-    e0.record(stream)
-    iters = []
-    for _ in range(args.steps):
-        done, info, st = g.step(1)
-        iters.append(info["subspace_iters"])
-    e1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = g.profile_read()
-    launches = g.launch_count() - launches0
-    ms_t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    modes = [p.strip() for p in args.modes.split(",") if p.strip()]
+    primary = modes[0]
+    g, res = run_mode(args, primary, local, world, barrier, args.steps)
+    m = args.m
 
     # end to end through the C-ABI with host buffers: per step load the state
     # from pinned host memory, step, read the spectrum back to the host.
@@ -264,35 +326,35 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(blob),
            "d2h_bytes_per_step": 8 * m}
-
-    # roofline of the dominant kernel class, timed live with events on the
-    # library's stream over the timed region
-    kern = {k: v for k, v in prof.items() if k != "all" and v["ms"] > 0}
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    d = kern[dom]
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak_fp64 = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-    workload = f"dodecahedron q=20 m={m} T={args.T} {args.prec}"
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": traffic_for(dom, workload),
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock",
-            "share_of_step": d["ms"] / ms, "launches": d["launches"]}
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
-           "config": {"workload": workload, "q": q, "m": m, "T": args.T, "prec": args.prec,
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, args)
+    g.close()
+    others = {}
+    for p in modes[1:]:
+        g2, r2 = run_mode(args, p, local, world, barrier, args.steps)
+        g2.close()
+        others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "gpu_launches", "subspace_iters_mean",
+                                        "jacobi_sweeps_mean", "rayleigh_ritz_paths", "kernels_ms_per_step",
+                                        "clocks")}
+    out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if primary == "fp64" else primary, "data": "synthetic",
+           "config": {"workload": res["workload"], "q": 20, "m": m, "T": args.T, "prec": primary,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (C~ is 210 MB FP64), no flush",
                       "subspace_iters_cap": args.subspace_iters,
-                      "subspace_iters_mean": float(np.mean(iters)), "prep_steps": args.prep},
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-           "kernels_ms": {k: round(v["ms"], 3) for k, v in kern.items()}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(g, args)
+                      "subspace_iters_mean": res["subspace_iters_mean"],
+                      "jacobi_sweeps_mean": res["jacobi_sweeps_mean"],
+                      "rayleigh_ritz_paths": res["rayleigh_ritz_paths"], "prep_steps": args.prep},
+           "roofline": res["roofline"], "e2e": e2e, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
+           "kernels_ms_per_step": res["kernels_ms_per_step"]}
+    if others:
+        out["other_modes"] = others
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out), flush=True)
-    g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

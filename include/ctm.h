@@ -87,9 +87,11 @@ typedef struct {
     int m_eff;             /* states kept after the multiplet rule             */
     int live_dim;          /* live dimension of C~ this step                   */
     int subspace_iters;    /* subspace iterations used                          */
-    int jacobi_sweeps;     /* Jacobi sweeps of the last Rayleigh-Ritz          */
+    int jacobi_sweeps;     /* sweeps of the last cooperative Jacobi solve      */
     int steps;             /* CTMRG steps done by this handle                   */
     int converged;         /* delta < tol_spectrum                              */
+    long long rr_refined;  /* Rayleigh-Ritz solves by simultaneous rotations   */
+    long long rr_jacobi;   /* Rayleigh-Ritz solves by the cooperative Jacobi   */
 } ctm_step_info;
 
 /* Observables of the current state (Eq. 4-6 and the free energy). */
@@ -198,15 +200,23 @@ ctm_status ctm_symeig_noalloc(int n, const double* A, int lda, double* evals, do
 /* One contraction of the step's shape on device memory:
  *   D (M x N) = A^t B,  A: K x M (lda), B: K x N (ldb), D: M x N (ldd),
  * all column-major FP64 (both operands contiguous along K, as every GEMM of
- * Algorithm 3 is here).  prec: CTM_FP64 runs the FP64 CUDA-core kernel;
- * CTM_TF32 / CTM_BF16 round A and B to that type (nearest, ties away for
- * TF32, ties to even for BF16) and run the tcgen05 tensor-core kernel with
- * FP32 accumulation; D is written in FP64.  workspace: device scratch of at
- * least ctm_contract_workspace_size(...) bytes, owned by the caller.
- * Synchronises the stream; CTM_ETIMEOUT if a bounded device wait gave up. */
-ctm_status ctm_contract_workspace_size(ctm_precision prec, int M, int N, int K, size_t* bytes);
-ctm_status ctm_contract(ctm_precision prec, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                        double* D, int ldd, void* workspace, size_t workspace_bytes, void* cuda_stream);
+ * Algorithm 3 is here).  prec selects the arithmetic:
+ *   CTM_FP64     the FP64 CUDA-core kernel;
+ *   CTM_TF32 /   A and B rounded to that type (nearest, ties away for TF32,
+ *   CTM_BF16     ties to even for BF16), tcgen05 tensor cores, FP32 accumulation;
+ *   CTM_OZAKI64  FP64 emulated on the bf16 tensor cores: every row of A and
+ *                of B is split into ozaki_slices (3..7; 0 selects 6) exact
+ *                7-bit digit planes; the digit products with i + j <= s + 1
+ *                are accumulated exactly over K-chunks of 512 and combined in
+ *                double-float; the error is below about 2^(-7s) K max|A_row|
+ *                max|B_row| per element.
+ * D is written in FP64.  workspace: device scratch of at least
+ * ctm_contract_workspace_size(...) bytes, owned by the caller.  Synchronises
+ * the stream; CTM_ETIMEOUT if a bounded device-side wait gave up. */
+ctm_status ctm_contract_workspace_size(ctm_precision prec, int ozaki_slices, int M, int N, int K, size_t* bytes);
+ctm_status ctm_contract(ctm_precision prec, int ozaki_slices, int M, int N, int K, const double* A, int lda,
+                        const double* B, int ldb, double* D, int ldd, void* workspace, size_t workspace_bytes,
+                        void* cuda_stream);
 
 /* Profiling.  While enabled, every kernel class of the step is bracketed by
  * CUDA events on the handle's stream; ctm_profile_read synchronises the

@@ -25,6 +25,7 @@
 #include "../../include/ctm.h"
 #include "ctm_internal.cuh"
 #include "eig_f64.cuh"
+#include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -50,7 +51,13 @@ struct Layout {
     size_t off_spins, off_E, off_Eh, off_mag, off_P, off_Pn, off_omega, off_prev, off_C, off_V, off_Y,
         off_Z, off_T, off_Zprev, off_U, off_Up, off_H, off_Sb, off_G, off_Linv, off_theta, off_res,
         off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
-        off_mfull, off_colv, total;
+        off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
+        off_ozSA, off_ozSB, off_ozeP, off_ozeBig, off_ozeSA, off_ozeSB, off_oaX, off_oaW1, off_oaS, off_oaR, off_oaE,
+        off_oapart, total;
+    int slices;     // digit planes of the FP64-emulating form
+    int prec;       // ctm_precision
+    int esz;        // operand element bytes (2 bf16, 4 tf32; 0 in FP64 form)
+    int ldm, ldN;   // operand leading dimensions for K = m and K = N
 };
 
 Layout make_layout(const ctm_config& c) {
@@ -107,6 +114,43 @@ Layout make_layout(const ctm_config& c) {
     L.off_ctl = take(sizeof(ctm::DevCtl));
     L.off_mfull = take(sizeof(int));
     L.off_colv = take(2 * np * d);
+    L.off_oaX = take(b * b * d);
+    L.off_oaW1 = take(b * b * d);
+    L.off_oaS = take(b * b * d);
+    L.off_oaR = take(b * b * d);
+    L.off_oaE = take(b * b * d);
+    L.off_oapart = take(1024 * d);
+    L.prec = c.prec;
+    L.slices = c.ozaki_slices > 0 ? c.ozaki_slices : 6;
+    L.esz = (c.prec == CTM_BF16) ? 2 : (c.prec == CTM_TF32 ? 4 : 0);
+    L.ldm = ((L.m + 63) / 64) * 64;
+    L.ldN = ((L.N + 63) / 64) * 64;
+    if (L.esz) {
+        const size_t e = L.esz;
+        L.off_opP = take(N * L.ldm * e);
+        L.off_opPw = take(N * L.ldm * e);
+        L.off_opC = take(N * L.ldN * e);
+        L.off_opV = take(b * L.ldN * e);
+        L.off_opUp = take(N * L.ldm * e);
+        L.off_opU = take(m * L.ldN * e);
+        L.off_tcerr = take(sizeof(int));
+    }
+    if (c.prec == CTM_OZAKI64) {
+        // digit-plane slots: P (A role, kept from the extension to the P
+        // update), BIG (C~ or X, N x N), SA / SB (the small operands)
+        const int S = L.slices, Ni = L.N, bi = L.b, mi = L.m;
+        auto opA = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, true); };
+        auto opB = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, false); };
+        L.off_ozP = take(opA(Ni, mi));
+        L.off_ozBig = take(std::max(opA(Ni, Ni), opB(Ni, Ni)));
+        L.off_ozSA = take(std::max({opA(Ni, bi), opA(bi, Ni), opA(mi, Ni)}));
+        L.off_ozSB = take(std::max({opB(Ni, mi), opB(bi, Ni), opB(bi, bi)}));
+        L.off_ozeP = take(N * sizeof(int));
+        L.off_ozeBig = take(N * sizeof(int));
+        L.off_ozeSA = take(N * sizeof(int));
+        L.off_ozeSB = take(N * sizeof(int));
+        L.off_tcerr = take(sizeof(int));
+    }
     L.total = o;
     return L;
 }
@@ -123,7 +167,13 @@ struct ctm_handle {
     double *spins, *E, *Eh, *mag, *P, *Pn, *omega, *prev, *C, *V, *Y, *Z, *T, *Zprev, *U, *Up, *H, *Sb, *G,
         *Linv, *theta, *res, *part, *red, *colv;
     int* mfull;
+    void *opP = nullptr, *opPw = nullptr, *opC = nullptr, *opV = nullptr, *opUp = nullptr, *opU = nullptr;
+    int* tcerr = nullptr;
+    void *ozP = nullptr, *ozBig = nullptr, *ozSA = nullptr, *ozSB = nullptr;
+    int *ozeP = nullptr, *ozeBig = nullptr, *ozeSA = nullptr, *ozeSB = nullptr;
     ctm::EigWork ew;
+    ctm::OaWork oa;
+    long long rr_refined = 0, rr_jacobi = 0;  // Rayleigh-Ritz solves by path
     ctm::DevCtl* ctl;
     ctm::DevCtl* hctl = nullptr;  // pinned mirror
     // host-side iteration state
@@ -165,17 +215,36 @@ ctm_status validate(const ctm_config* c) {
         for (int k = 0; k < c->dim; ++k) n2 += c->spins[s * c->dim + k] * c->spins[s * c->dim + k];
         if (!(fabs(sqrt(n2) - 1.0) <= 1e-12)) return fail(CTM_EINVAL, "spins must be unit vectors");
     }
-    if (c->prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "only CTM_FP64 is built in this library");
+    if (c->prec != CTM_FP64 && c->prec != CTM_TF32 && c->prec != CTM_BF16 && c->prec != CTM_OZAKI64)
+        return fail(CTM_EUNSUPPORTED, "precision mode not built in this library");
+    if (c->prec == CTM_OZAKI64 && c->ozaki_slices != 0 && (c->ozaki_slices < 3 || c->ozaki_slices > 7))
+        return fail(CTM_EINVAL, "ozaki_slices must be 0 (default 6) or in [3, 7]");
     return CTM_OK;
 }
 
+// Defaults.  The residual and the step-to-step change cannot fall below the
+// rounding of the contraction operands, so the reduced-precision forms get
+// tolerances at their floor (TF32: 10 explicit mantissa bits, BF16: 7).
 ctm_config with_defaults(const ctm_config& c) {
     ctm_config r = c;
-    if (r.tol_spectrum <= 0.0) r.tol_spectrum = 1e-12;
+    double floor_tol = (c.prec == CTM_BF16) ? 3e-3 : (c.prec == CTM_TF32 ? 3e-5 : 0.0);
+    if (c.prec == CTM_OZAKI64) {
+        // s digit planes of 7 bits: products carry about 2^(-7s) relative error
+        const int S = c.ozaki_slices > 0 ? c.ozaki_slices : 6;
+        floor_tol = std::max(1e-13, ldexp(1.0, -7 * S + 3));
+    }
+    if (r.tol_spectrum <= 0.0) r.tol_spectrum = floor_tol > 0.0 ? floor_tol : 1e-12;
     if (r.max_steps <= 0) r.max_steps = 5000;
     if (r.max_subspace_iters <= 0) r.max_subspace_iters = 50;
-    if (r.subspace_tol <= 0.0) r.subspace_tol = 1e-13;
-    if (r.tol_cluster <= 0.0) r.tol_cluster = 1e-10;
+    if (r.subspace_tol <= 0.0) r.subspace_tol = floor_tol > 0.0 ? floor_tol : 1e-13;
+    // Multiplets must still be recognised when rounding splits them: in the
+    // reduced-precision forms the cluster tolerance sits above the noise.
+    if (r.tol_cluster <= 0.0) {
+        r.tol_cluster = (c.prec == CTM_BF16) ? 3e-2 : (c.prec == CTM_TF32 ? 3e-4 : 1e-10);
+        // the digit expansion is relative to each row's largest entry, so the
+        // small eigenvalues of C~ carry errors near 2^(-7s) K times |w_1|
+        if (c.prec == CTM_OZAKI64) r.tol_cluster = (c.ozaki_slices == 7) ? 1e-9 : 1e-8;
+    }
     return r;
 }
 
@@ -347,9 +416,11 @@ inline int grid_for(size_t work, int cap = 152 * 8) {
 }
 
 // --------------------------------------------------------------- profiling
-enum ProfClass { PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_SMALL, PC_COUNT };
-const char* const kProfNames[PC_COUNT + 1] = {"gemm_f64", "wcontract_f64", "jacobi_f64", "cholqr_f64", "small",
-                                              "all"};
+enum ProfClass {
+    PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_TCGEMM, PC_CONVERT, PC_OZGEMM, PC_OZSPLIT, PC_SMALL, PC_COUNT
+};
+const char* const kProfNames[PC_COUNT + 1] = {"gemm_f64", "wcontract_f64", "jacobi_f64", "cholqr_f64", "tc_gemm",
+                                              "to_operand", "oz_gemm", "oz_split", "small", "all"};
 
 cudaEvent_t take_event(ctm_handle* h) {
     if (h->evnext == h->evpool.size()) {
@@ -394,10 +465,84 @@ void pgemm(ctm_handle* h, bool tA, bool tB, int M, int N, int K, const double* A
     prof_end(h, a, PC_GEMM, nk, fl, by);
 }
 
+// Profiled conversion of R rows (each a column of a column-major FP64 matrix,
+// K long) into the tensor-core operand precision.
+void pconvert(ctm_handle* h, int R, int K, const double* src, int lds, const double* scale, void* dst, int ldo) {
+    cudaEvent_t a = prof_begin(h);
+    ctm::to_operand(h->st, h->lay.esz == 2, R, K, src, lds, scale, dst, ldo);
+    prof_end(h, a, PC_CONVERT, 1, 0.0, (double)R * K * 8.0 + (double)R * ldo * h->lay.esz);
+}
+
+// Profiled tensor-core GEMM D = A B^t (operands already converted).
+ctm_status ptc(ctm_handle* h, int M, int N, int K, const void* A, int lda, const void* B, int ldb, double* D,
+               int ldd) {
+    cudaEvent_t a = prof_begin(h);
+    cudaError_t e = ctm::tc_gemm(h->st, h->lay.esz == 2, M, N, K, 1.0, A, lda, B, ldb, 0.0, D, ldd, h->tcerr);
+    if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("tc_gemm: ") + cudaGetErrorString(e));
+    double fl = 2.0 * M * (double)N * K;
+    double by = (double)h->lay.esz * ((double)M * K + (double)K * N) + 8.0 * (double)M * N;
+    prof_end(h, a, PC_TCGEMM, 1, fl, by);
+    return CTM_OK;
+}
+
+// Operand of a contraction D(i, j) = sum_k A(i, k) B(j, k): element (r, k) is
+// p[r rs + k ks], times scale[k] when scale is given.
+struct Opnd {
+    const double* p;
+    long rs, ks;
+    const double* scale;
+};
+enum OzSlot { OZ_P = 0, OZ_BIG, OZ_SA, OZ_SB };
+
+void oz_slot(ctm_handle* h, OzSlot sl, void** planes, int** e) {
+    switch (sl) {
+        case OZ_P: *planes = h->ozP; *e = h->ozeP; break;
+        case OZ_BIG: *planes = h->ozBig; *e = h->ozeBig; break;
+        case OZ_SA: *planes = h->ozSA; *e = h->ozeSA; break;
+        default: *planes = h->ozSB; *e = h->ozeSB; break;
+    }
+}
+
+// FP64-emulating contraction on the tensor cores: split A and B (unless the
+// slot already holds that operand) and multiply the digit planes.
+ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool splitA, Opnd B, OzSlot sb, bool splitB,
+                double* D, int ldd) {
+    const int S = h->lay.slices;
+    void *pa, *pb;
+    int *ea, *eb;
+    oz_slot(h, sa, &pa, &ea);
+    oz_slot(h, sb, &pb, &eb);
+    if (splitA || splitB) {
+        cudaEvent_t a = prof_begin(h);
+        int nk = 0;
+        if (splitA) {
+            ctm::oz_split_strided(h->st, M, K, S, A.p, A.rs, A.ks, A.scale, pa, true, ea);
+            ++nk;
+        }
+        if (splitB) {
+            ctm::oz_split_strided(h->st, N, K, S, B.p, B.rs, B.ks, B.scale, pb, false, eb);
+            ++nk;
+        }
+        prof_end(h, a, PC_OZSPLIT, nk, 0.0, 8.0 * ((splitA ? (double)M * K : 0.0) + (splitB ? (double)N * K : 0.0)));
+    }
+    cudaEvent_t a = prof_begin(h);
+    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr);
+    if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("oz_gemm: ") + cudaGetErrorString(e));
+    const double pairs = S * (S + 1) / 2.0;
+    prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * M * (double)N * K,
+             2.0 * S * ((double)M * K + (double)N * K) + 8.0 * (double)M * N);
+    return CTM_OK;
+}
+
+inline bool is_oz(const ctm_handle* h) { return h->lay.prec == CTM_OZAKI64; }
+
 void pwcontract(ctm_handle* h, double* X, const double* E1, const int* live_dev, int live_host) {
     const Layout& L = h->lay;
     cudaEvent_t a = prof_begin(h);
-    ctm::wcontract_f64(h->st, L.m, L.q, X, L.N, h->E, E1, live_dev);
+    // FP64 form: FP64; Ozaki form: double-float (its products carry ~2^-42);
+    // TF32 / BF16 forms: FP32 (far below their operand rounding)
+    const int arith = (L.prec == CTM_FP64) ? 0 : (L.prec == CTM_OZAKI64 ? 2 : 1);
+    ctm::wcontract_ar(h->st, arith, L.m, L.q, X, L.N, h->E, E1, live_dev);
     double nb = (double)live_host * live_host, q = L.q;
     prof_end(h, a, PC_WCONTRACT, 1, nb * 4.0 * q * q * q, nb * 2.0 * 8.0 * q * q);
 }
@@ -423,7 +568,18 @@ int gemm_splits(const Layout& L, int M, int Nn, int K) {
 // C = P^t diag(omega) P, then the vertex-weight contraction (E1 = E or Eh).
 void stage_extend(ctm_handle* h, const double* E1) {
     const Layout& L = h->lay;
-    pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega);
+    if (is_oz(h)) {
+        ozmm(h, L.N, L.N, L.m, {h->P, L.m, 1, nullptr}, OZ_P, true, {h->P, L.m, 1, h->omega}, OZ_SB, true, h->C,
+             L.N);
+    } else if (L.esz) {
+        // X1 = P^t diag(omega) P on the tensor cores: operand rows are the
+        // columns of P (K = m), the second one scaled by omega along K.
+        pconvert(h, L.N, L.m, h->P, L.m, nullptr, h->opP, L.ldm);
+        pconvert(h, L.N, L.m, h->P, L.m, h->omega, h->opPw, L.ldm);
+        ptc(h, L.N, L.N, L.m, h->opP, L.ldm, h->opPw, L.ldm, h->C, L.N);
+    } else {
+        pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega);
+    }
     pwcontract(h, h->C, E1, &h->ctl->live, h->live);
 }
 
@@ -436,13 +592,25 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
     double* cur = src;
     for (int i = 0; i < passes; ++i) {
         double* out = bufs[(passes - 1 - i) % 2];
-        pgemm(h, true, false, b, b, N, cur, N, cur, N, h->G, b, nullptr, gemm_splits(L, b, b, N));
+        if (is_oz(h)) {
+            ctm_status s0 = ozmm(h, b, b, N, {cur, N, 1, nullptr}, OZ_SA, true, {cur, N, 1, nullptr}, OZ_SB, true,
+                                 h->G, b);
+            if (s0 != CTM_OK) return s0;
+        } else {
+            pgemm(h, true, false, b, b, N, cur, N, cur, N, h->G, b, nullptr, gemm_splits(L, b, b, N));
+        }
         double shift_rel = (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
         cudaEvent_t a = prof_begin(h);
         CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl));
-        ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b);
-        prof_end(h, a, PC_CHOLQR, 2, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
-        pgemm(h, false, true, N, b, b, cur, N, h->Linv, b, out, N);
+        ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
+        prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
+        if (is_oz(h)) {
+            ctm_status s0 = ozmm(h, N, b, b, {cur, 1, N, nullptr}, OZ_SA, true, {h->Linv, 1, b, nullptr}, OZ_SB, true,
+                                 out, N);
+            if (s0 != CTM_OK) return s0;
+        } else {
+            pgemm(h, false, true, N, b, b, cur, N, h->Linv, b, out, N);
+        }
         cur = out;
     }
     CTM_CUDA(cudaGetLastError());
@@ -462,7 +630,8 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         count_small(h, 1);
         max_iters = 1;
         passes = 2;
-    } else if (h->warm && h->warm_live == h->live) {
+    } else if (h->warm && 2 * h->live >= h->warm_live && h->live <= 2 * h->warm_live) {
+        // the renormalised basis is the same one up to states near the cut
         CTM_CUDA(cudaMemcpyAsync(h->V, h->Zprev, sizeof(double) * N * b, cudaMemcpyDeviceToDevice, h->st));
         cold = false;
         passes = 2;
@@ -475,14 +644,50 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
     }
     bool conv = false;
     int it = 0;
+    if (L.esz) pconvert(h, N, N, h->C, N, nullptr, h->opC, L.ldN);  // C~ rows (symmetric)
     for (it = 0; it < max_iters; ++it) {
-        pgemm(h, false, false, N, b, N, h->C, N, h->V, N, h->Y, N);
-        pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+        if (is_oz(h)) {
+            // C~ is split once per eigen stage (first iteration), V every iteration
+            ctm_status s0 = ozmm(h, N, b, N, {h->C, N, 1, nullptr}, OZ_BIG, it == 0, {h->V, N, 1, nullptr}, OZ_SB,
+                                 true, h->Y, N);
+            if (s0 != CTM_OK) return s0;
+            s0 = ozmm(h, b, b, N, {h->V, N, 1, nullptr}, OZ_SA, true, {h->Y, N, 1, nullptr}, OZ_SB, true, h->H, b);
+            if (s0 != CTM_OK) return s0;
+        } else if (L.esz) {
+            pconvert(h, b, N, h->V, N, nullptr, h->opV, L.ldN);
+            ctm_status s0 = ptc(h, N, b, N, h->opC, L.ldN, h->opV, L.ldN, h->Y, N);
+            if (s0 != CTM_OK) return s0;
+            pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+        } else {
+            pgemm(h, false, false, N, b, N, h->C, N, h->V, N, h->Y, N);
+            pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+        }
+        // Rayleigh-Ritz: simultaneous Jacobi rotations when the block is warm
+        // (H nearly diagonal), the cooperative Jacobi solver otherwise or as a
+        // fallback.
         cudaEvent_t ja = prof_begin(h);
-        CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
-        prof_end(h, ja, PC_JACOBI, 4);
-        pgemm(h, false, false, N, b, b, h->V, N, h->Sb, b, h->Z, N);
-        pgemm(h, false, false, N, b, b, h->Y, N, h->Sb, b, h->T, N);
+        int nk_rr = 0, used = -1;
+        if (!cold || it > 0)
+            used = ctm::rr_refine_f64(h->st, b, std::min(b, m + 2), h->H, b, h->oa, h->ew, h->theta, h->Sb, b, 1e-13,
+                                      8, h->ctl, h->hctl, &nk_rr);
+        if (used < 0) {
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
+            nk_rr += 4;
+            ++h->rr_jacobi;
+        } else {
+            ++h->rr_refined;
+        }
+        prof_end(h, ja, PC_JACOBI, nk_rr);
+        if (is_oz(h)) {
+            ctm_status s0 = ozmm(h, N, b, b, {h->V, 1, N, nullptr}, OZ_SA, true, {h->Sb, b, 1, nullptr}, OZ_SB, true,
+                                 h->Z, N);
+            if (s0 != CTM_OK) return s0;
+            s0 = ozmm(h, N, b, b, {h->Y, 1, N, nullptr}, OZ_SA, true, {h->Sb, b, 1, nullptr}, OZ_SB, false, h->T, N);
+            if (s0 != CTM_OK) return s0;
+        } else {
+            pgemm(h, false, false, N, b, b, h->V, N, h->Sb, b, h->Z, N);
+            pgemm(h, false, false, N, b, b, h->Y, N, h->Sb, b, h->T, N);
+        }
         int nchk = std::min(m + 1, std::min(b, Ldim));
         ctm::resid_f64(h->st, N, nchk, h->T, h->Z, N, h->theta, h->res);
         ctm::decide(h->st, b, Ldim, m, h->cfg.subspace_tol, h->cfg.tol_cluster, h->theta, h->res, h->ctl);
@@ -534,9 +739,31 @@ ctm_status step_once(ctm_handle* h) {
     // a4: U, U' and P <- U^t Sub-CTMRG(P, U', W)
     k_make_U<<<grid_for((size_t)N * m), 256, 0, h->st>>>(N, m, L.q, h->Z, N, h->ctl, h->U, h->Up);
     count_small(h, 1);
-    pgemm(h, true, false, N, N, m, h->P, m, h->Up, m, h->C, N);
+    if (is_oz(h)) {
+        // X1' = P^t U' (the P planes of the extension are still current)
+        s = ozmm(h, N, N, m, {h->P, m, 1, nullptr}, OZ_P, false, {h->Up, m, 1, nullptr}, OZ_SB, true, h->C, N);
+        if (s != CTM_OK) return s;
+    } else if (L.esz) {
+        // X1' = P^t U' (the P operand of the extension is still current)
+        pconvert(h, N, m, h->Up, m, nullptr, h->opUp, L.ldm);
+        s = ptc(h, N, N, m, h->opP, L.ldm, h->opUp, L.ldm, h->C, N);
+        if (s != CTM_OK) return s;
+    } else {
+        pgemm(h, true, false, N, N, m, h->P, m, h->Up, m, h->C, N);
+    }
     pwcontract(h, h->C, h->E, h->mfull, m);
-    pgemm(h, true, false, m, N, N, h->U, N, h->C, N, h->Pn, m, nullptr, gemm_splits(L, m, N, N));
+    if (is_oz(h)) {
+        s = ozmm(h, m, N, N, {h->U, N, 1, nullptr}, OZ_SA, true, {h->C, N, 1, nullptr}, OZ_BIG, true, h->Pn, m);
+        if (s != CTM_OK) return s;
+    } else if (L.esz) {
+        // P_new = U^t X: operand rows are the columns of U and of X (K = N)
+        pconvert(h, m, N, h->U, N, nullptr, h->opU, L.ldN);
+        pconvert(h, N, N, h->C, N, nullptr, h->opC, L.ldN);
+        s = ptc(h, m, N, N, h->opU, L.ldN, h->opC, L.ldN, h->Pn, m);
+        if (s != CTM_OK) return s;
+    } else {
+        pgemm(h, true, false, m, N, N, h->U, N, h->C, N, h->Pn, m, nullptr, gemm_splits(L, m, N, N));
+    }
     // a5/a6
     const int nparts = 512;
     k_sumsq_partial<<<nparts, 256, 0, h->st>>>((size_t)m * N, h->Pn, h->red);
@@ -547,6 +774,11 @@ ctm_status step_once(ctm_handle* h) {
     s = sync_ctl(h);
     if (s != CTM_OK) return s;
     if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the renormalisation");
+    if (h->tcerr) {
+        int e = 0;
+        CTM_CUDA(cudaMemcpy(&e, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) return fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
+    }
     // the warm start for the next step is this step's aligned Ritz block
     std::swap(h->Z, h->Zprev);
     h->warm = true;
@@ -564,6 +796,8 @@ ctm_status step_once(ctm_handle* h) {
     I.jacobi_sweeps = h->hctl->jac_sweeps;
     I.steps = h->steps;
     I.converged = (h->hctl->delta < h->cfg.tol_spectrum) ? 1 : 0;
+    I.rr_refined = h->rr_refined;
+    I.rr_jacobi = h->rr_jacobi;
     return conv ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
@@ -635,6 +869,26 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
     h->part = D(L.off_part);
     h->red = D(L.off_red);
     h->colv = D(L.off_colv);
+    if (L.esz) {
+        h->opP = h->ws + L.off_opP;
+        h->opPw = h->ws + L.off_opPw;
+        h->opC = h->ws + L.off_opC;
+        h->opV = h->ws + L.off_opV;
+        h->opUp = h->ws + L.off_opUp;
+        h->opU = h->ws + L.off_opU;
+        h->tcerr = (int*)(h->ws + L.off_tcerr);
+    }
+    if (L.prec == CTM_OZAKI64) {
+        h->ozP = h->ws + L.off_ozP;
+        h->ozBig = h->ws + L.off_ozBig;
+        h->ozSA = h->ws + L.off_ozSA;
+        h->ozSB = h->ws + L.off_ozSB;
+        h->ozeP = (int*)(h->ws + L.off_ozeP);
+        h->ozeBig = (int*)(h->ws + L.off_ozeBig);
+        h->ozeSA = (int*)(h->ws + L.off_ozeSA);
+        h->ozeSB = (int*)(h->ws + L.off_ozeSB);
+        h->tcerr = (int*)(h->ws + L.off_tcerr);
+    }
     h->ew.A0 = D(L.off_A0);
     h->ew.A1 = D(L.off_A1);
     h->ew.S = D(L.off_S);
@@ -644,6 +898,14 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
     h->ew.gQ = D(L.off_gQ);
     h->ew.gkind = (int*)(h->ws + L.off_gk);
     h->ctl = (ctm::DevCtl*)(h->ws + L.off_ctl);
+    h->oa.X = D(L.off_oaX);
+    h->oa.W1 = D(L.off_oaW1);
+    h->oa.S = D(L.off_oaS);
+    h->oa.R = D(L.off_oaR);
+    h->oa.E = D(L.off_oaE);
+    h->oa.part = D(L.off_oapart);
+    h->oa.gpart = D(L.off_part);
+    h->oa.max_splits = L.splits;
     h->mfull = (int*)(h->ws + L.off_mfull);
     h->spins_h.assign(cfg->spins, cfg->spins + (size_t)cfg->q * cfg->dim);
 
@@ -777,30 +1039,41 @@ ctm_status ctm_symeig(int n, const double* A, int lda, double* evals, double* ve
 
 // ---- one contraction in a chosen precision
 namespace {
-size_t contract_ws(ctm_precision prec, int M, int N, int K) {
+size_t contract_ws(ctm_precision prec, int slices, int M, int N, int K) {
     if (prec == CTM_FP64) return 256;
+    if (prec == CTM_OZAKI64)
+        return align256(ctm::oz_operand_bytes(M, K, slices, true)) + align256(ctm::oz_operand_bytes(N, K, slices, false)) +
+               align256((size_t)M * sizeof(int)) + align256((size_t)N * sizeof(int)) + 256;
     size_t esz = (prec == CTM_BF16) ? 2 : 4;
     size_t ld = (size_t)ctm::tc_ld(K);
     return align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz) + 256;
 }
+bool contract_prec_ok(ctm_precision p) {
+    return p == CTM_FP64 || p == CTM_TF32 || p == CTM_BF16 || p == CTM_OZAKI64;
+}
 }  // namespace
 
-ctm_status ctm_contract_workspace_size(ctm_precision prec, int M, int N, int K, size_t* bytes) {
+ctm_status ctm_contract_workspace_size(ctm_precision prec, int ozaki_slices, int M, int N, int K, size_t* bytes) {
     if (!bytes || M < 1 || N < 1 || K < 1) return fail(CTM_EINVAL, "bad sizes");
-    if (prec != CTM_FP64 && prec != CTM_TF32 && prec != CTM_BF16)
-        return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
-    *bytes = contract_ws(prec, M, N, K);
+    if (!contract_prec_ok(prec)) return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
+    if (ozaki_slices == 0) ozaki_slices = 6;
+    if (prec == CTM_OZAKI64 && (ozaki_slices < 3 || ozaki_slices > 7))
+        return fail(CTM_EINVAL, "ozaki_slices must be in [3, 7]");
+    *bytes = contract_ws(prec, ozaki_slices, M, N, K);
     return CTM_OK;
 }
 
-ctm_status ctm_contract(ctm_precision prec, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                        double* D, int ldd, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+ctm_status ctm_contract(ctm_precision prec, int ozaki_slices, int M, int N, int K, const double* A, int lda,
+                        const double* B, int ldb, double* D, int ldd, void* workspace, size_t workspace_bytes,
+                        void* cuda_stream) {
     if (M < 1 || N < 1 || K < 1) return fail(CTM_EINVAL, "bad sizes");
     if (!A || !B || !D || !workspace) return fail(CTM_EINVAL, "NULL argument");
     if (lda < K || ldb < K || ldd < M) return fail(CTM_EINVAL, "leading dimension too small");
-    if (prec != CTM_FP64 && prec != CTM_TF32 && prec != CTM_BF16)
-        return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
-    if (workspace_bytes < contract_ws(prec, M, N, K)) return fail(CTM_EINVAL, "workspace too small");
+    if (!contract_prec_ok(prec)) return fail(CTM_EUNSUPPORTED, "precision not built for ctm_contract");
+    if (ozaki_slices == 0) ozaki_slices = 6;
+    if (prec == CTM_OZAKI64 && (ozaki_slices < 3 || ozaki_slices > 7))
+        return fail(CTM_EINVAL, "ozaki_slices must be in [3, 7]");
+    if (workspace_bytes < contract_ws(prec, ozaki_slices, M, N, K)) return fail(CTM_EINVAL, "workspace too small");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     char* ws = (char*)workspace;
     if (prec == CTM_FP64) {
@@ -809,16 +1082,31 @@ ctm_status ctm_contract(ctm_precision prec, int M, int N, int K, const double* A
         CTM_CUDA(cudaStreamSynchronize(st));
         return CTM_OK;
     }
-    const bool bf16 = prec == CTM_BF16;
-    const size_t esz = bf16 ? 2 : 4;
-    const int ld = ctm::tc_ld(K);
-    void* Aop = ws;
-    void* Bop = ws + align256((size_t)M * ld * esz);
-    int* err = (int*)(ws + align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz));
-    CTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-    ctm::to_operand(st, bf16, M, K, A, lda, nullptr, Aop, ld);
-    ctm::to_operand(st, bf16, N, K, B, ldb, nullptr, Bop, ld);
-    CTM_CUDA(ctm::tc_gemm(st, bf16, M, N, K, 1.0, Aop, ld, Bop, ld, 0.0, D, ldd, err));
+    int* err = nullptr;
+    if (prec == CTM_OZAKI64) {
+        size_t oa = align256(ctm::oz_operand_bytes(M, K, ozaki_slices, true));
+        size_t ob = align256(ctm::oz_operand_bytes(N, K, ozaki_slices, false));
+        void* Ap = ws;
+        void* Bp = ws + oa;
+        int* eA = (int*)(ws + oa + ob);
+        int* eB = (int*)(ws + oa + ob + align256((size_t)M * sizeof(int)));
+        err = (int*)(ws + oa + ob + align256((size_t)M * sizeof(int)) + align256((size_t)N * sizeof(int)));
+        CTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        ctm::oz_split(st, M, K, ozaki_slices, A, lda, nullptr, Ap, true, eA);
+        ctm::oz_split(st, N, K, ozaki_slices, B, ldb, nullptr, Bp, false, eB);
+        CTM_CUDA(ctm::oz_gemm(st, ozaki_slices, M, N, K, Ap, eA, Bp, eB, D, ldd, err));
+    } else {
+        const bool bf16 = prec == CTM_BF16;
+        const size_t esz = bf16 ? 2 : 4;
+        const int ld = ctm::tc_ld(K);
+        void* Aop = ws;
+        void* Bop = ws + align256((size_t)M * ld * esz);
+        err = (int*)(ws + align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz));
+        CTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        ctm::to_operand(st, bf16, M, K, A, lda, nullptr, Aop, ld);
+        ctm::to_operand(st, bf16, N, K, B, ldb, nullptr, Bop, ld);
+        CTM_CUDA(ctm::tc_gemm(st, bf16, M, N, K, 1.0, Aop, ld, Bop, ld, 0.0, D, ldd, err));
+    }
     int herr = 0;
     CTM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CTM_CUDA(cudaStreamSynchronize(st));
@@ -868,7 +1156,12 @@ ctm_status ctm_observables(ctm_handle* h, ctm_obs* out) {
     h->warm_live = h->live;
     // impurity corner C~_h (bond energy inserted), then Yh = C~_h Z
     stage_extend(h, h->Eh);
-    pgemm(h, false, false, N, b, N, h->C, N, h->Zprev, N, h->Y, N);
+    if (is_oz(h)) {
+        s = ozmm(h, N, b, N, {h->C, N, 1, nullptr}, OZ_BIG, true, {h->Zprev, N, 1, nullptr}, OZ_SB, true, h->Y, N);
+        if (s != CTM_OK) return s;
+    } else {
+        pgemm(h, false, false, N, b, N, h->C, N, h->Zprev, N, h->Y, N);
+    }
     k_obs_cols<<<b, 256, 0, h->st>>>(N, L.q, b, h->Zprev, h->Y, h->mag, h->colv);
     k_obs_finalize<<<1, 32, 0, h->st>>>(b, h->theta, h->colv, h->ctl);
     count_small(h, 2);

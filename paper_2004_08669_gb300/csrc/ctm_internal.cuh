@@ -43,6 +43,8 @@ struct DevCtl {
     int rot_count[64];   // rotations per Jacobi sweep
     // observables
     double obs_M_num, obs_u_num, obs_z4, obs_SE;
+    // warm Rayleigh-Ritz refinement
+    double oa_maxE;
 };
 
 // Grid-wide barrier for cooperative launches.  Every wait is bounded: after
@@ -93,5 +95,9 @@ int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, dou
 // gamma' >= *live are zero and skipped.
 void wcontract_f64(cudaStream_t st, int m, int q, double* X, int ldx, const double* E,
                    const double* E1, const int* live);
+
+// The same contraction with arithmetic 0 = FP64, 1 = FP32, 2 = double-float.
+void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, const double* E, const double* E1,
+                  const int* live);
 
 }  // namespace ctm

@@ -17,6 +17,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace ctm {
 
 namespace {
@@ -69,10 +71,18 @@ __global__ void k_jacobi_init(int n, int npad, const double* __restrict__ H, int
 }
 
 // Cooperative: all blocks co-resident (cudaLaunchAttributeCooperative).
+// Each round, every block first computes the npad/2 rotations of the round
+// into shared memory (one square root and division per pair, not per
+// element: FP64 division and square root are costly on this part), then
+// applies them to its share of the 2 x 2 blocks and of the rows of S.
 __global__ void k_jacobi(int n, int npad, double* A0, double* A1,
                          double* S, double* __restrict__ diag, int max_sweeps,
                          double eps, double floor_abs, DevCtl* ctl) {
+    extern __shared__ double rot_sh[];  // 3 * (npad / 2): c, s, t (t = 0: off)
     const int half = npad / 2;
+    double* rc = rot_sh;
+    double* rs = rot_sh + half;
+    double* rt = rot_sh + 2 * half;
     const long nblk_items = (long)half * half;
     const long nS_items = (long)npad * half;
     const long W = nblk_items + nS_items;
@@ -86,23 +96,33 @@ __global__ void k_jacobi(int n, int npad, double* A0, double* A1,
         for (int r = 0; r < npad - 1; ++r, ++round_total) {
             const double* Ac = (round_total & 1) ? A1 : A0;
             double* An = (round_total & 1) ? A0 : A1;
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int p, q;
+                rr_pair(r, k, npad, p, q);
+                Rot R = rot_of(Ac, npad, p, q, eps, floor_abs);
+                rc[k] = R.c;
+                rs[k] = R.s;
+                rt[k] = R.on ? R.t : 0.0;
+                if (R.on && blockIdx.x == 0) atomicAdd(&ctl->rot_count[sweep], 1);
+            }
+            __syncthreads();
             for (long it = gtid; it < W; it += gstride) {
                 if (it < nblk_items) {
                     int ka = (int)(it % half), kb = (int)(it / half);
                     int p, q, rr, tt;
                     rr_pair(r, ka, npad, p, q);
                     rr_pair(r, kb, npad, rr, tt);
-                    Rot Ra = rot_of(Ac, npad, p, q, eps, floor_abs);
+                    const double ca = rc[ka], sa = rs[ka];
+                    const bool ona = rt[ka] != 0.0;
                     if (ka == kb) {
                         double app = __ldcg(Ac + p + (size_t)npad * p);
                         double aqq = __ldcg(Ac + q + (size_t)npad * q);
                         double apq = __ldcg(Ac + p + (size_t)npad * q);
-                        if (Ra.on) {
-                            An[p + (size_t)npad * p] = app - Ra.t * apq;
-                            An[q + (size_t)npad * q] = aqq + Ra.t * apq;
+                        if (ona) {
+                            An[p + (size_t)npad * p] = app - rt[ka] * apq;
+                            An[q + (size_t)npad * q] = aqq + rt[ka] * apq;
                             An[p + (size_t)npad * q] = 0.0;
                             An[q + (size_t)npad * p] = 0.0;
-                            atomicAdd(&ctl->rot_count[sweep], 1);
                         } else {
                             An[p + (size_t)npad * p] = app;
                             An[q + (size_t)npad * q] = aqq;
@@ -110,31 +130,31 @@ __global__ void k_jacobi(int n, int npad, double* A0, double* A1,
                             An[q + (size_t)npad * p] = __ldcg(Ac + q + (size_t)npad * p);
                         }
                     } else {
-                        Rot Rb = rot_of(Ac, npad, rr, tt, eps, floor_abs);
+                        const double cb = rc[kb], sb = rs[kb];
                         double a_pr = __ldcg(Ac + p + (size_t)npad * rr);
                         double a_pt = __ldcg(Ac + p + (size_t)npad * tt);
                         double a_qr = __ldcg(Ac + q + (size_t)npad * rr);
                         double a_qt = __ldcg(Ac + q + (size_t)npad * tt);
                         // J_a^t from the left (rows p, q)
-                        double x_pr = Ra.c * a_pr - Ra.s * a_qr, x_pt = Ra.c * a_pt - Ra.s * a_qt;
-                        double x_qr = Ra.s * a_pr + Ra.c * a_qr, x_qt = Ra.s * a_pt + Ra.c * a_qt;
+                        double x_pr = ca * a_pr - sa * a_qr, x_pt = ca * a_pt - sa * a_qt;
+                        double x_qr = sa * a_pr + ca * a_qr, x_qt = sa * a_pt + ca * a_qt;
                         // J_b from the right (columns r, t)
-                        An[p + (size_t)npad * rr] = Rb.c * x_pr - Rb.s * x_pt;
-                        An[p + (size_t)npad * tt] = Rb.s * x_pr + Rb.c * x_pt;
-                        An[q + (size_t)npad * rr] = Rb.c * x_qr - Rb.s * x_qt;
-                        An[q + (size_t)npad * tt] = Rb.s * x_qr + Rb.c * x_qt;
+                        An[p + (size_t)npad * rr] = cb * x_pr - sb * x_pt;
+                        An[p + (size_t)npad * tt] = sb * x_pr + cb * x_pt;
+                        An[q + (size_t)npad * rr] = cb * x_qr - sb * x_qt;
+                        An[q + (size_t)npad * tt] = sb * x_qr + cb * x_qt;
                     }
                 } else {
                     long e = it - nblk_items;
                     int row = (int)(e % npad), k = (int)(e / npad);
-                    int p, q;
-                    rr_pair(r, k, npad, p, q);
-                    Rot Ra = rot_of(Ac, npad, p, q, eps, floor_abs);
-                    if (Ra.on) {
+                    if (rt[k] != 0.0) {
+                        int p, q;
+                        rr_pair(r, k, npad, p, q);
+                        const double c = rc[k], sn = rs[k];
                         double sp = __ldcg(S + row + (size_t)npad * p);
                         double sq = __ldcg(S + row + (size_t)npad * q);
-                        S[row + (size_t)npad * p] = Ra.c * sp - Ra.s * sq;
-                        S[row + (size_t)npad * q] = Ra.s * sp + Ra.c * sq;
+                        S[row + (size_t)npad * p] = c * sp - sn * sq;
+                        S[row + (size_t)npad * q] = sn * sp + c * sq;
                     }
                 }
             }
@@ -176,9 +196,14 @@ __global__ void k_gather_ritz(int n, int npad, const int* __restrict__ rank, con
 }
 
 // Blocked right-looking Cholesky G + shift I = L L^t (lower, in place),
-// panel width 32.  Cooperative launch.
-__global__ void k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
+// panel width 32.  Cooperative launch, two grid barriers per panel: every
+// block factors the 32 x 32 diagonal block itself (identical arithmetic in
+// each, so all agree) and solves its share of the panel rows; the trailing
+// update then runs on 64 x 64 lower tiles staged in shared memory.
+__global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
     __shared__ double D[32][33];
+    __shared__ double PI[32][65];  // panel rows of tile I (l-major)
+    __shared__ double PJ[32][65];  // panel rows of tile J
     int* err = &ctl->chol_status;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
@@ -193,86 +218,131 @@ __global__ void k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* c
     if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int kb = min(32, n - k0);
-        if (blockIdx.x == 0) {
-            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-                int i = e % kb, j = e / kb;
-                D[i][j] = __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j));
-            }
-            __syncthreads();
-            for (int j = 0; j < kb; ++j) {
-                if (threadIdx.x == 0) {
-                    double d = D[j][j];
-                    if (!(d > 0.0) || !isfinite(d)) {
-                        atomicMax(err, 1);
-                        d = 1.0;
-                    }
-                    D[j][j] = sqrt(d);
-                }
-                __syncthreads();
-                for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) D[i][j] /= D[j][j];
-                __syncthreads();
-                for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-                    int i = e % kb, l = e / kb;
-                    if (l > j && i >= l) D[i][l] -= D[i][j] * D[l][j];
-                }
-                __syncthreads();
-            }
-            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-                int i = e % kb, j = e / kb;
-                G[(k0 + i) + (size_t)ld * (k0 + j)] = (i >= j) ? D[i][j] : 0.0;
-            }
-        }
-        if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
-        const int k1 = k0 + kb;
-        if (k1 >= n) break;
-        // panel solve: rows below the diagonal block
+        // --- diagonal block, factored redundantly in every block
         for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
             int i = e % kb, j = e / kb;
             D[i][j] = __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j));
         }
         __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            if (threadIdx.x == 0) {
+                double d = D[j][j];
+                if (!(d > 0.0) || !isfinite(d)) {
+                    if (blockIdx.x == 0) atomicMax(err, 1);
+                    d = 1.0;
+                }
+                D[j][j] = sqrt(d);
+            }
+            __syncthreads();
+            for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) D[i][j] /= D[j][j];
+            __syncthreads();
+            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+                int i = e % kb, l = e / kb;
+                if (l > j && i >= l) D[i][l] -= D[i][j] * D[l][j];
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0)
+            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+                int i = e % kb, j = e / kb;
+                G[(k0 + i) + (size_t)ld * (k0 + j)] = (i >= j) ? D[i][j] : 0.0;
+            }
+        const int k1 = k0 + kb;
+        // --- panel rows below: L[i, k0:k1] = G[i, k0:k1] L_kk^{-t}
         for (long i = k1 + gtid; i < n; i += gstride) {
             double x[32];
             for (int j = 0; j < kb; ++j) {
-                double s = __ldcg(G + i + (size_t)ld * (k0 + j));
-                for (int l = 0; l < j; ++l) s -= x[l] * D[j][l];
-                x[j] = s / D[j][j];
+                double sacc = __ldcg(G + i + (size_t)ld * (k0 + j));
+                for (int l = 0; l < j; ++l) sacc -= x[l] * D[j][l];
+                x[j] = sacc / D[j][j];
             }
             for (int j = 0; j < kb; ++j) G[i + (size_t)ld * (k0 + j)] = x[j];
         }
-        __syncthreads();
         if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
-        // trailing update of the lower triangle
-        const long nt = n - k1;
-        for (long e = gtid; e < nt * nt; e += gstride) {
-            int i = k1 + (int)(e % nt), j = k1 + (int)(e / nt);
-            if (j > i) continue;
-            double s = 0.0;
-            for (int l = 0; l < kb; ++l)
-                s += __ldcg(G + i + (size_t)ld * (k0 + l)) * __ldcg(G + j + (size_t)ld * (k0 + l));
-            G[i + (size_t)ld * j] = __ldcg(G + i + (size_t)ld * j) - s;
+        if (k1 >= n) break;
+        // --- trailing update on 64 x 64 tiles of the lower triangle
+        const int nt = n - k1;
+        const int T = (nt + 63) / 64;
+        const long ntiles = (long)T * (T + 1) / 2;
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        for (long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
+            // tile (I, J), I >= J, enumerated row by row
+            int I = (int)((sqrt(8.0 * (double)tIdx + 1.0) - 1.0) / 2.0);
+            while ((long)(I + 1) * (I + 2) / 2 <= tIdx) ++I;
+            while ((long)I * (I + 1) / 2 > tIdx) --I;
+            const int J = (int)(tIdx - (long)I * (I + 1) / 2);
+            const int i0 = k1 + 64 * I, j0 = k1 + 64 * J;
+            __syncthreads();
+            for (int e = threadIdx.x; e < 64 * kb; e += blockDim.x) {
+                int r = e & 63, l = e >> 6;
+                PI[l][r] = (i0 + r < n) ? __ldcg(G + (i0 + r) + (size_t)ld * (k0 + l)) : 0.0;
+                PJ[l][r] = (j0 + r < n) ? __ldcg(G + (j0 + r) + (size_t)ld * (k0 + l)) : 0.0;
+            }
+            __syncthreads();
+            double acc[4][4] = {};
+            for (int l = 0; l < kb; ++l) {
+                double a[4], bq[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = PI[l][tx + 16 * u];
+                    bq[u] = PJ[l][ty + 16 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bq[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
+                    if (i < n && j < n && j <= i) {
+                        double* g = G + i + (size_t)ld * j;
+                        *g = __ldcg(g) - acc[u][v];
+                    }
+                }
         }
         if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
     }
 }
 
-// Linv = L^{-1} (lower triangular), one warp per column.
-__global__ void k_trinv(int n, const double* __restrict__ L, int ld, double* __restrict__ X, int ldx) {
+// Lt = L^t (so that row i of L is contiguous for the inverse below).
+__global__ void k_transpose(int n, const double* __restrict__ L, int ld, double* __restrict__ Lt) {
+    __shared__ double t[32][33];
+    for (int by = blockIdx.y; by * 32 < n; by += gridDim.y)
+        for (int bx = blockIdx.x; bx * 32 < n; bx += gridDim.x) {
+            for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+                int i = bx * 32 + threadIdx.x, j = by * 32 + r;
+                t[r][threadIdx.x] = (i < n && j < n) ? L[i + (size_t)ld * j] : 0.0;
+            }
+            __syncthreads();
+            for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+                int i = by * 32 + threadIdx.x, j = bx * 32 + r;
+                if (i < n && j < n) Lt[i + (size_t)n * j] = t[threadIdx.x][r];
+            }
+            __syncthreads();
+        }
+}
+
+// Linv = L^{-1} (lower triangular), one warp per column; Lt = L^t (n x n), so
+// that the dot products below read contiguous memory.
+__global__ void k_trinv(int n, const double* __restrict__ Lt, double* __restrict__ X, int ldx) {
     extern __shared__ double xs[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     double* x = xs + (size_t)warp * n;
     for (int j = blockIdx.x * wpb + warp; j < n; j += gridDim.x * wpb) {
         for (int i = lane; i < j; i += 32) X[i + (size_t)ldx * j] = 0.0;
-        double xj = 1.0 / L[j + (size_t)ld * j];
+        double xj = 1.0 / Lt[j + (size_t)n * j];
         if (lane == 0) x[j] = xj;
         __syncwarp();
         for (int i = j + 1; i < n; ++i) {
             double s = 0.0;
-            for (int k = j + lane; k < i; k += 32) s += L[i + (size_t)ld * k] * x[k];
+            for (int k = j + lane; k < i; k += 32) s += Lt[k + (size_t)n * i] * x[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            double xi = -s / L[i + (size_t)ld * i];
+            double xi = -s / Lt[i + (size_t)n * i];
             __syncwarp();
             if (lane == 0) x[i] = xi;
             __syncwarp();
@@ -520,8 +590,15 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     long half = npad / 2;
     long W = half * half + (long)npad * half;
     int grid = (int)((W + 255) / 256);
+    const size_t smem = 3 * (size_t)(npad / 2) * sizeof(double);
     static int limit = 0;
-    if (limit == 0) limit = coop_grid_limit((const void*)k_jacobi, 256, 0);
+    static size_t limit_smem = 0;
+    if (limit == 0 || smem > limit_smem) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        limit = coop_grid_limit((const void*)k_jacobi, 256, smem);
+        limit_smem = smem;
+    }
     if (grid > limit) grid = limit;
     if (grid < 1) grid = 1;
     double eps = 2.220446049250313e-16, floor_abs = 0.0;
@@ -530,7 +607,7 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     double* S = w.S;
     double* diag = w.diag;
     void* args[] = {&n, &npad, &A0, &A1, &S, &diag, &max_sweeps, &eps, &floor_abs, &ctl};
-    cudaError_t e = launch_coop((const void*)k_jacobi, grid, 256, args, 0, st);
+    cudaError_t e = launch_coop((const void*)k_jacobi, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);
     k_gather_ritz<<<grid_for((size_t)n * n), 256, 0, st>>>(n, npad, w.rank, w.S, Sout, ldo);
@@ -551,11 +628,13 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
     return launch_coop((const void*)k_cholesky, grid, 256, args, 0, st);
 }
 
-void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx) {
+void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch) {
+    dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
+    k_transpose<<<tg, tb, 0, st>>>(n, L, ld, scratch);
     const int wpb = 4;
     int grid = (n + wpb - 1) / wpb;
     size_t smem = (size_t)wpb * n * sizeof(double);
-    k_trinv<<<grid, 32 * wpb, smem, st>>>(n, L, ld, X, ldx);
+    k_trinv<<<grid, 32 * wpb, smem, st>>>(n, scratch, X, ldx);
 }
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
@@ -587,6 +666,160 @@ void randn_block(cudaStream_t st, int N, int b, double* V, int ld, uint64_t seed
 
 void identity_block(cudaStream_t st, int N, int b, double* V, int ld) {
     k_identity_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, V, ld);
+}
+
+}  // namespace ctm
+
+// ---------------------------------------------------------------------------
+// Warm-start Rayleigh-Ritz: simultaneous Jacobi rotations.
+// For a warm start H = V^t C~ V is nearly diagonal.  Instead of sweeping the
+// pairs one round at a time (a grid barrier per round), every pair (i, j) is
+// rotated at once by its own Jacobi angle, taken from the current
+//   S = X^t H X,  R = I - X^t X   (X = I at the start):
+//   t_ij = tan of the angle that zeroes s_ij in the 2 x 2 problem
+//          [[s_ii, s_ij], [s_ij, s_jj]] (its small root, |t| <= 1), for pairs
+//          with |s_ij| > 64 eps sqrt|s_ii s_jj| (Jacobi's relative rule with a
+//          margin that leaves rounding-level couplings inside exact
+//          multiplets alone), else 0;
+//   E_ij = t_ij + r_ij / 2,  E_ii = r_ii / 2;  X <- X (I + E).
+// Only pairs with an index in the head (the kept states and the first
+// discarded ones) are rotated; the oversampling tail keeps its basis and only
+// has its orthonormality restored, so every column stays orthonormal.
+// For well separated pairs t_ij = s_ij / (s_jj - s_ii) to first order and the
+// iteration is the quadratically convergent refinement of Ogita & Aishima
+// (Japan J. Indust. Appl. Math. 35, 2018); the r_ij / 2 terms restore
+// orthonormality.  It stops when no head pair needs a rotation larger than
+// tol and |I - X^t X| is below tol;
+// if that does not happen within max_iter the host falls back to the
+// cooperative Jacobi solver.
+namespace ctm {
+namespace {
+
+__global__ void k_oa_E(int b, int head, const double* __restrict__ S, const double* __restrict__ R,
+                       double* __restrict__ E, double* __restrict__ part) {
+    __shared__ double red[32];
+    double mx = 0.0;
+    const double eps = 2.220446049250313e-16;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e % b), j = (int)(e / b);
+        double rij = R ? 0.5 * (R[e] + R[j + (size_t)b * i]) : 0.0;
+        double v = 0.5 * rij;
+        mx = fmax(mx, fabs(rij));  // orthonormality must converge for every column
+        if (i != j) {
+            double sii = S[i + (size_t)b * i], sjj = S[j + (size_t)b * j];
+            double c = 0.5 * (S[e] + S[j + (size_t)b * i]);
+            double t = 0.0;
+            if (fabs(c) > 64.0 * eps * sqrt(fabs(sii * sjj)) && c != 0.0) {
+                double tau = (sjj - sii) / (2.0 * c);
+                if (fabs(tau) > 1e150) t = 0.5 / tau;
+                else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            }
+            // pairs inside the oversampling tail (both indices >= head) only
+            // need some orthonormal basis of their span: they are not rotated
+            const bool in_head = (i < head) || (j < head);
+            if (!in_head) t = 0.0;
+            v += t;
+            mx = fmax(mx, fabs(t));
+        }
+        E[e] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) part[blockIdx.x] = mx;
+    }
+}
+
+// max over the partial maxima -> ctl->oa_maxE
+__global__ void k_oa_finish(int nparts, const double* __restrict__ part, DevCtl* ctl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mx = 0.0;
+    for (int i = 0; i < nparts; ++i) mx = fmax(mx, part[i]);
+    ctl->oa_maxE = mx;
+}
+
+__global__ void k_identity_minus(int b, double* __restrict__ G) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e % b), j = (int)(e / b);
+        G[e] = (i == j ? 1.0 : 0.0) - G[e];
+    }
+}
+
+__global__ void k_copy_sym(int b, const double* __restrict__ H, int ldh, double* __restrict__ S) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e % b), j = (int)(e / b);
+        S[e] = 0.5 * (H[i + (size_t)ldh * j] + H[j + (size_t)ldh * i]);
+    }
+}
+
+__global__ void k_add_identity(int b, const double* __restrict__ E, double* __restrict__ X) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e % b), j = (int)(e / b);
+        X[e] = (i == j ? 1.0 : 0.0) + E[e];
+    }
+}
+
+__global__ void k_diag(int b, const double* __restrict__ S, double* __restrict__ d) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b; i += gridDim.x * blockDim.x) d[i] = S[i + (size_t)b * i];
+}
+
+inline int gfor(long work) {
+    long g = (work + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > 152 * 4) g = 152 * 4;
+    return (int)g;
+}
+
+}  // namespace
+
+int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, OaWork& w, EigWork& ew,
+                  double* theta, double* Sout, int ldo, double tol, int max_iter, DevCtl* ctl, DevCtl* hctl,
+                  int* nlaunch) {
+    const long bb = (long)b * b;
+    const int nparts = gfor(bb);
+    // split-K for the b x b x b products: about 150 blocks, K chunks >= 32
+    const int tiles = ((b + 63) / 64) * ((b + 63) / 64);
+    int splits = std::max(1, std::min(std::min(w.max_splits, (2 * 152 + tiles - 1) / tiles), std::max(1, b / 32)));
+    int nk = 0;
+    // X = I + E(H): the first simultaneous rotation, from S = H and R = 0
+    k_copy_sym<<<gfor(bb), 256, 0, st>>>(b, H, ldh, w.S);
+    k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, nullptr, w.E, w.part);
+    k_add_identity<<<gfor(bb), 256, 0, st>>>(b, w.E, w.X);
+    nk += 3;
+    bool conv = false;
+    int it = 1;
+    for (; it <= max_iter; ++it) {
+        // S = X^t (H X), R = I - X^t X
+        nk += gemm_f64(st, false, false, b, b, b, 1.0, H, ldh, w.X, b, 0.0, w.W1, b, nullptr, splits, w.gpart);
+        nk += gemm_f64(st, true, false, b, b, b, 1.0, w.X, b, w.W1, b, 0.0, w.S, b, nullptr, splits, w.gpart);
+        nk += gemm_f64(st, true, false, b, b, b, 1.0, w.X, b, w.X, b, 0.0, w.R, b, nullptr, splits, w.gpart);
+        k_identity_minus<<<gfor(bb), 256, 0, st>>>(b, w.R);
+        k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, w.R, w.E, w.part);
+        k_oa_finish<<<1, 32, 0, st>>>(nparts, w.part, ctl);
+        nk += 3;
+        cudaMemcpyAsync(&hctl->oa_maxE, &ctl->oa_maxE, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        const double mx = hctl->oa_maxE;
+        if (!(mx <= 0.5)) break;  // not a small correction any more: give up
+        // X <- X + X E (on convergence this only restores orthonormality)
+        cudaMemcpyAsync(w.W1, w.X, sizeof(double) * bb, cudaMemcpyDeviceToDevice, st);
+        nk += gemm_f64(st, false, false, b, b, b, 1.0, w.W1, b, w.E, b, 1.0, w.X, b, nullptr, splits, w.gpart);
+        if (mx <= tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (nlaunch) *nlaunch += nk;
+    if (!conv) return -1;
+    // Ritz values: the diagonal of the last S; vectors X; sort by |theta|
+    k_diag<<<gfor(b), 256, 0, st>>>(b, w.S, ew.diag);
+    k_rank_ritz<<<gfor(b), 256, 0, st>>>(b, ew.diag, ew.rank, theta);
+    k_gather_ritz<<<gfor(bb), 256, 0, st>>>(b, b, ew.rank, w.X, Sout, ldo);
+    if (nlaunch) *nlaunch += 3;
+    return it;
 }
 
 }  // namespace ctm

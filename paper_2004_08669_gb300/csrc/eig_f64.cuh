@@ -20,7 +20,28 @@ struct EigWork {
     int* gkind;     // b
 };
 
+// Scratch of the warm-start Rayleigh-Ritz refinement (device, b x b each).
+struct OaWork {
+    double* X;
+    double* W1;
+    double* S;
+    double* R;
+    double* E;
+    double* part;   // partial maxima (<= 608)
+    double* gpart;  // split-K partial sums, max_splits b^2
+    int max_splits;
+};
+
 int coop_grid_limit(const void* fn, int block, size_t smem);
+
+// Warm-start Rayleigh-Ritz by simultaneous Jacobi rotations (Ogita-Aishima
+// refinement from X = I).  Returns iterations used, or -1 when it did not
+// converge (largest rotation <= tol) in max_iter iterations: fall back to Jacobi.
+// head: columns (in the warm order) whose Ritz pairs must converge; the rest
+// are the oversampling tail, rotated with damped angles and not tested.
+int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, OaWork& w, EigWork& ew,
+                  double* theta, double* Sout, int ldo, double tol, int max_iter, DevCtl* ctl, DevCtl* hctl,
+                  int* nlaunch);
 
 // Eigenpairs of the symmetric n x n matrix H (FP64 cyclic Jacobi, round-robin
 // parallel order), sorted by |theta| descending: theta (n), Sout (n x n, ldo).
@@ -30,8 +51,8 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);
 
-// X = L^{-1} for lower-triangular L.
-void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx);
+// X = L^{-1} for lower-triangular L; scratch: n x n doubles (L^t).
+void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch);
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
                const double* theta, double* res);

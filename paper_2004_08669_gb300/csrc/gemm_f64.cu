@@ -181,7 +181,119 @@ __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
     }
 }
 
+// ---- the same contraction in other arithmetic: plain FP32, or double-float
+// (an unevaluated sum hi + lo of two floats, ~48 significant bits; Dekker's
+// products and Knuth's sums) for the FP64-emulating form, where GB300's FP32
+// pipe is 64 times faster than its FP64 pipe.
+struct ArF32 {
+    using T = float;
+    __device__ static T load(double x) { return (float)x; }
+    __device__ static double store(T a) { return (double)a; }
+    __device__ static T mul(T a, T b) { return a * b; }
+    __device__ static T fma(T a, T b, T c) { return fmaf(a, b, c); }
+    __device__ static T zero() { return 0.f; }
+};
+
+struct ArDF {
+    using T = float2;  // x = hi, y = lo
+    __device__ static T quick(float s, float e) {
+        float h = s + e;
+        return make_float2(h, e - (h - s));
+    }
+    __device__ static T load(double x) {
+        float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    }
+    __device__ static double store(T a) { return (double)a.x + (double)a.y; }
+    __device__ static T mul(T a, T b) {
+        float p = a.x * b.x;
+        float e = fmaf(a.x, b.x, -p);
+        e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+        return quick(p, e);
+    }
+    __device__ static T add(T a, T b) {
+        float s = a.x + b.x;
+        float bb = s - a.x;
+        float e = (a.x - (s - bb)) + (b.x - bb);
+        e += a.y + b.y;
+        return quick(s, e);
+    }
+    __device__ static T fma(T a, T b, T c) { return add(mul(a, b), c); }
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+};
+
+template <class Ar>
+__global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, const double* __restrict__ E,
+                               const double* __restrict__ E1, const int* __restrict__ live_ptr) {
+    using T = typename Ar::T;
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    T* sh = (T*)sh_raw;
+    const int q2 = q * q;
+    const int nb = max(1, (int)blockDim.x / q2);
+    T* sE = sh;
+    T* sE1 = sE + q2;
+    T* G = sE1 + q2;
+    T* T1 = G + nb * q2;
+    for (int e = threadIdx.x; e < q2; e += blockDim.x) {
+        sE[e] = Ar::load(E[e]);
+        sE1[e] = Ar::load(E1[e]);
+    }
+    const int live = min(*live_ptr, m);
+    const long nblk = (long)live * live;
+    const int jb = threadIdx.x / q2;
+    const int el = threadIdx.x - jb * q2;
+    const bool act = jb < nb;
+    const int i = el % q, j = el / q;
+    __syncthreads();
+    for (long base = (long)blockIdx.x * nb; base < nblk; base += (long)gridDim.x * nb) {
+        long blk = base + jb;
+        bool ok = act && blk < nblk;
+        size_t off = 0;
+        if (ok) {
+            int g = (int)(blk % live), gp = (int)(blk / live);
+            off = (size_t)q * g + (size_t)ldx * ((size_t)q * gp);
+            G[jb * q2 + el] = Ar::mul(Ar::load(X[off + i + (size_t)ldx * j]), sE1[el]);
+        }
+        __syncthreads();
+        if (ok) {
+            T s = Ar::zero();
+            for (int k = 0; k < q; ++k) s = Ar::fma(G[jb * q2 + i + q * k], sE[k + q * j], s);
+            T1[jb * q2 + el] = s;
+        }
+        __syncthreads();
+        if (ok) {
+            T s = Ar::zero();
+            for (int k = 0; k < q; ++k) s = Ar::fma(sE[i + q * k], T1[jb * q2 + k + q * j], s);
+            X[off + i + (size_t)ldx * j] = Ar::store(Ar::mul(sE[el], s));
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, const double* E, const double* E1,
+                  const int* live) {
+    if (arith == 0) {
+        wcontract_f64(st, m, q, X, ldx, E, E1, live);
+        return;
+    }
+    int q2 = q * q;
+    int threads = q2 <= 256 ? 256 : ((q2 + 31) / 32) * 32;
+    int nb = threads / q2;
+    if (nb < 1) nb = 1;
+    long nblk = (long)m * m;
+    long grid = (nblk + nb - 1) / nb;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    if (arith == 1) {
+        size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float);
+        k_wcontract_ar<ArF32><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live);
+    } else {
+        size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float2);
+        k_wcontract_ar<ArDF><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live);
+    }
+}
 
 int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, double alpha,
              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,

@@ -1,0 +1,427 @@
+// oz_gemm.cu -- FP64-accurate GEMM emulated on the bf16 tensor cores
+// (Ozaki-style error-free splitting), for the FP64-equivalent mixed form.
+//
+//   D (M x N, column-major FP64) = A . B^t,  A: M x K, B: N x K (FP64, rows
+//   contiguous in K after k_oz_split).
+//
+// Splitting (k_oz_split): each row r of an operand is scaled by a power of
+// two 2^-e_r so that |x| < 1, rounded to a 7s-bit fixed-point integer X, and
+// written as s balanced base-2^7 digits, X = sum_i d_i 2^{7(s-i)}, with
+// |d_1| <= 128 and |d_i| <= 64 after: every digit is an integer that bf16
+// holds exactly.  The digit planes are stored stacked (plane i, row r) as
+// K-major bf16 with leading dimension ld.
+//
+// Products (k_oz_gemm): A.B^t = 2^{e_r + f_c} sum_{i,j} 2^{-7(i+j)} A_i B_j^t.
+// Pairs with i + j <= s + 1 are kept; pairs of equal t = i + j share one
+// TMEM accumulator.  Over a K-chunk of 512 the FP32 accumulation of every
+// group is exact (all partial sums are integers below 2^24 for s <= 6), so
+// after each chunk the four epilogue warps read the groups back, scale them
+// by 2^{-7t} (exact) and add them into a double-float (hi, lo) accumulator
+// per output element; the end result is written in FP64.  A producer warp
+// streams all digit planes of a 32-wide K-tile per stage (3-stage TMA ring,
+// 64-byte swizzle) and an MMA warp issues the tcgen05.mma of every pair.
+// All mbarrier waits are bounded (error flag, TMEM freed, return).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ctm_internal.cuh"
+#include "oz_gemm.cuh"
+
+namespace ctm {
+
+namespace {
+
+constexpr int kOzBM = 128;
+constexpr int kOzBN = 64;
+constexpr int kOzKT = 32;       // K per stage (64 bytes of bf16: one 64B-swizzle row)
+constexpr int kOzChunk = 512;   // K per exact FP32 accumulation
+constexpr long kOzSpin = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    for (long i = 0; i < kOzSpin; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(20);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// K-major, 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// (hi, lo) += v with an error-free sum (Knuth's TwoSum).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+    float s = hi + v;
+    float bp = s - hi;
+    float e = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += e;
+}
+
+// One warp per operand row: exponent of the row maximum, then the digit planes.
+// src(r, k) = src[r rs + k ks] (* scale[k]); planes[(i Rp + r) ld + k].
+__global__ void k_oz_split(int R, int K, int s, const double* __restrict__ src, long rs, long ks,
+                           const double* __restrict__ scale, __nv_bfloat16* __restrict__ planes, int Rp, int ld,
+                           int* __restrict__ rexp) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < R; r += nwarps) {
+        const double* row = src + rs * r;
+        int emax = -2000;
+        for (int k = lane; k < K; k += 32) {
+            double v = row[ks * k];
+            if (scale) v *= scale[k];
+            uint64_t bits = (uint64_t)__double_as_longlong(v);
+            int E = (int)((bits >> 52) & 0x7FF);
+            if ((bits & 0x7FFFFFFFFFFFFFFFull) != 0) emax = max(emax, E == 0 ? 1 : E);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        // value = m * 2^(E - 1075) with m < 2^53, so |value| < 2^(E - 1022) = 2^e_r
+        const int er = (emax == -2000) ? 0 : emax - 1022;
+        if (lane == 0) rexp[r] = er;
+        const int fbits = 7 * s;
+        for (int k = lane; k < ld; k += 32) {
+            long long X = 0;
+            if (k < K && emax != -2000) {
+                double v = row[ks * k];
+                if (scale) v *= scale[k];
+                uint64_t bits = (uint64_t)__double_as_longlong(v);
+                int E = (int)((bits >> 52) & 0x7FF);
+                uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+                if (E != 0) mant |= (1ull << 52);
+                else E = 1;
+                // X = round(|v| 2^(fbits - er)) = round(mant 2^(E - 1075 - er + fbits))
+                int sh = E - 1075 - er + fbits;
+                uint64_t mag;
+                if (sh >= 0) mag = mant << sh;  // sh <= fbits - 53 < 11 here
+                else if (sh > -64) mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+                else mag = 0;
+                X = (long long)mag;
+                if (bits >> 63) X = -X;
+            }
+            for (int i = 0; i < s; ++i) {
+                int shf = 7 * (s - 1 - i);
+                long long d = (shf > 0) ? ((X + (1ll << (shf - 1))) >> shf) : X;
+                X -= d * (1ll << shf);
+                planes[((size_t)i * Rp + r) * ld + k] = __float2bfloat16_rn((float)d);
+            }
+        }
+    }
+}
+
+// Stages of the TMA ring: all S digit planes of A (8 KB each) and B (4 KB
+// each) per stage; three stages fit in shared memory up to S = 6.
+template <int S>
+struct OzStages {
+    static constexpr int value = (S <= 6) ? 3 : 2;
+};
+
+template <int S>
+__global__ void __launch_bounds__(192, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
+              int Mp, int Np, const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ D, int ldd,
+              int* err) {
+    constexpr int kOzStages = OzStages<S>::value;
+    constexpr int NG = S;                           // groups t = 2 .. S + 1
+    constexpr uint32_t A_PLANE = kOzBM * kOzKT * 2;  // 8 KB
+    constexpr uint32_t B_PLANE = kOzBN * kOzKT * 2;  // 4 KB
+    constexpr uint32_t STAGE = S * (A_PLANE + B_PLANE);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[kOzStages];
+    __shared__ __align__(8) uint64_t empty_bar[kOzStages];
+    __shared__ __align__(8) uint64_t acc_full;
+    __shared__ __align__(8) uint64_t acc_empty;
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kOzBM, n0 = blockIdx.y * kOzBN;
+    const int nk = (K + kOzKT - 1) / kOzKT;
+    const int kt_per_chunk = kOzChunk / kOzKT;
+    const int nchunk = (nk + kt_per_chunk - 1) / kt_per_chunk;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 128);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 4) {
+        // ---- producer: all digit planes of one K-tile per stage
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < nk; ++kt) {
+                int st = kt % kOzStages;
+                if (kt >= kOzStages && !mbar_wait(&empty_bar[st], ((kt / kOzStages) - 1) & 1, err)) break;
+                uint8_t* base = smem + st * STAGE;
+                mbar_expect_tx(&full_bar[st], STAGE);
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    tma_load_2d(base + i * A_PLANE, &mapA, &full_bar[st], kt * kOzKT, i * Mp + m0);
+                    tma_load_2d(base + S * A_PLANE + i * B_PLANE, &mapB, &full_bar[st], kt * kOzKT, i * Np + n0);
+                }
+                ++issued;
+            }
+            // own copies must land before the CTA may exit
+            for (int kt = (issued > kOzStages ? issued - kOzStages : 0); kt < issued; ++kt)
+                mbar_wait(&full_bar[kt % kOzStages], (kt / kOzStages) & 1, err);
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
+                                   ((uint32_t)(kOzBM >> 4) << 24);
+            bool ok = true;
+            for (int c = 0; c < nchunk && ok; ++c) {
+                if (c > 0 && !mbar_wait(&acc_empty, (c - 1) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int kt0 = c * kt_per_chunk, kt1 = min(nk, kt0 + kt_per_chunk);
+                for (int kt = kt0; kt < kt1; ++kt) {
+                    int st = kt % kOzStages;
+                    if (!mbar_wait(&full_bar[st], (kt / kOzStages) & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_u32(smem + st * STAGE);
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+#pragma unroll
+                        for (int j = 0; j < S; ++j) {
+                            if (i + j > S - 1) continue;  // keep i + j <= s + 1 (1-based)
+                            const int g = i + j;          // group index 0 .. S - 1
+                            const uint32_t a0 = base + i * A_PLANE;
+                            const uint32_t b0 = base + S * A_PLANE + j * B_PLANE;
+#pragma unroll
+                            for (int kk = 0; kk < kOzKT / 16; ++kk) {
+                                // the first MMA of a group in this chunk overwrites its accumulator
+                                const bool first = (kt == kt0) && (kk == 0) &&
+                                                   (i == (g < S ? 0 : g - (S - 1)));
+                                mma_bf16(tmem + (uint32_t)(g * kOzBN), sdesc64(a0 + 32 * kk), sdesc64(b0 + 32 * kk),
+                                         idesc, first ? 0u : 1u);
+                            }
+                        }
+                    }
+                    mma_commit(&empty_bar[st]);
+                }
+                mma_commit(&acc_full);
+            }
+            if (!ok) mma_commit(&acc_full);
+        }
+    } else {
+        // ---- epilogue warps 0..3: TMEM lanes 32 w .. 32 w + 31 = tile rows
+        float hi[kOzBN], lo[kOzBN];
+#pragma unroll
+        for (int j = 0; j < kOzBN; ++j) {
+            hi[j] = 0.f;
+            lo[j] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunk; ++c) {
+            if (!mbar_wait(&acc_full, c & 1, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int g = 0; g < NG; ++g) {
+                const float sc = exp2f(-7.0f * (float)(g + 2));
+#pragma unroll
+                for (int cb = 0; cb < kOzBN; cb += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kOzBN + cb), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) df_add(hi[cb + j], lo[cb + j], v[j] * sc);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acc_empty);
+        }
+        const int row = m0 + warp * 32 + lane;
+        if (ok && row < M) {
+            const int er = eA[row];
+#pragma unroll
+            for (int j = 0; j < kOzBN; ++j) {
+                const int col = n0 + j;
+                if (col < N) D[row + (size_t)ldd * col] = ldexp((double)hi[j] + (double)lo[j], er + eB[col]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool oz_map(CUtensorMap* map, const void* base, int K, int rows, int ld, int box_rows) {
+    auto fn = oz_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kOzKT, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int S>
+cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int Mp, int Np,
+                      const int* eA, const int* eB, double* D, int ldd, int* err) {
+    const size_t smem = 1024 + (size_t)OzStages<S>::value * S * (kOzBM * kOzKT * 2 + kOzBN * kOzKT * 2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN);
+    k_oz_gemm<S><<<grid, 192, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int oz_rows_pad(int R, int box) { return ((R + box - 1) / box) * box; }
+int oz_ld(int K) { return ((K + 63) / 64) * 64; }
+
+size_t oz_operand_bytes(int R, int K, int s, bool is_a) {
+    int Rp = oz_rows_pad(R, is_a ? kOzBM : kOzBN);
+    return (size_t)s * Rp * oz_ld(K) * 2;
+}
+
+void oz_split(cudaStream_t st, int R, int K, int s, const double* src, int lds, const double* scale, void* planes,
+              bool is_a, int* rexp) {
+    oz_split_strided(st, R, K, s, src, lds, 1, scale, planes, is_a, rexp);
+}
+
+void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, long rs, long ks,
+                      const double* scale, void* planes, bool is_a, int* rexp) {
+    int Rp = oz_rows_pad(R, is_a ? kOzBM : kOzBN);
+    int warps = std::min(R, 152 * 32);
+    int grid = (warps * 32 + 255) / 256;
+    if (grid < 1) grid = 1;
+    k_oz_split<<<grid, 256, 0, st>>>(R, K, s, src, rs, ks, scale, (__nv_bfloat16*)planes, Rp, oz_ld(K), rexp);
+}
+
+cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
+                    const void* Bplanes, const int* eB, double* D, int ldd, int* err) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (s < 3 || s > 7) return cudaErrorInvalidValue;
+    const int Mp = oz_rows_pad(M, kOzBM), Np = oz_rows_pad(N, kOzBN), ld = oz_ld(K);
+    CUtensorMap ma, mb;
+    if (!oz_map(&ma, Aplanes, K, s * Mp, ld, kOzBM) || !oz_map(&mb, Bplanes, K, s * Np, ld, kOzBN))
+        return cudaErrorInvalidValue;
+    switch (s) {
+        case 3: return oz_launch<3>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+        case 4: return oz_launch<4>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+        case 5: return oz_launch<5>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+        case 6: return oz_launch<6>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+        default: return oz_launch<7>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+    }
+}
+
+}  // namespace ctm

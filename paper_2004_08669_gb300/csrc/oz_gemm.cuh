@@ -1,0 +1,27 @@
+// oz_gemm.cuh -- host entry points of the FP64-emulating tensor-core GEMM.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace ctm {
+
+// Bytes of the stacked digit planes of an operand with R rows of length K
+// and s digits (A role: rows padded to 128; B role: to 64).
+size_t oz_operand_bytes(int R, int K, int s, bool is_a);
+
+// Split rows src(r, k) = src[k + lds r] (* scale[k]) into s bf16 digit planes
+// and one power-of-two exponent per row (rexp, R ints).
+void oz_split(cudaStream_t st, int R, int K, int s, const double* src, int lds, const double* scale, void* planes,
+              bool is_a, int* rexp);
+
+// Same with general strides: src(r, k) = src[r rs + k ks] (* scale[k]).
+void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, long rs, long ks,
+                      const double* scale, void* planes, bool is_a, int* rexp);
+
+// D (M x N, column-major FP64, ldd) = A . B^t from split operands (A: M rows,
+// B: N rows, length K, s digits, 3 <= s <= 7).  *err (device) set on timeout.
+cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
+                    const void* Bplanes, const int* eB, double* D, int ldd, int* err);
+
+}  // namespace ctm

@@ -38,7 +38,7 @@ class ctm_step_info(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("delta", ctypes.c_double), ("S_E", ctypes.c_double),
                 ("residual", ctypes.c_double), ("m_eff", ctypes.c_int), ("live_dim", ctypes.c_int),
                 ("subspace_iters", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int), ("steps", ctypes.c_int),
-                ("converged", ctypes.c_int)]
+                ("converged", ctypes.c_int), ("rr_refined", ctypes.c_longlong), ("rr_jacobi", ctypes.c_longlong)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,10 +89,10 @@ def _load():
         "ctm_symeig_workspace_size": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
         "ctm_symeig_noalloc": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
-        "ctm_contract_workspace_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        "ctm_contract_workspace_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_size_t)],
-        "ctm_contract": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
-                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+        "ctm_contract": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                         ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                          ctypes.c_size_t, ctypes.c_void_p],
         "ctm_symeig": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                        ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
@@ -281,7 +281,7 @@ def ctm_symeig_noalloc(A, max_sweeps: int = 0):
     return ev, vt.t(), status
 
 
-def ctm_contract(A, B, prec: str = "fp64"):
+def ctm_contract(A, B, prec: str = "fp64", ozaki_slices: int = 0):
     """D = A^t B for FP64 torch CUDA tensors A (K x M) and B (K x N) through
     the library's contraction kernel in the given precision."""
     import torch
@@ -293,11 +293,11 @@ def ctm_contract(A, B, prec: str = "fp64"):
     Bc = B.t().contiguous()
     Dt = torch.empty(N, M, dtype=torch.float64, device=A.device)  # column-major M x N
     nb = ctypes.c_size_t(0)
-    _check(lib.ctm_contract_workspace_size(p, M, N, K, ctypes.byref(nb)))
+    _check(lib.ctm_contract_workspace_size(p, int(ozaki_slices), M, N, K, ctypes.byref(nb)))
     ws = torch.empty(nb.value, dtype=torch.uint8, device=A.device)
     st = torch.cuda.current_stream(A.device).cuda_stream
-    _check(lib.ctm_contract(p, M, N, K, Ac.data_ptr(), K, Bc.data_ptr(), K, Dt.data_ptr(), M, ws.data_ptr(),
-                            ws.numel(), ctypes.c_void_p(st)))
+    _check(lib.ctm_contract(p, int(ozaki_slices), M, N, K, Ac.data_ptr(), K, Bc.data_ptr(), K, Dt.data_ptr(), M,
+                            ws.data_ptr(), ws.numel(), ctypes.c_void_p(st)))
     return Dt.t()
 
 
