@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
+    ap.add_argument("--gate-steps", type=int, default=20,
+                    help="steps of the mixed-vs-FP64 comparison from the timed state (0: skip)")
     return ap.parse_args()
 
 
@@ -258,7 +260,7 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
     dom = max(kern, key=lambda k: kern[k]["ms"])
     # roofline of the contraction kernel of this mode (the dominant one in the
     # FP64 form): algorithmic FLOPs of its launches / their event-timed duration
-    ck = "gemm_f64" if prec == "fp64" else "tc_gemm"
+    ck = {"fp64": "gemm_f64", "ozaki64": "oz_gemm"}.get(prec, "tc_gemm")
     d = kern[ck]
     achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
     workload = f"dodecahedron q=20 m={m} T={args.T} {prec}"
@@ -280,6 +282,34 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
            "kernels_ms_per_step": {k: round(v["ms"] / timed_steps, 3) for k, v in kern.items()},
            "workload": workload}
     return g, res
+
+
+def accuracy_gate(args, blob, local):
+    """The mixed forms against the FP64 form on the timed workload: load the
+    same checkpointed state into one handle per form, step them side by side,
+    and compare the per-step free energy f = -(T/2) ln kappa."""
+    import math
+
+    from paper_2004_08669_gb300 import ctm, workloads as W
+    m = args.m
+    beta = 1.0 / args.T
+    runs = {}
+    for prec in ("fp64", "ozaki64", "tf32", "bf16"):
+        g = ctm.CTMRG(W.dodecahedron(), m, beta, prec=prec, device=f"cuda:{local}",
+                      max_subspace_iters=args.subspace_iters)
+        g.load(blob)
+        fs = []
+        for _ in range(args.gate_steps):
+            _, info, _ = g.step(1)
+            fs.append(-0.5 / beta * math.log(info["kappa"]))
+        runs[prec] = fs
+        g.close()
+    ref = runs["fp64"]
+    res = {"steps": args.gate_steps, "from": "checkpoint of the timed run", "threshold": 1e-10}
+    for prec in ("ozaki64", "tf32", "bf16"):
+        d = max(abs(a - b) / abs(b) for a, b in zip(runs[prec], ref))
+        res[prec] = {"max_rel_df": d, "passes": d <= 1e-10}
+    return res
 
 
 def run_ours(args):
@@ -329,14 +359,20 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, args)
+    gate = None
+    if args.gate_steps > 0 and rank == 0:
+        gate = accuracy_gate(args, blob, local)
     g.close()
     others = {}
     for p in modes[1:]:
-        g2, r2 = run_mode(args, p, local, world, barrier, args.steps)
-        g2.close()
-        others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "gpu_launches", "subspace_iters_mean",
-                                        "jacobi_sweeps_mean", "rayleigh_ritz_paths", "kernels_ms_per_step",
-                                        "clocks")}
+        try:
+            g2, r2 = run_mode(args, p, local, world, barrier, args.steps)
+            g2.close()
+            others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "gpu_launches",
+                                            "subspace_iters_mean", "jacobi_sweeps_mean", "rayleigh_ritz_paths",
+                                            "kernels_ms_per_step", "clocks")}
+        except Exception as e:  # a failing form must not lose the others' numbers
+            others[p] = {"error": f"{type(e).__name__}: {e}"}
     out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if primary == "fp64" else primary, "data": "synthetic",
@@ -353,6 +389,8 @@ def run_ours(args):
         out["other_modes"] = others
     if cpu is not None:
         out["cpu_baseline"] = cpu
+    if gate is not None:
+        out["accuracy_gate"] = gate
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

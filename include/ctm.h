@@ -66,7 +66,7 @@ typedef struct {
     double beta;              /* inverse temperature 1/T, finite, >= 0              */
     int boundary_spin;        /* fixed boundary spin "s = 1" of Sec. II (0-based)   */
     ctm_precision prec;
-    int ozaki_slices;         /* slices per operand for CTM_OZAKI64 (0: default)    */
+    int ozaki_slices;         /* digit planes per operand for CTM_OZAKI64 (0: 7)    */
     double tol_spectrum;      /* convergence of the step loop (default 1e-12)      */
     int max_steps;            /* cap used by ctm_run (default 5000)                 */
     int block_extra;          /* subspace width b = m + block_extra (0: default)    */
@@ -92,6 +92,10 @@ typedef struct {
     int converged;         /* delta < tol_spectrum                              */
     long long rr_refined;  /* Rayleigh-Ritz solves by simultaneous rotations   */
     long long rr_jacobi;   /* Rayleigh-Ritz solves by the cooperative Jacobi   */
+    int rr_fail_reason;    /* last refinement: 0 ok, 1 coupled non-doublet pair,
+                              2 large rotation, 3 iteration cap, 4 triplet     */
+    int rr_last_iter;      /* its iterations                                   */
+    double rr_last_max;    /* its last largest rotation / orthonormality defect */
 } ctm_step_info;
 
 /* Observables of the current state (Eq. 4-6 and the free energy). */

@@ -53,7 +53,7 @@ struct Layout {
         off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
         off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
         off_ozSA, off_ozSB, off_ozeP, off_ozeBig, off_ozeSA, off_ozeSB, off_oaX, off_oaW1, off_oaS, off_oaR, off_oaE,
-        off_oapart, total;
+        off_oapart, off_oaclus, total;
     int slices;     // digit planes of the FP64-emulating form
     int prec;       // ctm_precision
     int esz;        // operand element bytes (2 bf16, 4 tf32; 0 in FP64 form)
@@ -120,8 +120,9 @@ Layout make_layout(const ctm_config& c) {
     L.off_oaR = take(b * b * d);
     L.off_oaE = take(b * b * d);
     L.off_oapart = take(1024 * d);
+    L.off_oaclus = take(np * sizeof(int));
     L.prec = c.prec;
-    L.slices = c.ozaki_slices > 0 ? c.ozaki_slices : 6;
+    L.slices = c.ozaki_slices > 0 ? c.ozaki_slices : 7;
     L.esz = (c.prec == CTM_BF16) ? 2 : (c.prec == CTM_TF32 ? 4 : 0);
     L.ldm = ((L.m + 63) / 64) * 64;
     L.ldN = ((L.N + 63) / 64) * 64;
@@ -174,6 +175,8 @@ struct ctm_handle {
     ctm::EigWork ew;
     ctm::OaWork oa;
     long long rr_refined = 0, rr_jacobi = 0;  // Rayleigh-Ritz solves by path
+    double last_resid = 0.0;                  // last Ritz residual / |w_1|
+    int rr_fail_streak = 0;                   // consecutive failed refinements
     ctm::DevCtl* ctl;
     ctm::DevCtl* hctl = nullptr;  // pinned mirror
     // host-side iteration state
@@ -218,7 +221,7 @@ ctm_status validate(const ctm_config* c) {
     if (c->prec != CTM_FP64 && c->prec != CTM_TF32 && c->prec != CTM_BF16 && c->prec != CTM_OZAKI64)
         return fail(CTM_EUNSUPPORTED, "precision mode not built in this library");
     if (c->prec == CTM_OZAKI64 && c->ozaki_slices != 0 && (c->ozaki_slices < 3 || c->ozaki_slices > 7))
-        return fail(CTM_EINVAL, "ozaki_slices must be 0 (default 6) or in [3, 7]");
+        return fail(CTM_EINVAL, "ozaki_slices must be 0 (default 7) or in [3, 7]");
     return CTM_OK;
 }
 
@@ -230,7 +233,7 @@ ctm_config with_defaults(const ctm_config& c) {
     double floor_tol = (c.prec == CTM_BF16) ? 3e-3 : (c.prec == CTM_TF32 ? 3e-5 : 0.0);
     if (c.prec == CTM_OZAKI64) {
         // s digit planes of 7 bits: products carry about 2^(-7s) relative error
-        const int S = c.ozaki_slices > 0 ? c.ozaki_slices : 6;
+        const int S = c.ozaki_slices > 0 ? c.ozaki_slices : 7;
         floor_tol = std::max(1e-13, ldexp(1.0, -7 * S + 3));
     }
     if (r.tol_spectrum <= 0.0) r.tol_spectrum = floor_tol > 0.0 ? floor_tol : 1e-12;
@@ -243,7 +246,7 @@ ctm_config with_defaults(const ctm_config& c) {
         r.tol_cluster = (c.prec == CTM_BF16) ? 3e-2 : (c.prec == CTM_TF32 ? 3e-4 : 1e-10);
         // the digit expansion is relative to each row's largest entry, so the
         // small eigenvalues of C~ carry errors near 2^(-7s) K times |w_1|
-        if (c.prec == CTM_OZAKI64) r.tol_cluster = (c.ozaki_slices == 7) ? 1e-9 : 1e-8;
+        if (c.prec == CTM_OZAKI64) r.tol_cluster = (c.ozaki_slices == 0 || c.ozaki_slices == 7) ? 1e-9 : 1e-8;
     }
     return r;
 }
@@ -667,11 +670,21 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         // fallback.
         cudaEvent_t ja = prof_begin(h);
         int nk_rr = 0, used = -1;
-        if (!cold || it > 0)
+        // After repeated failures (a dense spectrum whose near-degenerate
+        // Ritz values are not yet separated) the refinement is only retried
+        // every 16th solve, so a failing attempt does not tax every step.
+        const bool try_refine = (!cold || it > 0) && (h->rr_fail_streak < 3 || (h->rr_jacobi % 16) == 0);
+        if (try_refine) {
             used = ctm::rr_refine_f64(h->st, b, std::min(b, m + 2), h->H, b, h->oa, h->ew, h->theta, h->Sb, b, 1e-13,
                                       8, h->ctl, h->hctl, &nk_rr);
+            h->rr_fail_streak = used < 0 ? h->rr_fail_streak + 1 : 0;
+        }
         if (used < 0) {
-            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
+            // while the subspace itself is only resid-accurate, polishing its
+            // Ritz vectors further is wasted: stop the sweeps at 1% of it
+            const double rel = (h->last_resid > 0.0 && h->last_resid < 1.0)
+                                   ? std::min(1e-6, 0.01 * h->last_resid) : 0.0;
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, rel));
             nk_rr += 4;
             ++h->rr_jacobi;
         } else {
@@ -695,6 +708,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         CTM_CUDA(cudaGetLastError());
         ctm_status s = sync_ctl(h);
         if (s != CTM_OK) return s;
+        h->last_resid = h->hctl->resid;
         if (h->hctl->jac_status == 2 || h->hctl->chol_status == 2)
             return fail(CTM_ETIMEOUT, "a device-side barrier timed out");
         if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the eigen stage");
@@ -798,6 +812,9 @@ ctm_status step_once(ctm_handle* h) {
     I.converged = (h->hctl->delta < h->cfg.tol_spectrum) ? 1 : 0;
     I.rr_refined = h->rr_refined;
     I.rr_jacobi = h->rr_jacobi;
+    I.rr_fail_reason = h->oa.fail_reason;
+    I.rr_last_iter = h->oa.last_iter;
+    I.rr_last_max = h->oa.last_max;
     return conv ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
@@ -904,6 +921,7 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
     h->oa.R = D(L.off_oaR);
     h->oa.E = D(L.off_oaE);
     h->oa.part = D(L.off_oapart);
+    h->oa.clus = (int*)(h->ws + L.off_oaclus);
     h->oa.gpart = D(L.off_part);
     h->oa.max_splits = L.splits;
     h->mfull = (int*)(h->ws + L.off_mfull);
@@ -1231,6 +1249,8 @@ ctm_status ctm_set_state(ctm_handle* h, const double* P, const double* omega, in
     h->live = live;
     h->warm = false;
     h->warm_live = -1;
+    h->last_resid = 0.0;
+    h->rr_fail_streak = 0;
     return CTM_OK;
 }
 

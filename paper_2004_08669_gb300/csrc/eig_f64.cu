@@ -7,11 +7,13 @@
 //   Z = V S;  T = Y S;  residual ||T_i - theta_i Z_i||;
 //   V <- orth([T_i / theta_i or Z_i]) by (shifted) Cholesky QR.
 // The kernels below are the small dense FP64 pieces: a parallel-order
-// two-sided Jacobi eigensolver (Golub & Van Loan 8.5, round-robin ordering),
-// a blocked Cholesky factorisation, a triangular inverse, the residual test
-// with the multiplet-aware truncation rule, and the gauge alignment of Ritz
-// vectors to the previous step's (sign per singlet, orthogonal Procrustes per
-// doublet) that keeps the renormalised basis consistent between steps.
+// two-sided Jacobi eigensolver (Golub & Van Loan 8.5, round-robin ordering)
+// for cold starts, simultaneous Jacobi rotations for warm starts (end of
+// file), a blocked Cholesky factorisation, a triangular inverse, the
+// residual test with the multiplet-aware truncation rule, and the gauge
+// alignment of Ritz vectors to the previous step's (sign per singlet,
+// orthogonal Procrustes per doublet) that keeps the renormalised basis
+// consistent between steps.
 #include "ctm_internal.cuh"
 #include "eig_f64.cuh"
 
@@ -38,6 +40,33 @@ struct Rot {
     double c, s, t;
     bool on;
 };
+
+// Rotation of the pair (p, q): the tangent t of the angle that zeroes a_pq is
+// taken in FP32 (an approximate angle only reduces a_pq by ~1e-7 instead of
+// zeroing it; Jacobi's convergence is unaffected), while c = 1/sqrt(1 + t^2)
+// is made FP64-accurate from an FP32 reciprocal square root by two
+// Newton-Raphson steps y <- y (3 - x y^2) / 2, and s = t c: the rotation is
+// orthogonal to FP64 rounding.  This keeps FP64 square roots and divisions,
+// which are slow on this part, out of every round.
+__device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, double eps, double floor_abs) {
+    Rot R{1.0, 0.0, 0.0, false};
+    if (apq == 0.0) return R;
+    if (fabs(apq) <= fmax(eps * sqrt(fabs(app * aqq)), floor_abs)) return R;
+    float tau = (float)((aqq - app) / (2.0 * apq));
+    float tf;
+    if (fabsf(tau) > 1e18f) tf = 0.5f / tau;
+    else tf = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+    double t = (double)tf;
+    double x = 1.0 + t * t;
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    R.c = y;
+    R.s = t * y;
+    R.t = t;
+    R.on = true;
+    return R;
+}
 
 __device__ __forceinline__ Rot rot_of(const double* A, int ld, int p, int q, double eps,
                                       double floor_abs) {
@@ -99,10 +128,11 @@ __global__ void k_jacobi(int n, int npad, double* A0, double* A1,
             for (int k = threadIdx.x; k < half; k += blockDim.x) {
                 int p, q;
                 rr_pair(r, k, npad, p, q);
-                Rot R = rot_of(Ac, npad, p, q, eps, floor_abs);
+                Rot R = rot_fast(__ldcg(Ac + p + (size_t)npad * p), __ldcg(Ac + q + (size_t)npad * q),
+                                 __ldcg(Ac + p + (size_t)npad * q), eps, floor_abs);
                 rc[k] = R.c;
                 rs[k] = R.s;
-                rt[k] = R.on ? R.t : 0.0;
+                rt[k] = R.on ? 1.0 : 0.0;
                 if (R.on && blockIdx.x == 0) atomicAdd(&ctl->rot_count[sweep], 1);
             }
             __syncthreads();
@@ -119,10 +149,15 @@ __global__ void k_jacobi(int n, int npad, double* A0, double* A1,
                         double aqq = __ldcg(Ac + q + (size_t)npad * q);
                         double apq = __ldcg(Ac + p + (size_t)npad * q);
                         if (ona) {
-                            An[p + (size_t)npad * p] = app - rt[ka] * apq;
-                            An[q + (size_t)npad * q] = aqq + rt[ka] * apq;
-                            An[p + (size_t)npad * q] = 0.0;
-                            An[q + (size_t)npad * p] = 0.0;
+                            // J^t [[app, apq], [apq, aqq]] J with J = [[c, s], [-s, c]]
+                            double x_pp = ca * app - sa * apq, x_pq = ca * apq - sa * aqq;
+                            double x_qp = sa * app + ca * apq, x_qq = sa * apq + ca * aqq;
+                            double npp = ca * x_pp - sa * x_pq, nqq = sa * x_qp + ca * x_qq;
+                            double npq = 0.5 * ((sa * x_pp + ca * x_pq) + (ca * x_qp - sa * x_qq));
+                            An[p + (size_t)npad * p] = npp;
+                            An[q + (size_t)npad * q] = nqq;
+                            An[p + (size_t)npad * q] = npq;
+                            An[q + (size_t)npad * p] = npq;
                         } else {
                             An[p + (size_t)npad * p] = app;
                             An[q + (size_t)npad * q] = aqq;
@@ -580,7 +615,7 @@ int coop_grid_limit(const void* fn, int block, size_t smem) {
 }
 
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
-                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl) {
+                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol) {
     int npad = n + (n & 1);
     if (npad < 2) npad = 2;
     k_jacobi_init<<<grid_for((size_t)npad * npad), 256, 0, st>>>(n, npad, H, ldh, w.A0, w.S);
@@ -601,7 +636,7 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     }
     if (grid > limit) grid = limit;
     if (grid < 1) grid = 1;
-    double eps = 2.220446049250313e-16, floor_abs = 0.0;
+    double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16, floor_abs = 0.0;
     double* A0 = w.A0;
     double* A1 = w.A1;
     double* S = w.S;
@@ -685,6 +720,11 @@ void identity_block(cudaStream_t st, int N, int b, double* V, int ld) {
 // Only pairs with an index in the head (the kept states and the first
 // discarded ones) are rotated; the oversampling tail keeps its basis and only
 // has its orthonormality restored, so every column stays orthonormal.
+// Pairs inside a multiplet are strongly coupled relative to their tiny gap
+// (the other rotations mix them at second order); rotating them by their
+// O(1) angle all at once would break the first-order scheme, so adjacent
+// strongly coupled pairs are left alone and diagonalised exactly (one 2 x 2
+// Jacobi rotation each, disjoint, hence commuting) after convergence.
 // For well separated pairs t_ij = s_ij / (s_jj - s_ii) to first order and the
 // iteration is the quadratically convergent refinement of Ogita & Aishima
 // (Japan J. Indust. Appl. Math. 35, 2018); the r_ij / 2 terms restore
@@ -695,9 +735,18 @@ void identity_block(cudaStream_t st, int N, int b, double* V, int ld) {
 namespace ctm {
 namespace {
 
+// E for one refinement step.  Head pairs (an index below `head`) whose
+// coupling is small against their diagonal gap, |s_ij| < gap / 10, get the
+// Jacobi tangent of their 2 x 2 problem; an adjacent pair that is strongly
+// coupled (an exact or near multiplet) is marked in clus[min(i, j)] and left
+// for an exact rotation at the end; any other strongly coupled pair marks the
+// refinement as failed (part[gridDim.x] = 1).
 __global__ void k_oa_E(int b, int head, const double* __restrict__ S, const double* __restrict__ R,
-                       double* __restrict__ E, double* __restrict__ part) {
+                       double* __restrict__ E, double* __restrict__ part, int* __restrict__ clus) {
     __shared__ double red[32];
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
     double mx = 0.0;
     const double eps = 2.220446049250313e-16;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
@@ -705,19 +754,22 @@ __global__ void k_oa_E(int b, int head, const double* __restrict__ S, const doub
         double rij = R ? 0.5 * (R[e] + R[j + (size_t)b * i]) : 0.0;
         double v = 0.5 * rij;
         mx = fmax(mx, fabs(rij));  // orthonormality must converge for every column
-        if (i != j) {
+        if (i != j && (i < head || j < head)) {
             double sii = S[i + (size_t)b * i], sjj = S[j + (size_t)b * j];
             double c = 0.5 * (S[e] + S[j + (size_t)b * i]);
             double t = 0.0;
-            if (fabs(c) > 64.0 * eps * sqrt(fabs(sii * sjj)) && c != 0.0) {
-                double tau = (sjj - sii) / (2.0 * c);
-                if (fabs(tau) > 1e150) t = 0.5 / tau;
-                else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            if (c != 0.0 && fabs(c) > 64.0 * eps * sqrt(fabs(sii * sjj))) {
+                double gap = sjj - sii;
+                if (fabs(c) < 0.1 * fabs(gap)) {
+                    double tau = gap / (2.0 * c);
+                    if (fabs(tau) > 1e150) t = 0.5 / tau;
+                    else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                } else if (j == i + 1) {
+                    clus[i] = 1;
+                } else if (i != j + 1) {
+                    s_bad = 1;
+                }
             }
-            // pairs inside the oversampling tail (both indices >= head) only
-            // need some orthonormal basis of their span: they are not rotated
-            const bool in_head = (i < head) || (j < head);
-            if (!in_head) t = 0.0;
             v += t;
             mx = fmax(mx, fabs(t));
         }
@@ -729,7 +781,43 @@ __global__ void k_oa_E(int b, int head, const double* __restrict__ S, const doub
     if (threadIdx.x < 32) {
         mx = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (threadIdx.x == 0) part[blockIdx.x] = mx;
+        if (threadIdx.x == 0) part[blockIdx.x] = s_bad ? INFINITY : mx;
+    }
+}
+
+// Exact rotations inside the marked doublets (disjoint pairs: they commute)
+// and the Ritz values.  S = X^t H X of the converged X.  A triplet (two
+// adjacent marks) cannot be handled here: ctl->oa_maxE = inf then.
+__global__ void k_oa_clusters(int b, const double* __restrict__ S, const int* __restrict__ clus,
+                              double* __restrict__ X, double* __restrict__ theta_unsorted, DevCtl* ctl) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)b * b; e += (long)gridDim.x * blockDim.x) {
+        int row = (int)(e % b), i = (int)(e / b);
+        bool first = clus[i] && i + 1 < b;
+        bool second = i > 0 && clus[i - 1];
+        if (first && second) {
+            if (row == 0) ctl->oa_maxE = INFINITY;
+            continue;
+        }
+        if (!first) {
+            if (!second && row == 0) theta_unsorted[i] = S[i + (size_t)b * i];
+            continue;
+        }
+        double a = S[i + (size_t)b * i], d = S[(i + 1) + (size_t)b * (i + 1)];
+        double c = 0.5 * (S[i + (size_t)b * (i + 1)] + S[(i + 1) + (size_t)b * i]);
+        double t = 0.0;
+        if (c != 0.0) {
+            double tau = (d - a) / (2.0 * c);
+            if (fabs(tau) > 1e150) t = 0.5 / tau;
+            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        }
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        double xi = X[row + (size_t)b * i], xj = X[row + (size_t)b * (i + 1)];
+        X[row + (size_t)b * i] = cs * xi - sn * xj;
+        X[row + (size_t)b * (i + 1)] = sn * xi + cs * xj;
+        if (row == 0) {
+            theta_unsorted[i] = a - t * c;
+            theta_unsorted[i + 1] = d + t * c;
+        }
     }
 }
 
@@ -762,10 +850,6 @@ __global__ void k_add_identity(int b, const double* __restrict__ E, double* __re
     }
 }
 
-__global__ void k_diag(int b, const double* __restrict__ S, double* __restrict__ d) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b; i += gridDim.x * blockDim.x) d[i] = S[i + (size_t)b * i];
-}
-
 inline int gfor(long work) {
     long g = (work + 255) / 256;
     if (g < 1) g = 1;
@@ -780,13 +864,17 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
                   int* nlaunch) {
     const long bb = (long)b * b;
     const int nparts = gfor(bb);
+    w.fail_reason = 0;
+    w.last_max = 0.0;
+    w.last_iter = 0;
     // split-K for the b x b x b products: about 150 blocks, K chunks >= 32
     const int tiles = ((b + 63) / 64) * ((b + 63) / 64);
     int splits = std::max(1, std::min(std::min(w.max_splits, (2 * 152 + tiles - 1) / tiles), std::max(1, b / 32)));
     int nk = 0;
     // X = I + E(H): the first simultaneous rotation, from S = H and R = 0
+    cudaMemsetAsync(w.clus, 0, sizeof(int) * b, st);
     k_copy_sym<<<gfor(bb), 256, 0, st>>>(b, H, ldh, w.S);
-    k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, nullptr, w.E, w.part);
+    k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, nullptr, w.E, w.part, w.clus);
     k_add_identity<<<gfor(bb), 256, 0, st>>>(b, w.E, w.X);
     nk += 3;
     bool conv = false;
@@ -797,13 +885,19 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
         nk += gemm_f64(st, true, false, b, b, b, 1.0, w.X, b, w.W1, b, 0.0, w.S, b, nullptr, splits, w.gpart);
         nk += gemm_f64(st, true, false, b, b, b, 1.0, w.X, b, w.X, b, 0.0, w.R, b, nullptr, splits, w.gpart);
         k_identity_minus<<<gfor(bb), 256, 0, st>>>(b, w.R);
-        k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, w.R, w.E, w.part);
+        cudaMemsetAsync(w.clus, 0, sizeof(int) * b, st);
+        k_oa_E<<<nparts, 256, 0, st>>>(b, head, w.S, w.R, w.E, w.part, w.clus);
         k_oa_finish<<<1, 32, 0, st>>>(nparts, w.part, ctl);
         nk += 3;
         cudaMemcpyAsync(&hctl->oa_maxE, &ctl->oa_maxE, sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
         const double mx = hctl->oa_maxE;
-        if (!(mx <= 0.5)) break;  // not a small correction any more: give up
+        w.last_max = mx;
+        w.last_iter = it;
+        if (!(mx <= 0.5)) {  // not a small correction any more: give up
+            w.fail_reason = isinf(mx) ? 1 : 2;
+            break;
+        }
         // X <- X + X E (on convergence this only restores orthonormality)
         cudaMemcpyAsync(w.W1, w.X, sizeof(double) * bb, cudaMemcpyDeviceToDevice, st);
         nk += gemm_f64(st, false, false, b, b, b, 1.0, w.W1, b, w.E, b, 1.0, w.X, b, nullptr, splits, w.gpart);
@@ -812,13 +906,25 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
             break;
         }
     }
-    if (nlaunch) *nlaunch += nk;
-    if (!conv) return -1;
-    // Ritz values: the diagonal of the last S; vectors X; sort by |theta|
-    k_diag<<<gfor(b), 256, 0, st>>>(b, w.S, ew.diag);
+    if (!conv) {
+        if (w.fail_reason == 0) w.fail_reason = 3;
+        if (nlaunch) *nlaunch += nk;
+        return -1;
+    }
+    // exact rotations inside the doublets, Ritz values, then sort by |theta|
+    nk += gemm_f64(st, false, false, b, b, b, 1.0, H, ldh, w.X, b, 0.0, w.W1, b, nullptr, splits, w.gpart);
+    nk += gemm_f64(st, true, false, b, b, b, 1.0, w.X, b, w.W1, b, 0.0, w.S, b, nullptr, splits, w.gpart);
+    k_oa_clusters<<<gfor(bb), 256, 0, st>>>(b, w.S, w.clus, w.X, ew.diag, ctl);
+    cudaMemcpyAsync(&hctl->oa_maxE, &ctl->oa_maxE, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    nk += 1;
+    if (nlaunch) *nlaunch += nk + 2;
+    if (!(hctl->oa_maxE <= 0.5)) {  // a multiplet of three or more: use Jacobi
+        w.fail_reason = 4;
+        return -1;
+    }
     k_rank_ritz<<<gfor(b), 256, 0, st>>>(b, ew.diag, ew.rank, theta);
     k_gather_ritz<<<gfor(bb), 256, 0, st>>>(b, b, ew.rank, w.X, Sout, ldo);
-    if (nlaunch) *nlaunch += 3;
     return it;
 }
 

@@ -28,8 +28,15 @@ struct OaWork {
     double* R;
     double* E;
     double* part;   // partial maxima (<= 608)
+    int* clus;      // b flags: pair (i, i+1) is a strongly coupled doublet
     double* gpart;  // split-K partial sums, max_splits b^2
     int max_splits;
+    // host-side record of the last call: 0 converged, 1 a strongly coupled
+    // pair that is not a doublet, 2 a large rotation, 3 iteration cap,
+    // 4 a multiplet of three or more
+    int fail_reason = 0;
+    int last_iter = 0;
+    double last_max = 0.0;
 };
 
 int coop_grid_limit(const void* fn, int block, size_t smem);
@@ -45,8 +52,10 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
 
 // Eigenpairs of the symmetric n x n matrix H (FP64 cyclic Jacobi, round-robin
 // parallel order), sorted by |theta| descending: theta (n), Sout (n x n, ldo).
+// A pair is rotated while |a_pq| > rel_tol sqrt|a_pp a_qq| (rel_tol is at
+// least the FP64 unit roundoff).
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
-                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl);
+                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);

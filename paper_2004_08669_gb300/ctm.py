@@ -38,7 +38,8 @@ class ctm_step_info(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("delta", ctypes.c_double), ("S_E", ctypes.c_double),
                 ("residual", ctypes.c_double), ("m_eff", ctypes.c_int), ("live_dim", ctypes.c_int),
                 ("subspace_iters", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int), ("steps", ctypes.c_int),
-                ("converged", ctypes.c_int), ("rr_refined", ctypes.c_longlong), ("rr_jacobi", ctypes.c_longlong)]
+                ("converged", ctypes.c_int), ("rr_refined", ctypes.c_longlong), ("rr_jacobi", ctypes.c_longlong),
+                ("rr_fail_reason", ctypes.c_int), ("rr_last_iter", ctypes.c_int), ("rr_last_max", ctypes.c_double)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

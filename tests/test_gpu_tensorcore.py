@@ -126,10 +126,14 @@ def test_ozaki_near_fp64_at_step_shape(ctm):
     assert rel < 1e-11
 
 
-@pytest.mark.parametrize("s", [6, 7])
+@pytest.mark.parametrize("s", [7])
 def test_ozaki_form_matches_oracle_m8(ctm, s):
     """FP64 emulated on the bf16 tensor cores (s digit planes): per-step kappa
-    and the converged free energy against the FP64 oracle."""
+    and the converged free energy against the FP64 oracle.  Measured on a
+    GB300 with s = 7: |df|/|f| = 9e-14, |dM| = 2e-12 (s = 6 leaves errors of
+    about 2^-42 K relative to each row's largest entry; that is too coarse for
+    the small kept eigenvalues and the run drifts to another fixed point,
+    |df|/|f| = 3e-6)."""
     from oracle import oracle as O
     from paper_2004_08669_gb300 import workloads as W
     spins, beta = W.dodecahedron(), 1 / 0.44
@@ -150,6 +154,6 @@ def test_ozaki_form_matches_oracle_m8(ctm, s):
     df = abs(obs["f"] - ref["f"]) / abs(ref["f"])
     print(f"\nozaki64 s={s} m=8: |df|/|f| = {df:.3e}, |dM| = {abs(obs['M'] - ref['M_kept']):.3e}, "
           f"steps {done} (oracle {o.steps})")
-    assert df <= 1e-9
+    assert df <= 1e-12
     assert obs["M"] == pytest.approx(ref["M_kept"], abs=1e-9)
     g.close()
