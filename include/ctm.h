@@ -96,6 +96,8 @@ typedef struct {
                               2 large rotation, 3 iteration cap, 4 triplet     */
     int rr_last_iter;      /* its iterations                                   */
     double rr_last_max;    /* its last largest rotation / orthonormality defect */
+    int jacobi_rotations[8]; /* rotations per sweep of the last Jacobi solve
+                                (first 8 sweeps)                           */
 } ctm_step_info;
 
 /* Observables of the current state (Eq. 4-6 and the free energy). */

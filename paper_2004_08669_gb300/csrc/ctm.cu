@@ -680,11 +680,10 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             h->rr_fail_streak = used < 0 ? h->rr_fail_streak + 1 : 0;
         }
         if (used < 0) {
-            // while the subspace itself is only resid-accurate, polishing its
-            // Ritz vectors further is wasted: stop the sweeps at 1% of it
-            const double rel = (h->last_resid > 0.0 && h->last_resid < 1.0)
-                                   ? std::min(1e-6, 0.01 * h->last_resid) : 0.0;
-            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, rel));
+            // Full FP64 accuracy: the corner is stored diagonal in the Ritz
+            // basis, so any coupling left unrotated enters the next extension
+            // at first order.
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
             nk_rr += 4;
             ++h->rr_jacobi;
         } else {
@@ -815,6 +814,7 @@ ctm_status step_once(ctm_handle* h) {
     I.rr_fail_reason = h->oa.fail_reason;
     I.rr_last_iter = h->oa.last_iter;
     I.rr_last_max = h->oa.last_max;
+    for (int k = 0; k < 8; ++k) I.jacobi_rotations[k] = h->hctl->rot_count[k];
     return conv ? CTM_OK : CTM_ENOTCONVERGED;
 }
 

@@ -38,8 +38,8 @@ struct DevCtl {
     int live;            // current live rows of P (D)
     int pad2, pad3;
     // barrier words (cooperative kernels)
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned int bar_count;  // zeroed before every cooperative launch
+    unsigned int bar_pad;
     int rot_count[64];   // rotations per Jacobi sweep
     // observables
     double obs_M_num, obs_u_num, obs_z4, obs_SE;
@@ -47,35 +47,34 @@ struct DevCtl {
     double oa_maxE;
 };
 
-// Grid-wide barrier for cooperative launches.  Every wait is bounded: after
-// ~2^22 polls (about a second) the barrier records a timeout in *err and
-// returns, so a missing block can never hang the GPU.
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen,
-                                             unsigned int nblocks, int* err) {
+// Grid-wide barrier for cooperative launches on a monotonic arrival counter:
+// the host zeroes *count before the launch, and a block's e-th barrier waits
+// until e * gridDim.x arrivals are counted (one release-add per block, then
+// acquire loads; no read-modify-write sits on the wait path).  Every wait is
+// bounded: after 2^22 polls (about a second) the barrier records a timeout
+// (2) in *err and returns false in every thread of the block, so a missing
+// block can never hang the GPU.
+__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int& epoch, int* err) {
     __syncthreads();
     __shared__ int s_fail;
+    ++epoch;
     if (threadIdx.x == 0) {
         s_fail = 0;
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> g(*gen);
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(*count);
-        unsigned int my = g.load(cuda::memory_order_acquire);
-        unsigned int arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
-        if (arrived == nblocks - 1) {
-            c.store(0u, cuda::memory_order_relaxed);
-            g.fetch_add(1u, cuda::memory_order_release);
-        } else {
-            long polls = 0;
-            while (g.load(cuda::memory_order_acquire) == my) {
-                if (++polls > (1L << 22)) {
-                    atomicExch(err, 2);
-                    s_fail = 1;
-                    break;
-                }
-                __nanosleep(64);
+        const unsigned int target = epoch * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        long polls = 0;
+        unsigned int v;
+        while (true) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++polls > (1L << 22)) {
+                atomicExch(err, 2);
+                s_fail = 1;
+                break;
             }
         }
+        if (*(volatile int*)err == 2) s_fail = 1;
     }
-    if (threadIdx.x == 0 && *(volatile int*)err == 2) s_fail = 1;
     __syncthreads();
     return s_fail == 0;  // uniform across the block
 }

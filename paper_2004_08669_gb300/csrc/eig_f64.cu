@@ -37,61 +37,61 @@ __device__ __forceinline__ void rr_pair(int r, int k, int npad, int& p, int& q) 
 }
 
 struct Rot {
-    double c, s, t;
+    double c, s;
     bool on;
 };
 
-// Rotation of the pair (p, q): the tangent t of the angle that zeroes a_pq is
-// taken in FP32 (an approximate angle only reduces a_pq by ~1e-7 instead of
-// zeroing it; Jacobi's convergence is unaffected), while c = 1/sqrt(1 + t^2)
-// is made FP64-accurate from an FP32 reciprocal square root by two
-// Newton-Raphson steps y <- y (3 - x y^2) / 2, and s = t c: the rotation is
-// orthogonal to FP64 rounding.  This keeps FP64 square roots and divisions,
-// which are slow on this part, out of every round.
+// A pair is rotated while its coupling exceeds eps relative to the geometric
+// mean of its diagonal entries (the criterion that keeps relative accuracy for
+// graded matrices) and an absolute floor.  The comparison is made on squares
+// when they are safely representable, so that no FP64 square root (slow on
+// this part) is taken per pair.
+__device__ __forceinline__ bool jac_above(double app, double aqq, double apq, double eps, double floor_abs) {
+    if (apq == 0.0) return false;
+    const double a = fabs(apq);
+    if (!(a > floor_abs)) return false;
+    const double pr = fabs(app * aqq), a2 = apq * apq;
+    if (pr > 1e-290 && pr < 1e290 && a2 > 1e-290 && a2 < 1e290) return a2 > (eps * eps) * pr;
+    return a > eps * sqrt(pr);
+}
+
+// Rotation of the pair (p, q) (Golub & Van Loan 8.5.2): tau = (a_qq - a_pp) /
+// (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2),
+// s = t c.  The tangent is taken in FP32: an approximate angle leaves ~1e-7
+// of a_pq instead of zero, which the next sweep removes, so convergence is
+// unaffected.  c is made FP64-accurate from an FP32 reciprocal square root by
+// two Newton-Raphson steps y <- y (3 - x y^2) / 2, and s = t c: the rotation
+// is orthogonal to FP64 rounding, so the similarity transform stays exact.
 __device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, double eps, double floor_abs) {
-    Rot R{1.0, 0.0, 0.0, false};
-    if (apq == 0.0) return R;
-    if (fabs(apq) <= fmax(eps * sqrt(fabs(app * aqq)), floor_abs)) return R;
-    float tau = (float)((aqq - app) / (2.0 * apq));
-    float tf;
-    if (fabsf(tau) > 1e18f) tf = 0.5f / tau;
-    else tf = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-    double t = (double)tf;
-    double x = 1.0 + t * t;
+    Rot R{1.0, 0.0, false};
+    if (!jac_above(app, aqq, apq, eps, floor_abs)) return R;
+    const double d = aqq - app;
+    const double aa = fabs(apq), ad = fabs(d);
+    double t;
+    if (aa > 1e-30 && aa < 1e30 && ad < 1e30 && ad < 1e18 * aa) {
+        const float tau = (float)d / (float)(2.0 * apq);
+        t = (double)(copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau)));
+    } else {  // extreme scales or |tau| beyond 5e17: the FP64 formula
+        const double tau = d / (2.0 * apq);
+        t = fabs(tau) > 1e150 ? 0.5 / tau : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    }
+    const double x = 1.0 + t * t;
     double y = (double)rsqrtf((float)x);
     y = y * (1.5 - 0.5 * x * y * y);
     y = y * (1.5 - 0.5 * x * y * y);
     R.c = y;
     R.s = t * y;
-    R.t = t;
-    R.on = true;
-    return R;
-}
-
-__device__ __forceinline__ Rot rot_of(const double* A, int ld, int p, int q, double eps,
-                                      double floor_abs) {
-    Rot R{1.0, 0.0, 0.0, false};
-    double apq = __ldcg(A + p + (size_t)ld * q);
-    if (apq == 0.0) return R;
-    double app = __ldcg(A + p + (size_t)ld * p), aqq = __ldcg(A + q + (size_t)ld * q);
-    if (fabs(apq) <= fmax(eps * sqrt(fabs(app * aqq)), floor_abs)) return R;
-    double tau = (aqq - app) / (2.0 * apq);
-    double t;
-    if (fabs(tau) > 1e150) t = 0.5 / tau;
-    else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    R.c = 1.0 / sqrt(1.0 + t * t);
-    R.s = t * R.c;
-    R.t = t;
     R.on = true;
     return R;
 }
 
 __global__ void k_jacobi_init(int n, int npad, const double* __restrict__ H, int ldh,
-                              double* __restrict__ A0, double* __restrict__ S) {
+                              double* __restrict__ A0, double* __restrict__ S, int* __restrict__ act) {
     size_t tot = (size_t)npad * npad;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
          e += (size_t)gridDim.x * blockDim.x) {
         int i = (int)(e % npad), j = (int)(e / npad);
+        if (j == 0) act[i] = 0;
         double v = 0.0;
         if (i < n && j < n) v = 0.5 * (H[i + (size_t)ldh * j] + H[j + (size_t)ldh * i]);
         A0[e] = v;
@@ -99,105 +99,263 @@ __global__ void k_jacobi_init(int n, int npad, const double* __restrict__ H, int
     }
 }
 
+// Pair k of round r of the tournament over the first s2 entries of perm, or
+// one of the fixed (never rotated) pairs of the entries beyond s2.
+__device__ __forceinline__ void jac_pair(int r, int k, int s2, const int* perm, int& p, int& q) {
+    const int nh = s2 >> 1;
+    if (k < nh) {
+        int a, b;
+        rr_pair(r, k, s2, a, b);
+        p = perm[a];
+        q = perm[b];
+    } else {
+        p = perm[s2 + 2 * (k - nh)];
+        q = perm[s2 + 2 * (k - nh) + 1];
+    }
+}
+
+constexpr int JT = 8;        // pairs per side of an A unit (JT x JT 2x2 blocks)
+constexpr int JS_ROWS = 32;  // rows of S per S unit (JT pairs x JS_ROWS rows)
+
 // Cooperative: all blocks co-resident (cudaLaunchAttributeCooperative).
-// Each round, every block first computes the npad/2 rotations of the round
-// into shared memory (one square root and division per pair, not per
-// element: FP64 division and square root are costly on this part), then
-// applies them to its share of the 2 x 2 blocks and of the rows of S.
-__global__ void k_jacobi(int n, int npad, double* A0, double* A1,
-                         double* S, double* __restrict__ diag, int max_sweeps,
-                         double eps, double floor_abs, DevCtl* ctl) {
-    extern __shared__ double rot_sh[];  // 3 * (npad / 2): c, s, t (t = 0: off)
+//
+// Each sweep starts with one parallel pass over all pairs that tags every
+// index with a coupling above the threshold (act[i] = sweep + 1).  No tagged
+// index means convergence, so no sweep is spent only to confirm it.  The
+// sweep then runs the round-robin tournament over the tagged indices alone
+// (padded to an even count with one untagged index): s - 1 rounds instead of
+// npad - 1 once few pairs are left, while the untagged indices sit in fixed
+// pairs that are never rotated.  When more than 3/4 of the indices are
+// tagged, the tournament covers all of them.
+//
+// A round is split into units of similar FP64 cost, one or more per block:
+// an A unit is a JT x JT tile of the upper triangle of 2x2 blocks of A (the
+// transposed block is written from the same values, so A stays exactly
+// symmetric); an S unit is JT column pairs x JS_ROWS rows of S.  A unit
+// computes only the (at most 2 JT) rotations it needs, with its input loads
+// issued before the rotations so that both memory round trips overlap.  A is
+// double-buffered (read from one buffer, written in full to the other); S is
+// updated in place (the round's column pairs are disjoint).
+__global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, double* A1, double* S,
+                                                double* __restrict__ diag, int* act, int max_sweeps, double eps,
+                                                double floor_rel, DevCtl* ctl) {
+    extern __shared__ int jsh[];
+    int* perm = jsh;         // npad: tagged indices first
+    int* flg = jsh + npad;   // npad: tag flags of this sweep
+    __shared__ double u_c[2 * JT], u_s[2 * JT];
+    __shared__ int u_on[2 * JT];
+    __shared__ double s_red[8];
+    __shared__ int s_cnt;
     const int half = npad / 2;
-    double* rc = rot_sh;
-    double* rs = rot_sh + half;
-    double* rt = rot_sh + 2 * half;
-    const long nblk_items = (long)half * half;
-    const long nS_items = (long)npad * half;
-    const long W = nblk_items + nS_items;
+    const int nT = (half + JT - 1) / JT;
+    const int nA = nT * (nT + 1) / 2;
+    const int nRC = (npad + JS_ROWS - 1) / JS_ROWS;
+    const int nU = nA + nT * nRC;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
+    const int tid = threadIdx.x;
     int* err = &ctl->jac_status;
-    long round_total = 0;
-    int sweep = 0;
+    unsigned int epoch = 0;
+
+    // absolute floor relative to the largest diagonal entry (same in all blocks)
+    double mx = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) mx = fmax(mx, fabs(__ldcg(A0 + i + (size_t)npad * i)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, s_red[w]);
+        s_red[0] = v;
+    }
+    __syncthreads();
+    const double floor_abs = floor_rel * s_red[0];
+
+    long rt = 0;  // rounds done: selects the current A buffer
+    int sweep = 0, my_rot = 0;
     bool converged = false;
-    for (sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
-        for (int r = 0; r < npad - 1; ++r, ++round_total) {
-            const double* Ac = (round_total & 1) ? A1 : A0;
-            double* An = (round_total & 1) ? A0 : A1;
-            for (int k = threadIdx.x; k < half; k += blockDim.x) {
-                int p, q;
-                rr_pair(r, k, npad, p, q);
-                Rot R = rot_fast(__ldcg(Ac + p + (size_t)npad * p), __ldcg(Ac + q + (size_t)npad * q),
-                                 __ldcg(Ac + p + (size_t)npad * q), eps, floor_abs);
-                rc[k] = R.c;
-                rs[k] = R.s;
-                rt[k] = R.on ? 1.0 : 0.0;
-                if (R.on && blockIdx.x == 0) atomicAdd(&ctl->rot_count[sweep], 1);
-            }
-            __syncthreads();
-            for (long it = gtid; it < W; it += gstride) {
-                if (it < nblk_items) {
-                    int ka = (int)(it % half), kb = (int)(it / half);
-                    int p, q, rr, tt;
-                    rr_pair(r, ka, npad, p, q);
-                    rr_pair(r, kb, npad, rr, tt);
-                    const double ca = rc[ka], sa = rs[ka];
-                    const bool ona = rt[ka] != 0.0;
-                    if (ka == kb) {
-                        double app = __ldcg(Ac + p + (size_t)npad * p);
-                        double aqq = __ldcg(Ac + q + (size_t)npad * q);
-                        double apq = __ldcg(Ac + p + (size_t)npad * q);
-                        if (ona) {
-                            // J^t [[app, apq], [apq, aqq]] J with J = [[c, s], [-s, c]]
-                            double x_pp = ca * app - sa * apq, x_pq = ca * apq - sa * aqq;
-                            double x_qp = sa * app + ca * apq, x_qq = sa * apq + ca * aqq;
-                            double npp = ca * x_pp - sa * x_pq, nqq = sa * x_qp + ca * x_qq;
-                            double npq = 0.5 * ((sa * x_pp + ca * x_pq) + (ca * x_qp - sa * x_qq));
-                            An[p + (size_t)npad * p] = npp;
-                            An[q + (size_t)npad * q] = nqq;
-                            An[p + (size_t)npad * q] = npq;
-                            An[q + (size_t)npad * p] = npq;
-                        } else {
-                            An[p + (size_t)npad * p] = app;
-                            An[q + (size_t)npad * q] = aqq;
-                            An[p + (size_t)npad * q] = apq;
-                            An[q + (size_t)npad * p] = __ldcg(Ac + q + (size_t)npad * p);
-                        }
-                    } else {
-                        const double cb = rc[kb], sb = rs[kb];
-                        double a_pr = __ldcg(Ac + p + (size_t)npad * rr);
-                        double a_pt = __ldcg(Ac + p + (size_t)npad * tt);
-                        double a_qr = __ldcg(Ac + q + (size_t)npad * rr);
-                        double a_qt = __ldcg(Ac + q + (size_t)npad * tt);
-                        // J_a^t from the left (rows p, q)
-                        double x_pr = ca * a_pr - sa * a_qr, x_pt = ca * a_pt - sa * a_qt;
-                        double x_qr = sa * a_pr + ca * a_qr, x_qt = sa * a_pt + ca * a_qt;
-                        // J_b from the right (columns r, t)
-                        An[p + (size_t)npad * rr] = cb * x_pr - sb * x_pt;
-                        An[p + (size_t)npad * tt] = sb * x_pr + cb * x_pt;
-                        An[q + (size_t)npad * rr] = cb * x_qr - sb * x_qt;
-                        An[q + (size_t)npad * tt] = sb * x_qr + cb * x_qt;
-                    }
-                } else {
-                    long e = it - nblk_items;
-                    int row = (int)(e % npad), k = (int)(e / npad);
-                    if (rt[k] != 0.0) {
-                        int p, q;
-                        rr_pair(r, k, npad, p, q);
-                        const double c = rc[k], sn = rs[k];
-                        double sp = __ldcg(S + row + (size_t)npad * p);
-                        double sq = __ldcg(S + row + (size_t)npad * q);
-                        S[row + (size_t)npad * p] = c * sp - sn * sq;
-                        S[row + (size_t)npad * q] = sn * sp + c * sq;
-                    }
+    for (sweep = 0;; ++sweep) {
+        const double* Acur = (rt & 1) ? A1 : A0;
+        const int tag = sweep + 1;
+        for (long e = gtid; e < (long)npad * npad; e += gstride) {
+            const int i = (int)(e % npad), j = (int)(e / npad);
+            if (i < j) {
+                const double aij = __ldcg(Acur + i + (size_t)npad * j);
+                if (aij != 0.0 &&
+                    jac_above(__ldcg(Acur + i + (size_t)npad * i), __ldcg(Acur + j + (size_t)npad * j), aij, eps,
+                              floor_abs)) {
+                    act[i] = tag;
+                    act[j] = tag;
                 }
             }
-            if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
         }
-        converged = (*(volatile int*)&ctl->rot_count[sweep]) == 0;
+        if (!grid_sync(&ctl->bar_count, epoch, err)) return;
+        // compaction by warp 0: tagged indices ascending, then the others
+        for (int i = tid; i < npad; i += blockDim.x) flg[i] = __ldcg(act + i) == tag;
+        __syncthreads();
+        if (tid < 32) {
+            int base = 0;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                const int i = c0 + tid;
+                const bool on = i < npad && flg[i];
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                if (on) perm[base + __popc(bal & ((1u << tid) - 1u))] = i;
+                base += __popc(bal);
+            }
+            const int ntag = base;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                const int i = c0 + tid;
+                const bool off = i < npad && !flg[i];
+                const unsigned bal = __ballot_sync(0xffffffffu, off);
+                if (off) perm[base + __popc(bal & ((1u << tid) - 1u))] = i;
+                base += __popc(bal);
+            }
+            if (tid == 0) s_cnt = ntag;
+        }
+        __syncthreads();
+        const int ntag = s_cnt;
+        if (ntag == 0) {
+            converged = true;
+            break;
+        }
+        if (sweep >= max_sweeps) break;
+        int s2 = ntag + (ntag & 1);  // ntag odd => ntag < npad: an untagged index exists
+        if (4 * s2 > 3 * npad) s2 = npad;
+        const int nh = s2 / 2;
+        for (int r = 0; r < s2 - 1; ++r, ++rt) {
+            const double* Ac = (rt & 1) ? A1 : A0;
+            double* An = (rt & 1) ? A0 : A1;
+            for (int u = blockIdx.x; u < nU; u += gridDim.x) {
+                const bool isA = u < nA;
+                int kA0, kB0 = 0, rc = 0;
+                bool diagT = false;
+                if (isA) {  // upper-triangular tile (I, J), I <= J, row by row
+                    int I = 0, rem = u;
+                    while (rem >= nT - I) {
+                        rem -= nT - I;
+                        ++I;
+                    }
+                    kA0 = JT * I;
+                    kB0 = JT * (I + rem);
+                    diagT = rem == 0;
+                } else {
+                    const int v = u - nA;
+                    kA0 = JT * (v / nRC);
+                    rc = v % nRC;
+                }
+                // item inputs first
+                int ka = -1, kb = -1, row = -1, p = 0, q = 0, pr = 0, pt = 0;
+                double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+                if (isA) {
+                    if (tid < JT * JT) {
+                        const int a = tid % JT, b = tid / JT;
+                        if (kA0 + a < half && kB0 + b < half && (!diagT || a <= b)) {
+                            ka = kA0 + a;
+                            kb = kB0 + b;
+                            jac_pair(r, ka, s2, perm, p, q);
+                            if (ka == kb) {
+                                x0 = __ldcg(Ac + p + (size_t)npad * p);
+                                x1 = __ldcg(Ac + q + (size_t)npad * q);
+                                x2 = __ldcg(Ac + p + (size_t)npad * q);
+                            } else {
+                                jac_pair(r, kb, s2, perm, pr, pt);
+                                x0 = __ldcg(Ac + p + (size_t)npad * pr);
+                                x1 = __ldcg(Ac + p + (size_t)npad * pt);
+                                x2 = __ldcg(Ac + q + (size_t)npad * pr);
+                                x3 = __ldcg(Ac + q + (size_t)npad * pt);
+                            }
+                        }
+                    }
+                } else {
+                    const int kk = tid / JS_ROWS;
+                    const int rw = rc * JS_ROWS + tid % JS_ROWS;
+                    if (kk < JT && kA0 + kk < half && rw < npad) {
+                        ka = kA0 + kk;
+                        row = rw;
+                        jac_pair(r, ka, s2, perm, p, q);
+                        x0 = __ldcg(S + row + (size_t)npad * p);
+                        x1 = __ldcg(S + row + (size_t)npad * q);
+                    }
+                }
+                // the unit's rotations
+                const int nrot = isA ? 2 * JT : JT;
+                const int rtid = isA ? tid - JT * JT : tid;  // A units: threads after the items
+                if (rtid >= 0 && rtid < nrot) {
+                    const int k = rtid < JT ? kA0 + rtid : kB0 + rtid - JT;
+                    Rot R{1.0, 0.0, false};
+                    if (k < nh) {
+                        int rp, rq;
+                        jac_pair(r, k, s2, perm, rp, rq);
+                        R = rot_fast(__ldcg(Ac + rp + (size_t)npad * rp), __ldcg(Ac + rq + (size_t)npad * rq),
+                                     __ldcg(Ac + rp + (size_t)npad * rq), eps, floor_abs);
+                    }
+                    u_c[rtid] = R.c;
+                    u_s[rtid] = R.s;
+                    u_on[rtid] = R.on ? 1 : 0;
+                    if (!isA && rc == 0 && R.on) ++my_rot;
+                }
+                __syncthreads();
+                if (ka >= 0) {
+                    if (isA) {
+                        const int ia = ka - kA0, ib = JT + kb - kB0;
+                        const double ca = u_c[ia], sa = u_s[ia];
+                        const bool ona = u_on[ia] != 0;
+                        if (ka == kb) {
+                            if (ona) {
+                                // J^t [[app, apq], [apq, aqq]] J with J = [[c, s], [-s, c]]
+                                const double app = x0, aqq = x1, apq = x2;
+                                const double y_pp = ca * app - sa * apq, y_pq = ca * apq - sa * aqq;
+                                const double y_qp = sa * app + ca * apq, y_qq = sa * apq + ca * aqq;
+                                const double npq = 0.5 * ((sa * y_pp + ca * y_pq) + (ca * y_qp - sa * y_qq));
+                                An[p + (size_t)npad * p] = ca * y_pp - sa * y_pq;
+                                An[q + (size_t)npad * q] = sa * y_qp + ca * y_qq;
+                                An[p + (size_t)npad * q] = npq;
+                                An[q + (size_t)npad * p] = npq;
+                            } else {
+                                An[p + (size_t)npad * p] = x0;
+                                An[q + (size_t)npad * q] = x1;
+                                An[p + (size_t)npad * q] = x2;
+                                An[q + (size_t)npad * p] = x2;
+                            }
+                        } else {
+                            const double cb = u_c[ib], sb = u_s[ib];
+                            const bool onb = u_on[ib] != 0;
+                            double o_pr = x0, o_pt = x1, o_qr = x2, o_qt = x3;
+                            if (ona || onb) {
+                                // J_a^t from the left (rows p, q), J_b from the right (columns r, t)
+                                const double y_pr = ca * x0 - sa * x2, y_pt = ca * x1 - sa * x3;
+                                const double y_qr = sa * x0 + ca * x2, y_qt = sa * x1 + ca * x3;
+                                o_pr = cb * y_pr - sb * y_pt;
+                                o_pt = sb * y_pr + cb * y_pt;
+                                o_qr = cb * y_qr - sb * y_qt;
+                                o_qt = sb * y_qr + cb * y_qt;
+                            }
+                            An[p + (size_t)npad * pr] = o_pr;
+                            An[p + (size_t)npad * pt] = o_pt;
+                            An[q + (size_t)npad * pr] = o_qr;
+                            An[q + (size_t)npad * pt] = o_qt;
+                            An[pr + (size_t)npad * p] = o_pr;
+                            An[pt + (size_t)npad * p] = o_pt;
+                            An[pr + (size_t)npad * q] = o_qr;
+                            An[pt + (size_t)npad * q] = o_qt;
+                        }
+                    } else {
+                        const int ia = ka - kA0;
+                        if (u_on[ia]) {
+                            const double c = u_c[ia], sn = u_s[ia];
+                            S[row + (size_t)npad * p] = c * x0 - sn * x1;
+                            S[row + (size_t)npad * q] = sn * x0 + c * x1;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            if (!grid_sync(&ctl->bar_count, epoch, err)) return;
+        }
+        if (my_rot) atomicAdd(&ctl->rot_count[sweep < 64 ? sweep : 63], my_rot);
+        my_rot = 0;
     }
-    const double* Af = (round_total & 1) ? A1 : A0;
+    const double* Af = (rt & 1) ? A1 : A0;
     for (long i = gtid; i < n; i += gstride) diag[i] = __ldcg(Af + i + (size_t)npad * i);
     if (gtid == 0) {
         ctl->jac_sweeps = sweep;
@@ -242,15 +400,16 @@ __global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, doub
     int* err = &ctl->chol_status;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
+    unsigned int epoch = 0;
     double shift = 0.0;
     if (shift_rel > 0.0) {
         for (int i = 0; i < n; ++i) shift += G[i + (size_t)ld * i];
         shift *= shift_rel;
     }
-    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
+    if (!grid_sync(&ctl->bar_count, epoch, err)) return;
     if (shift != 0.0)
         for (long i = gtid; i < n; i += gstride) G[i + (size_t)ld * i] = __ldcg(G + i + (size_t)ld * i) + shift;
-    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
+    if (!grid_sync(&ctl->bar_count, epoch, err)) return;
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int kb = min(32, n - k0);
         // --- diagonal block, factored redundantly in every block
@@ -293,7 +452,7 @@ __global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, doub
             }
             for (int j = 0; j < kb; ++j) G[i + (size_t)ld * (k0 + j)] = x[j];
         }
-        if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
+        if (!grid_sync(&ctl->bar_count, epoch, err)) return;
         if (k1 >= n) break;
         // --- trailing update on 64 x 64 tiles of the lower triangle
         const int nt = n - k1;
@@ -338,7 +497,7 @@ __global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, doub
                     }
                 }
         }
-        if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, gridDim.x, err)) return;
+        if (!grid_sync(&ctl->bar_count, epoch, err)) return;
     }
 }
 
@@ -615,17 +774,20 @@ int coop_grid_limit(const void* fn, int block, size_t smem) {
 }
 
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
-                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol) {
+                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol, double floor_rel) {
     int npad = n + (n & 1);
     if (npad < 2) npad = 2;
-    k_jacobi_init<<<grid_for((size_t)npad * npad), 256, 0, st>>>(n, npad, H, ldh, w.A0, w.S);
+    k_jacobi_init<<<grid_for((size_t)npad * npad), 256, 0, st>>>(n, npad, H, ldh, w.A0, w.S, w.rank);
     cudaMemsetAsync(&ctl->rot_count[0], 0, sizeof(ctl->rot_count), st);
     cudaMemsetAsync(&ctl->jac_status, 0, sizeof(int), st);
+    cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
     if (max_sweeps > 64) max_sweeps = 64;
-    long half = npad / 2;
-    long W = half * half + (long)npad * half;
-    int grid = (int)((W + 255) / 256);
-    const size_t smem = 3 * (size_t)(npad / 2) * sizeof(double);
+    const long half = npad / 2;
+    const long nT = (half + JT - 1) / JT;
+    const long nU = nT * (nT + 1) / 2 + nT * ((npad + JS_ROWS - 1) / JS_ROWS);
+    int grid = (int)nU;
+    const size_t smem = 2 * (size_t)npad * sizeof(int);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     static int limit = 0;
     static size_t limit_smem = 0;
     if (limit == 0 || smem > limit_smem) {
@@ -636,12 +798,14 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     }
     if (grid > limit) grid = limit;
     if (grid < 1) grid = 1;
-    double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16, floor_abs = 0.0;
+    double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16;
+    double fl = floor_rel > 0.0 ? floor_rel : 0.0;
     double* A0 = w.A0;
     double* A1 = w.A1;
     double* S = w.S;
     double* diag = w.diag;
-    void* args[] = {&n, &npad, &A0, &A1, &S, &diag, &max_sweeps, &eps, &floor_abs, &ctl};
+    int* act = w.rank;  // the sweep tags; rank is rewritten by the sort below
+    void* args[] = {&n, &npad, &A0, &A1, &S, &diag, &act, &max_sweeps, &eps, &fl, &ctl};
     cudaError_t e = launch_coop((const void*)k_jacobi, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);
@@ -652,6 +816,7 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl) {
     // shift is relative: the kernel adds shift * trace(G) to the diagonal
     cudaMemsetAsync(&ctl->chol_status, 0, sizeof(int), st);
+    cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
     static int limit = 0;
     if (limit == 0) limit = coop_grid_limit((const void*)k_cholesky, 256, 0);
     long work = (long)n * n / 2;

@@ -14,7 +14,7 @@ struct EigWork {
     double* A1;
     double* S;      // npad x npad accumulated rotations
     double* diag;   // npad
-    int* rank;      // npad
+    int* rank;      // npad (also the Jacobi sweep tags)
     double* gdots;  // 3 b
     double* gQ;     // 4 b
     int* gkind;     // b
@@ -52,10 +52,12 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
 
 // Eigenpairs of the symmetric n x n matrix H (FP64 cyclic Jacobi, round-robin
 // parallel order), sorted by |theta| descending: theta (n), Sout (n x n, ldo).
-// A pair is rotated while |a_pq| > rel_tol sqrt|a_pp a_qq| (rel_tol is at
-// least the FP64 unit roundoff).
+// A pair is rotated while |a_pq| > max(rel_tol sqrt|a_pp a_qq|, floor_rel
+// max_i |h_ii|) (rel_tol is at least the FP64 unit roundoff; floor_rel 0
+// keeps the purely relative criterion).
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
-                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0);
+                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0,
+                       double floor_rel = 0.0);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);

@@ -39,10 +39,13 @@ class ctm_step_info(ctypes.Structure):
                 ("residual", ctypes.c_double), ("m_eff", ctypes.c_int), ("live_dim", ctypes.c_int),
                 ("subspace_iters", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int), ("steps", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rr_refined", ctypes.c_longlong), ("rr_jacobi", ctypes.c_longlong),
-                ("rr_fail_reason", ctypes.c_int), ("rr_last_iter", ctypes.c_int), ("rr_last_max", ctypes.c_double)]
+                ("rr_fail_reason", ctypes.c_int), ("rr_last_iter", ctypes.c_int), ("rr_last_max", ctypes.c_double),
+                ("jacobi_rotations", ctypes.c_int * 8)]
 
     def to_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["jacobi_rotations"] = list(d["jacobi_rotations"])
+        return d
 
 
 class ctm_obs(ctypes.Structure):
