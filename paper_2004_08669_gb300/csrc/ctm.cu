@@ -177,6 +177,7 @@ struct ctm_handle {
     long long rr_refined = 0, rr_jacobi = 0;  // Rayleigh-Ritz solves by path
     double last_resid = 0.0;                  // last Ritz residual / |w_1|
     int rr_fail_streak = 0;                   // consecutive failed refinements
+    double resid_rate = 0.5;                  // measured Ritz residual reduction per iteration
     ctm::DevCtl* ctl;
     ctm::DevCtl* hctl = nullptr;  // pinned mirror
     // host-side iteration state
@@ -302,40 +303,76 @@ __global__ void k_sumsq_partial(size_t n, const double* __restrict__ x, double* 
 }
 
 // a5/a6: kappa, Omega normalisation, S_E of the kept spectrum, delta.
-__global__ void k_step_finalize(int m, int nparts, const double* __restrict__ part,
-                                const double* __restrict__ theta, double* __restrict__ omega,
-                                double* __restrict__ prev, ctm::DevCtl* ctl) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Block-wide sum / max over 256 threads (result valid in every thread).
+__device__ double block_sum256(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    return t;
+}
+
+__device__ double block_max256(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = red[0];
+    for (int w = 1; w < 8; ++w) t = fmax(t, red[w]);
+    return t;
+}
+
+// a5/a6 of a step, one block of 256 threads: kappa = ||P_new||_F from the
+// partial sums, the kept spectrum omega = theta / (sum theta^4)^(1/4), S_E
+// (Eq. 6) and the convergence measure delta (reading R6).
+__global__ void __launch_bounds__(256) k_step_finalize(int m, int nparts, const double* __restrict__ part,
+                                                       const double* __restrict__ theta,
+                                                       double* __restrict__ omega, double* __restrict__ prev,
+                                                       ctm::DevCtl* ctl) {
+    __shared__ double red[8];
+    const int t = threadIdx.x;
     double ss = 0.0;
-    for (int i = 0; i < nparts; ++i) ss += part[i];
-    double kappa = sqrt(ss);
-    int meff = ctl->meff_new;
-    double z4 = 0.0;
-    for (int i = 0; i < meff; ++i) z4 += pow(theta[i], 4);
-    double sc = pow(z4, -0.25);
-    double SE = 0.0;
-    for (int i = 0; i < meff; ++i) {
-        double p = pow(theta[i], 4) / z4;
-        if (p > 0.0) SE -= p * log(p);
+    for (int i = t; i < nparts; i += 256) ss += part[i];
+    const double kappa = sqrt(block_sum256(ss, red));
+    const int meff = ctl->meff_new;
+    double z = 0.0;
+    for (int i = t; i < meff; i += 256) {
+        const double x = theta[i] * theta[i];
+        z += x * x;
     }
-    double a1 = fabs(theta[0]);
-    double delta = 0.0;
-    for (int i = 0; i < m; ++i) {
-        double w = (i < meff) ? theta[i] * sc : 0.0;
+    const double z4 = block_sum256(z, red);
+    const double sc = 1.0 / sqrt(sqrt(z4));
+    double se = 0.0;
+    for (int i = t; i < meff; i += 256) {
+        const double x = theta[i] * theta[i];
+        const double p = x * x / z4;
+        if (p > 0.0) se -= p * log(p);
+    }
+    const double SE = block_sum256(se, red);
+    const double a1 = fabs(theta[0]);
+    const int have_prev = ctl->have_prev;
+    double dl = 0.0;
+    for (int i = t; i < m; i += 256) {
+        const double w = (i < meff) ? theta[i] * sc : 0.0;
         omega[i] = w;
-        double r = (i < meff) ? fabs(theta[i]) / a1 : 0.0;
-        if (ctl->have_prev) delta = fmax(delta, fabs(r - prev[i]));
+        const double r = (i < meff) ? fabs(theta[i]) / a1 : 0.0;
+        if (have_prev) dl = fmax(dl, fabs(r - prev[i]));
         prev[i] = r;
     }
-    if (ctl->have_prev) delta = fmax(delta, fabs(kappa / ctl->prev_kappa - 1.0));
-    else delta = INFINITY;
-    if (!isfinite(kappa) || kappa == 0.0 || !isfinite(SE)) ctl->numeric_bad = 1;
-    ctl->have_prev = 1;
-    ctl->prev_kappa = kappa;
-    ctl->kappa = kappa;
-    ctl->delta = delta;
-    ctl->SE = SE;
-    ctl->live = meff;
+    double delta = block_max256(dl, red);
+    if (t == 0) {
+        if (have_prev) delta = fmax(delta, fabs(kappa / ctl->prev_kappa - 1.0));
+        else delta = INFINITY;
+        if (!isfinite(kappa) || kappa == 0.0 || !isfinite(SE)) ctl->numeric_bad = 1;
+        ctl->have_prev = 1;
+        ctl->prev_kappa = kappa;
+        ctl->kappa = kappa;
+        ctl->delta = delta;
+        ctl->SE = SE;
+        ctl->live = meff;
+    }
 }
 
 __global__ void k_scale(size_t n, const double* __restrict__ x, const ctm::DevCtl* __restrict__ ctl,
@@ -628,6 +665,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
     const int Ldim = L.q * h->live;
     bool cold = true;
     int passes = 3;
+    CTM_CUDA(cudaMemsetAsync(&h->ctl->chol_status, 0, sizeof(int), h->st));
     if (Ldim <= b) {
         ctm::identity_block(h->st, N, b, h->V, N);
         count_small(h, 1);
@@ -647,23 +685,53 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
     }
     bool conv = false;
     int it = 0;
+    // last measured Ritz residual (the previous stage's final one to start)
+    double r_meas = h->last_resid > 0.0 ? h->last_resid : 1.0;
+    int it_meas = -1;
+    bool meas_here = false;
     if (L.esz) pconvert(h, N, N, h->C, N, nullptr, h->opC, L.ldN);  // C~ rows (symmetric)
     for (it = 0; it < max_iters; ++it) {
+        // A warm block is advanced without a Rayleigh-Ritz solve while the
+        // residual cannot yet meet the tolerance: span(C~ V) does not depend
+        // on the rotation within span(V), so a later solve extracts the same
+        // Ritz pairs.  The residual is predicted from the last measured one
+        // and the measured rate per iteration; a solve is taken at the last
+        // allowed iteration, when the prediction reaches 10x the tolerance,
+        // and at least every 16 iterations.  Skipped blocks are scaled by the
+        // previous Ritz values (their columns are last Ritz vectors) and
+        // re-orthonormalised by shifted Cholesky QR.
+        bool skip_rr = false;
+        if (!cold && it + 1 < max_iters && it - it_meas < 16) {
+            const double pred = r_meas * std::pow(h->resid_rate, (double)(it - it_meas));
+            skip_rr = pred > 10.0 * h->cfg.subspace_tol;
+        }
         if (is_oz(h)) {
             // C~ is split once per eigen stage (first iteration), V every iteration
             ctm_status s0 = ozmm(h, N, b, N, {h->C, N, 1, nullptr}, OZ_BIG, it == 0, {h->V, N, 1, nullptr}, OZ_SB,
                                  true, h->Y, N);
             if (s0 != CTM_OK) return s0;
-            s0 = ozmm(h, b, b, N, {h->V, N, 1, nullptr}, OZ_SA, true, {h->Y, N, 1, nullptr}, OZ_SB, true, h->H, b);
-            if (s0 != CTM_OK) return s0;
+            if (!skip_rr) {
+                s0 = ozmm(h, b, b, N, {h->V, N, 1, nullptr}, OZ_SA, true, {h->Y, N, 1, nullptr}, OZ_SB, true, h->H,
+                          b);
+                if (s0 != CTM_OK) return s0;
+            }
         } else if (L.esz) {
             pconvert(h, b, N, h->V, N, nullptr, h->opV, L.ldN);
             ctm_status s0 = ptc(h, N, b, N, h->opC, L.ldN, h->opV, L.ldN, h->Y, N);
             if (s0 != CTM_OK) return s0;
-            pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+            if (!skip_rr)
+                pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
         } else {
             pgemm(h, false, false, N, b, N, h->C, N, h->V, N, h->Y, N);
-            pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+            if (!skip_rr)
+                pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+        }
+        if (skip_rr) {
+            ctm::next_block(h->st, N, b, h->Y, h->V, N, h->theta, 1e-12, h->T);
+            count_small(h, 1);
+            ctm_status s = stage_orth(h, h->T, h->V, h->Y, 3);
+            if (s != CTM_OK) return s;
+            continue;
         }
         // Rayleigh-Ritz: simultaneous Jacobi rotations when the block is warm
         // (H nearly diagonal), the cooperative Jacobi solver otherwise or as a
@@ -708,8 +776,16 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         ctm_status s = sync_ctl(h);
         if (s != CTM_OK) return s;
         h->last_resid = h->hctl->resid;
+        if (meas_here && r_meas > 0.0 && h->last_resid > 0.0 && it > it_meas) {
+            const double rate = std::pow(h->last_resid / r_meas, 1.0 / (double)(it - it_meas));
+            if (std::isfinite(rate)) h->resid_rate = std::min(0.999, std::max(1e-3, rate));
+        }
+        r_meas = h->last_resid;
+        it_meas = it;
+        meas_here = true;
         if (h->hctl->jac_status == 2 || h->hctl->chol_status == 2)
             return fail(CTM_ETIMEOUT, "a device-side barrier timed out");
+        if (h->hctl->chol_status == 1) return fail(CTM_ENUMERIC, "Cholesky QR met a non-positive pivot");
         if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the eigen stage");
         if (h->hctl->sub_converged) {
             conv = true;
@@ -724,9 +800,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         count_small(h, 1);
         s = stage_orth(h, h->Y, h->V, h->T, passes);
         if (s != CTM_OK) return s;
-        CTM_CUDA(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(ctm::DevCtl), cudaMemcpyDeviceToHost, h->st));
-        CTM_CUDA(cudaStreamSynchronize(h->st));
-        if (h->hctl->chol_status == 1) return fail(CTM_ENUMERIC, "Cholesky QR met a non-positive pivot");
+        // the Cholesky status is sticky and read at the next iteration's sync
     }
     if (!cold) {
         ctm::gauge_align(h->st, N, b, h->Z, h->Zprev, N, h->theta, h->cfg.tol_cluster, h->ew);
@@ -780,7 +854,7 @@ ctm_status step_once(ctm_handle* h) {
     // a5/a6
     const int nparts = 512;
     k_sumsq_partial<<<nparts, 256, 0, h->st>>>((size_t)m * N, h->Pn, h->red);
-    k_step_finalize<<<1, 32, 0, h->st>>>(m, nparts, h->red, h->theta, h->omega, h->prev, h->ctl);
+    k_step_finalize<<<1, 256, 0, h->st>>>(m, nparts, h->red, h->theta, h->omega, h->prev, h->ctl);
     k_scale<<<grid_for((size_t)m * N), 256, 0, h->st>>>((size_t)m * N, h->Pn, h->ctl, h->P);
     count_small(h, 3);
     CTM_CUDA(cudaGetLastError());
@@ -1250,6 +1324,7 @@ ctm_status ctm_set_state(ctm_handle* h, const double* P, const double* omega, in
     h->warm = false;
     h->warm_live = -1;
     h->last_resid = 0.0;
+    h->resid_rate = 0.5;
     h->rr_fail_streak = 0;
     return CTM_OK;
 }

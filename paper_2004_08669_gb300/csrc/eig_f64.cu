@@ -814,8 +814,8 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 }
 
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl) {
-    // shift is relative: the kernel adds shift * trace(G) to the diagonal
-    cudaMemsetAsync(&ctl->chol_status, 0, sizeof(int), st);
+    // shift is relative: the kernel adds shift * trace(G) to the diagonal.
+    // ctl->chol_status is sticky (atomicMax): the caller clears it.
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
     static int limit = 0;
     if (limit == 0) limit = coop_grid_limit((const void*)k_cholesky, 256, 0);
