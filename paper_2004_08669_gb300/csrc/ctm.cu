@@ -115,7 +115,7 @@ Layout make_layout(const ctm_config& c) {
     L.off_mfull = take(sizeof(int));
     L.off_colv = take(2 * np * d);
     L.off_oaX = take(b * b * d);
-    L.off_oaW1 = take(b * b * d);
+    L.off_oaW1 = take(std::max<size_t>((size_t)b * b, (size_t)((b + 31) / 32) * 1024) * d);  // also trinv scratch
     L.off_oaS = take(b * b * d);
     L.off_oaR = take(b * b * d);
     L.off_oaE = take(b * b * d);
@@ -566,7 +566,8 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
         prof_end(h, a, PC_OZSPLIT, nk, 0.0, 8.0 * ((splitA ? (double)M * K : 0.0) + (splitB ? (double)N * K : 0.0)));
     }
     cudaEvent_t a = prof_begin(h);
-    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr);
+    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr, h->part,
+                                 (size_t)h->lay.splits * h->lay.b * h->lay.b);
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("oz_gemm: ") + cudaGetErrorString(e));
     const double pairs = S * (S + 1) / 2.0;
     prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * M * (double)N * K,

@@ -391,15 +391,19 @@ __global__ void k_gather_ritz(int n, int npad, const int* __restrict__ rank, con
 // Blocked right-looking Cholesky G + shift I = L L^t (lower, in place),
 // panel width 32.  Cooperative launch, two grid barriers per panel: every
 // block factors the 32 x 32 diagonal block itself (identical arithmetic in
-// each, so all agree) and solves its share of the panel rows; the trailing
-// update then runs on 64 x 64 lower tiles staged in shared memory.
-__global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
+// each, so all agree) and solves its share of the panel rows (one row per
+// thread, held in registers, with the pivots' reciprocals taken once); the
+// trailing update then runs on 16 x 16 lower tiles, so that it spreads over
+// many SMs (FP64 throughput per SM is low on this part).
+__global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
     __shared__ double D[32][33];
-    __shared__ double PI[32][65];  // panel rows of tile I (l-major)
-    __shared__ double PJ[32][65];  // panel rows of tile J
+    __shared__ double dinv[32];
+    __shared__ double PI[32][17];  // panel rows of tile I (l-major)
+    __shared__ double PJ[32][17];  // panel rows of tile J
     int* err = &ctl->chol_status;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
+    const int tid = threadIdx.x;
     unsigned int epoch = 0;
     double shift = 0.0;
     if (shift_rel > 0.0) {
@@ -413,135 +417,161 @@ __global__ void __launch_bounds__(256) k_cholesky(int n, double* G, int ld, doub
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int kb = min(32, n - k0);
         // --- diagonal block, factored redundantly in every block
-        for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-            int i = e % kb, j = e / kb;
-            D[i][j] = __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j));
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int i = e % 32, j = e / 32;
+            D[i][j] = (i < kb && j < kb) ? __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j)) : 0.0;
         }
         __syncthreads();
         for (int j = 0; j < kb; ++j) {
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 double d = D[j][j];
                 if (!(d > 0.0) || !isfinite(d)) {
                     if (blockIdx.x == 0) atomicMax(err, 1);
                     d = 1.0;
                 }
-                D[j][j] = sqrt(d);
+                const double sq = sqrt(d);
+                D[j][j] = sq;
+                dinv[j] = 1.0 / sq;
             }
             __syncthreads();
-            for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) D[i][j] /= D[j][j];
+            if (tid > j && tid < kb) D[tid][j] *= dinv[j];
             __syncthreads();
-            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-                int i = e % kb, l = e / kb;
+            for (int e = tid; e < kb * kb; e += blockDim.x) {
+                const int i = e % kb, l = e / kb;
                 if (l > j && i >= l) D[i][l] -= D[i][j] * D[l][j];
             }
             __syncthreads();
         }
         if (blockIdx.x == 0)
-            for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-                int i = e % kb, j = e / kb;
+            for (int e = tid; e < kb * kb; e += blockDim.x) {
+                const int i = e % kb, j = e / kb;
                 G[(k0 + i) + (size_t)ld * (k0 + j)] = (i >= j) ? D[i][j] : 0.0;
             }
         const int k1 = k0 + kb;
         // --- panel rows below: L[i, k0:k1] = G[i, k0:k1] L_kk^{-t}
         for (long i = k1 + gtid; i < n; i += gstride) {
             double x[32];
-            for (int j = 0; j < kb; ++j) {
-                double sacc = __ldcg(G + i + (size_t)ld * (k0 + j));
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = (j < kb) ? __ldcg(G + i + (size_t)ld * (k0 + j)) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                double sacc = x[j];
+#pragma unroll
                 for (int l = 0; l < j; ++l) sacc -= x[l] * D[j][l];
-                x[j] = sacc / D[j][j];
+                x[j] = sacc * dinv[j];
             }
-            for (int j = 0; j < kb; ++j) G[i + (size_t)ld * (k0 + j)] = x[j];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < kb) G[i + (size_t)ld * (k0 + j)] = x[j];
         }
         if (!grid_sync(&ctl->bar_count, epoch, err)) return;
         if (k1 >= n) break;
-        // --- trailing update on 64 x 64 tiles of the lower triangle
+        // --- trailing update on 16 x 16 tiles of the lower triangle
         const int nt = n - k1;
-        const int T = (nt + 63) / 64;
+        const int T = (nt + 15) / 16;
         const long ntiles = (long)T * (T + 1) / 2;
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        const int tx = tid & 15, ty = tid >> 4;
         for (long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
             // tile (I, J), I >= J, enumerated row by row
             int I = (int)((sqrt(8.0 * (double)tIdx + 1.0) - 1.0) / 2.0);
             while ((long)(I + 1) * (I + 2) / 2 <= tIdx) ++I;
             while ((long)I * (I + 1) / 2 > tIdx) --I;
             const int J = (int)(tIdx - (long)I * (I + 1) / 2);
-            const int i0 = k1 + 64 * I, j0 = k1 + 64 * J;
-            __syncthreads();
-            for (int e = threadIdx.x; e < 64 * kb; e += blockDim.x) {
-                int r = e & 63, l = e >> 6;
-                PI[l][r] = (i0 + r < n) ? __ldcg(G + (i0 + r) + (size_t)ld * (k0 + l)) : 0.0;
-                PJ[l][r] = (j0 + r < n) ? __ldcg(G + (j0 + r) + (size_t)ld * (k0 + l)) : 0.0;
+            const int i0 = k1 + 16 * I, j0 = k1 + 16 * J;
+            for (int e = tid; e < 16 * 32; e += blockDim.x) {
+                const int r = e & 15, l = e >> 4;
+                PI[l][r] = (l < kb && i0 + r < n) ? __ldcg(G + (i0 + r) + (size_t)ld * (k0 + l)) : 0.0;
+                PJ[l][r] = (l < kb && j0 + r < n) ? __ldcg(G + (j0 + r) + (size_t)ld * (k0 + l)) : 0.0;
             }
             __syncthreads();
-            double acc[4][4] = {};
-            for (int l = 0; l < kb; ++l) {
-                double a[4], bq[4];
+            const int i = i0 + tx, j = j0 + ty;
+            if (i < n && j < n && j <= i) {
+                double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    a[u] = PI[l][tx + 16 * u];
-                    bq[u] = PJ[l][ty + 16 * u];
+                for (int l = 0; l < 32; l += 2) {
+                    a0 = fma(PI[l][tx], PJ[l][ty], a0);
+                    a1 = fma(PI[l + 1][tx], PJ[l + 1][ty], a1);
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bq[v], acc[u][v]);
+                double* g = G + i + (size_t)ld * j;
+                *g = __ldcg(g) - (a0 + a1);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
-                    if (i < n && j < n && j <= i) {
-                        double* g = G + i + (size_t)ld * j;
-                        *g = __ldcg(g) - acc[u][v];
-                    }
-                }
+            __syncthreads();
         }
         if (!grid_sync(&ctl->bar_count, epoch, err)) return;
     }
 }
 
-// Lt = L^t (so that row i of L is contiguous for the inverse below).
-__global__ void k_transpose(int n, const double* __restrict__ L, int ld, double* __restrict__ Lt) {
-    __shared__ double t[32][33];
-    for (int by = blockIdx.y; by * 32 < n; by += gridDim.y)
-        for (int bx = blockIdx.x; bx * 32 < n; bx += gridDim.x) {
-            for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-                int i = bx * 32 + threadIdx.x, j = by * 32 + r;
-                t[r][threadIdx.x] = (i < n && j < n) ? L[i + (size_t)ld * j] : 0.0;
-            }
-            __syncthreads();
-            for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-                int i = by * 32 + threadIdx.x, j = bx * 32 + r;
-                if (i < n && j < n) Lt[i + (size_t)n * j] = t[threadIdx.x][r];
-            }
-            __syncthreads();
-        }
+// Inverses of the 32 x 32 diagonal blocks of the lower triangular L
+// (column-major, ld): Dinv + 1024 I holds the inverse of block I, column-major
+// and zero-padded.  One warp per block, one column of the inverse per lane
+// (forward substitution with the pivots' reciprocals taken once).
+__global__ void __launch_bounds__(32) k_trinv_diag(int n, const double* __restrict__ L, int ld,
+                                                   double* __restrict__ Dinv) {
+    __shared__ double Ls[32][33];
+    __shared__ double rd[32];
+    const int I = blockIdx.x, r0 = 32 * I, nbI = min(32, n - r0);
+    const int c = threadIdx.x;
+    for (int i = 0; i < 32; ++i)
+        Ls[i][c] = (i < nbI && c < nbI && c <= i) ? L[(r0 + i) + (size_t)ld * (r0 + c)] : 0.0;
+    __syncwarp();
+    rd[c] = (c < nbI) ? 1.0 / Ls[c][c] : 0.0;
+    __syncwarp();
+    double x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        double sacc = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < i; ++k) sacc -= Ls[i][k] * x[k];
+        x[i] = (i >= c && i < nbI && c < nbI) ? sacc * rd[i] : 0.0;
+    }
+    double* out = Dinv + (size_t)1024 * I + 32 * c;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out[i] = x[i];
 }
 
-// Linv = L^{-1} (lower triangular), one warp per column; Lt = L^t (n x n), so
-// that the dot products below read contiguous memory.
-__global__ void k_trinv(int n, const double* __restrict__ Lt, double* __restrict__ X, int ldx) {
-    extern __shared__ double xs[];
+// X = L^{-1} (lower triangular), one warp per column j, by blocked forward
+// substitution over 32-row blocks: x_J = Dinv_J e_j, then for each later
+// block x_I = -Dinv_I (L_{I, J:I} x_{J:I}), reading L column by column
+// (coalesced over the lanes) against x held in shared memory.
+__global__ void __launch_bounds__(128) k_trinv_cols(int n, const double* __restrict__ L, int ld,
+                                                    const double* __restrict__ Dinv, double* __restrict__ X,
+                                                    int ldx) {
+    extern __shared__ double tsh[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    double* x = xs + (size_t)warp * n;
-    for (int j = blockIdx.x * wpb + warp; j < n; j += gridDim.x * wpb) {
-        for (int i = lane; i < j; i += 32) X[i + (size_t)ldx * j] = 0.0;
-        double xj = 1.0 / Lt[j + (size_t)n * j];
-        if (lane == 0) x[j] = xj;
-        __syncwarp();
-        for (int i = j + 1; i < n; ++i) {
-            double s = 0.0;
-            for (int k = j + lane; k < i; k += 32) s += Lt[k + (size_t)n * i] * x[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            double xi = -s / Lt[i + (size_t)n * i];
-            __syncwarp();
-            if (lane == 0) x[i] = xi;
-            __syncwarp();
+    const int npad = ((n + 31) / 32) * 32;
+    double* xs = tsh + (size_t)warp * (npad + 32);
+    double* ys = xs + npad;
+    const int j = blockIdx.x * 4 + warp;
+    if (j >= n) return;
+    const int J = j / 32, c = j % 32, nb = npad / 32;
+    for (int i = lane; i < 32 * J; i += 32) X[i + (size_t)ldx * j] = 0.0;
+    {
+        const double v = Dinv[(size_t)1024 * J + 32 * c + lane];  // zero above row c
+        const int r = 32 * J + lane;
+        xs[r] = v;
+        if (r < n) X[r + (size_t)ldx * j] = v;
+    }
+    __syncwarp();
+    for (int I = J + 1; I < nb; ++I) {
+        const int r = 32 * I + lane;
+        const bool live = r < n;
+        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+        const double* Lr = L + (live ? r : 0);
+        for (int col = 32 * J; col < 32 * I; col += 4) {
+            y0 = fma(live ? Lr[(size_t)ld * col] : 0.0, xs[col], y0);
+            y1 = fma(live ? Lr[(size_t)ld * (col + 1)] : 0.0, xs[col + 1], y1);
+            y2 = fma(live ? Lr[(size_t)ld * (col + 2)] : 0.0, xs[col + 2], y2);
+            y3 = fma(live ? Lr[(size_t)ld * (col + 3)] : 0.0, xs[col + 3], y3);
         }
-        for (int i = j + lane; i < n; i += 32) X[i + (size_t)ldx * j] = x[i];
+        ys[lane] = (y0 + y1) + (y2 + y3);
+        __syncwarp();
+        const double* Di = Dinv + (size_t)1024 * I;
+        double xi = 0.0;
+#pragma unroll 8
+        for (int s2 = 0; s2 < 32; ++s2) xi = fma(Di[lane + 32 * s2], ys[s2], xi);
+        xi = -xi;
+        xs[r] = xi;
+        if (live) X[r + (size_t)ldx * j] = xi;
         __syncwarp();
     }
 }
@@ -658,12 +688,14 @@ __global__ void k_gauge_dots(int N, int b, const double* __restrict__ Z, const d
 // Plan: per Ritz column a 2x2 block Q (singlet: sign in Q00; doublet of
 // equal theta: orthogonal polar factor of K = Z_c^t V_c).  kind[i]: 0
 // singlet, 1 first of a doublet, 2 second of a doublet.
+// One thread per column; the thread of a cluster's first column plans it.
 __global__ void k_gauge_plan(int b, const double* __restrict__ theta, double tol_c,
                              const double* __restrict__ d, double* __restrict__ Q, int* __restrict__ kind) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a1 = fabs(theta[0]);
-    int i = 0;
-    while (i < b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b) return;
+    const double a1 = fabs(theta[0]);
+    if (i > 0 && fabs(theta[i] - theta[i - 1]) <= tol_c * a1) return;  // not a cluster's first column
+    {
         int j = i + 1;
         while (j < b && fabs(theta[j] - theta[j - 1]) <= tol_c * a1) ++j;
         int sz = j - i;
@@ -688,7 +720,6 @@ __global__ void k_gauge_plan(int b, const double* __restrict__ theta, double tol
                 kind[k] = 0;
             }
         }
-        i = j;
     }
 }
 
@@ -819,24 +850,22 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
     static int limit = 0;
     if (limit == 0) limit = coop_grid_limit((const void*)k_cholesky, 256, 0);
-    long work = (long)n * n / 2;
-    int grid = (int)((work + 255) / 256);
+    const long T = (n + 15) / 16;
+    int grid = (int)std::max<long>(T * (T + 1) / 2, (n + 255) / 256);
     if (grid > limit) grid = limit;
-    if (grid > 152) grid = 152;
+    if (grid > 2 * 152) grid = 2 * 152;
     if (grid < 1) grid = 1;
     void* args[] = {&n, &G, &ld, &shift, &ctl};
     return launch_coop((const void*)k_cholesky, grid, 256, args, 0, st);
 }
 
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch) {
-    dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
-    k_transpose<<<tg, tb, 0, st>>>(n, L, ld, scratch);
-    const int wpb = 4;
-    int grid = (n + wpb - 1) / wpb;
-    size_t smem = (size_t)wpb * n * sizeof(double);
-    k_trinv<<<grid, 32 * wpb, smem, st>>>(n, scratch, X, ldx);
+    // scratch: ceil(n / 32) * 1024 doubles (the diagonal blocks' inverses)
+    const int nb = (n + 31) / 32;
+    k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch);
+    const size_t smem = 4 * (size_t)(nb * 32 + 32) * sizeof(double);
+    k_trinv_cols<<<(n + 3) / 4, 128, smem, st>>>(n, L, ld, scratch, X, ldx);
 }
-
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
                const double* theta, double* res) {
     if (ncol <= 0) return;
@@ -856,7 +885,7 @@ void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z,
 void gauge_align(cudaStream_t st, int N, int b, double* Z, const double* V, int ld, const double* theta,
                  double tol_c, EigWork& w) {
     k_gauge_dots<<<b, 256, 0, st>>>(N, b, Z, V, ld, w.gdots);
-    k_gauge_plan<<<1, 32, 0, st>>>(b, theta, tol_c, w.gdots, w.gQ, w.gkind);
+    k_gauge_plan<<<(b + 127) / 128, 128, 0, st>>>(b, theta, tol_c, w.gdots, w.gQ, w.gkind);
     k_gauge_apply<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, Z, ld, w.gQ, w.gkind);
 }
 

@@ -62,7 +62,8 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);
 
-// X = L^{-1} for lower-triangular L; scratch: n x n doubles (L^t).
+// X = L^{-1} for lower-triangular L (upper part of X zeroed); scratch:
+// ceil(n / 32) * 1024 doubles.
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch);
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,

@@ -126,42 +126,64 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
     lo += e;
 }
 
-// One warp per operand row: exponent of the row maximum, then the digit planes.
+// Row exponents of the split: rexp[r] holds the largest biased FP64 exponent
+// of row r (subnormals count as 1), 0 for an all-zero row; the row scale is
+// 2^e_r with e_r = rexp - 1022 (so |x| < 2^e_r), 0 for a zero row.
+__device__ __forceinline__ int oz_e(int raw) { return raw == 0 ? 0 : raw - 1022; }
+
+// The split runs over 32 x 32 tiles (rows r, K-index k) staged in shared
+// memory, so that the reads are coalesced along whichever of the two indices
+// is contiguous and every row is spread over many CTAs.  Pass 1 takes the row
+// maxima of the exponents (atomicMax into rexp, zeroed before); pass 2 writes
+// the digit planes, K-contiguous, zero beyond K up to ld.
 // src(r, k) = src[r rs + k ks] (* scale[k]); planes[(i Rp + r) ld + k].
-__global__ void k_oz_split(int R, int K, int s, const double* __restrict__ src, long rs, long ks,
-                           const double* __restrict__ scale, __nv_bfloat16* __restrict__ planes, int Rp, int ld,
-                           int* __restrict__ rexp) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int r = warp; r < R; r += nwarps) {
-        const double* row = src + rs * r;
-        int emax = -2000;
-        for (int k = lane; k < K; k += 32) {
-            double v = row[ks * k];
-            if (scale) v *= scale[k];
-            uint64_t bits = (uint64_t)__double_as_longlong(v);
-            int E = (int)((bits >> 52) & 0x7FF);
-            if ((bits & 0x7FFFFFFFFFFFFFFFull) != 0) emax = max(emax, E == 0 ? 1 : E);
+template <bool PASS2>
+__global__ void __launch_bounds__(256) k_oz_split(int R, int K, int s, const double* __restrict__ src, long rs,
+                                                  long ks, const double* __restrict__ scale,
+                                                  __nv_bfloat16* __restrict__ planes, int Rp, int ld,
+                                                  int* __restrict__ rexp) {
+    __shared__ double tile[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    if (rs == 1 && ks != 1) {  // r contiguous
+        for (int kk = ty; kk < 32; kk += 8) {
+            const int r = r0 + tx, k = k0 + kk;
+            double v = (r < R && k < K) ? src[r + ks * (long)k] : 0.0;
+            if (scale && k < K) v *= scale[k];
+            tile[tx][kk] = v;
         }
+    } else {
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int r = r0 + rr, k = k0 + tx;
+            double v = (r < R && k < K) ? src[rs * (long)r + ks * (long)k] : 0.0;
+            if (scale && k < K) v *= scale[k];
+            tile[rr][tx] = v;
+        }
+    }
+    __syncthreads();
+    const int fbits = 7 * s;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, k = k0 + tx;
+        if (r >= R) break;  // uniform over the warp
+        const double v = tile[rr][tx];
+        const uint64_t bits = (uint64_t)__double_as_longlong(v);
+        int E = (int)((bits >> 52) & 0x7FF);
+        if (!PASS2) {
+            int e = ((bits & 0x7FFFFFFFFFFFFFFFull) != 0) ? (E == 0 ? 1 : E) : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        // value = m * 2^(E - 1075) with m < 2^53, so |value| < 2^(E - 1022) = 2^e_r
-        const int er = (emax == -2000) ? 0 : emax - 1022;
-        if (lane == 0) rexp[r] = er;
-        const int fbits = 7 * s;
-        for (int k = lane; k < ld; k += 32) {
+            for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+            if (tx == 0 && e > 0) atomicMax(rexp + r, e);
+        } else {
+            if (k >= ld) continue;
+            const int raw = rexp[r];
             long long X = 0;
-            if (k < K && emax != -2000) {
-                double v = row[ks * k];
-                if (scale) v *= scale[k];
-                uint64_t bits = (uint64_t)__double_as_longlong(v);
-                int E = (int)((bits >> 52) & 0x7FF);
+            if (k < K && raw != 0) {
+                const int er = raw - 1022;
                 uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
                 if (E != 0) mant |= (1ull << 52);
                 else E = 1;
                 // X = round(|v| 2^(fbits - er)) = round(mant 2^(E - 1075 - er + fbits))
-                int sh = E - 1075 - er + fbits;
+                const int sh = E - 1075 - er + fbits;
                 uint64_t mag;
                 if (sh >= 0) mag = mant << sh;  // sh <= fbits - 53 < 11 here
                 else if (sh > -64) mag = (mant + (1ull << (-sh - 1))) >> (-sh);
@@ -170,8 +192,8 @@ __global__ void k_oz_split(int R, int K, int s, const double* __restrict__ src, 
                 if (bits >> 63) X = -X;
             }
             for (int i = 0; i < s; ++i) {
-                int shf = 7 * (s - 1 - i);
-                long long d = (shf > 0) ? ((X + (1ll << (shf - 1))) >> shf) : X;
+                const int shf = 7 * (s - 1 - i);
+                const long long d = (shf > 0) ? ((X + (1ll << (shf - 1))) >> shf) : X;
                 X -= d * (1ll << shf);
                 planes[((size_t)i * Rp + r) * ld + k] = __float2bfloat16_rn((float)d);
             }
@@ -190,7 +212,7 @@ template <int S>
 __global__ void __launch_bounds__(192, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
               int Mp, int Np, const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ D, int ldd,
-              int* err) {
+              int kper, double* __restrict__ part, int* err) {
     constexpr int kOzStages = OzStages<S>::value;
     constexpr int NG = S;                           // groups t = 2 .. S + 1
     constexpr uint32_t A_PLANE = kOzBM * kOzKT * 2;  // 8 KB
@@ -206,7 +228,9 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kOzBM, n0 = blockIdx.y * kOzBN;
-    const int nk = (K + kOzKT - 1) / kOzKT;
+    // split-K: this CTA's K range (kper is a multiple of the exact chunk)
+    const int kbeg = blockIdx.z * kper;
+    const int nk = (min(K, kbeg + kper) - kbeg + kOzKT - 1) / kOzKT;
     const int kt_per_chunk = kOzChunk / kOzKT;
     const int nchunk = (nk + kt_per_chunk - 1) / kt_per_chunk;
 
@@ -242,8 +266,9 @@ __global__ void __launch_bounds__(192, 1)
                 mbar_expect_tx(&full_bar[st], STAGE);
 #pragma unroll
                 for (int i = 0; i < S; ++i) {
-                    tma_load_2d(base + i * A_PLANE, &mapA, &full_bar[st], kt * kOzKT, i * Mp + m0);
-                    tma_load_2d(base + S * A_PLANE + i * B_PLANE, &mapB, &full_bar[st], kt * kOzKT, i * Np + n0);
+                    tma_load_2d(base + i * A_PLANE, &mapA, &full_bar[st], kbeg + kt * kOzKT, i * Mp + m0);
+                    tma_load_2d(base + S * A_PLANE + i * B_PLANE, &mapB, &full_bar[st], kbeg + kt * kOzKT,
+                                i * Np + n0);
                 }
                 ++issued;
             }
@@ -327,11 +352,14 @@ __global__ void __launch_bounds__(192, 1)
         }
         const int row = m0 + warp * 32 + lane;
         if (ok && row < M) {
-            const int er = eA[row];
+            const int er = oz_e(eA[row]);
+            // split-K partials go to part + z M N (column-major, ld M)
+            double* out = (gridDim.z > 1) ? part + (size_t)blockIdx.z * M * N : D;
+            const size_t ldo = (gridDim.z > 1) ? (size_t)M : (size_t)ldd;
 #pragma unroll
             for (int j = 0; j < kOzBN; ++j) {
                 const int col = n0 + j;
-                if (col < N) D[row + (size_t)ldd * col] = ldexp((double)hi[j] + (double)lo[j], er + eB[col]);
+                if (col < N) out[row + ldo * col] = ldexp((double)hi[j] + (double)lo[j], er + oz_e(eB[col]));
             }
         }
     }
@@ -369,17 +397,34 @@ bool oz_map(CUtensorMap* map, const void* base, int K, int rows, int ld, int box
     return r == CUDA_SUCCESS;
 }
 
+// D = sum over the split-K partials (column-major M x N each).
+__global__ void k_oz_reduce(int M, int N, int splits, const double* __restrict__ part, double* __restrict__ D,
+                            int ldd) {
+    const size_t total = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        double sacc = 0.0;
+        for (int z = 0; z < splits; ++z) sacc += part[e + (size_t)z * total];
+        D[(e % M) + (size_t)ldd * (e / M)] = sacc;
+    }
+}
+
 template <int S>
 cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int Mp, int Np,
-                      const int* eA, const int* eB, double* D, int ldd, int* err) {
+                      const int* eA, const int* eB, double* D, int ldd, int kper, int splits, double* part,
+                      int* err) {
     const size_t smem = 1024 + (size_t)OzStages<S>::value * S * (kOzBM * kOzKT * 2 + kOzBN * kOzKT * 2);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN);
-    k_oz_gemm<S><<<grid, 192, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+    dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN, splits);
+    k_oz_gemm<S><<<grid, 192, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err);
+    if (splits > 1) {
+        const size_t total = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
+        k_oz_reduce<<<blocks, 256, 0, st>>>(M, N, splits, part, D, ldd);
+    }
     return cudaGetLastError();
 }
 
@@ -400,27 +445,46 @@ void oz_split(cudaStream_t st, int R, int K, int s, const double* src, int lds, 
 
 void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, long rs, long ks,
                       const double* scale, void* planes, bool is_a, int* rexp) {
-    int Rp = oz_rows_pad(R, is_a ? kOzBM : kOzBN);
-    int warps = std::min(R, 152 * 32);
-    int grid = (warps * 32 + 255) / 256;
-    if (grid < 1) grid = 1;
-    k_oz_split<<<grid, 256, 0, st>>>(R, K, s, src, rs, ks, scale, (__nv_bfloat16*)planes, Rp, oz_ld(K), rexp);
+    if (R <= 0) return;
+    const int Rp = oz_rows_pad(R, is_a ? kOzBM : kOzBN), ld = oz_ld(K);
+    cudaMemsetAsync(rexp, 0, sizeof(int) * (size_t)R, st);
+    const dim3 blk(32, 8);
+    k_oz_split<false><<<dim3((K + 31) / 32, (R + 31) / 32), blk, 0, st>>>(R, K, s, src, rs, ks, scale,
+                                                                           (__nv_bfloat16*)planes, Rp, ld, rexp);
+    k_oz_split<true><<<dim3((ld + 31) / 32, (R + 31) / 32), blk, 0, st>>>(R, K, s, src, rs, ks, scale,
+                                                                          (__nv_bfloat16*)planes, Rp, ld, rexp);
 }
-
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
-                    const void* Bplanes, const int* eB, double* D, int ldd, int* err) {
+                    const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part,
+                    size_t part_cap) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (s < 3 || s > 7) return cudaErrorInvalidValue;
+    // split-K when the output tiles alone cannot fill the GPU
+    const long tiles = (long)((M + kOzBM - 1) / kOzBM) * ((N + kOzBN - 1) / kOzBN);
+    int splits = 1, kper = K;
+    if (part && tiles < 152 && K >= 2 * kOzChunk) {
+        const long chunks = (K + kOzChunk - 1) / kOzChunk;
+        long want = std::min<long>((2 * 152 + tiles - 1) / tiles, chunks);
+        want = std::min<long>(want, (long)(part_cap / ((size_t)M * N)));
+        if (want > 1) {
+            kper = (int)(((chunks + want - 1) / want) * kOzChunk);
+            splits = (K + kper - 1) / kper;
+        }
+        if (splits < 2) {
+            splits = 1;
+            kper = K;
+        }
+    }
     const int Mp = oz_rows_pad(M, kOzBM), Np = oz_rows_pad(N, kOzBN), ld = oz_ld(K);
     CUtensorMap ma, mb;
     if (!oz_map(&ma, Aplanes, K, s * Mp, ld, kOzBM) || !oz_map(&mb, Bplanes, K, s * Np, ld, kOzBN))
         return cudaErrorInvalidValue;
     switch (s) {
-        case 3: return oz_launch<3>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
-        case 4: return oz_launch<4>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
-        case 5: return oz_launch<5>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
-        case 6: return oz_launch<6>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
-        default: return oz_launch<7>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, err);
+        case 3: return oz_launch<3>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
+        case 4: return oz_launch<4>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
+        case 5: return oz_launch<5>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
+        case 6: return oz_launch<6>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
+        default: return oz_launch<7>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
     }
 }
 

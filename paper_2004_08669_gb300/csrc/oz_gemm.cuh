@@ -11,7 +11,8 @@ namespace ctm {
 size_t oz_operand_bytes(int R, int K, int s, bool is_a);
 
 // Split rows src(r, k) = src[k + lds r] (* scale[k]) into s bf16 digit planes
-// and one power-of-two exponent per row (rexp, R ints).
+// and one exponent per row (rexp, R ints: the largest biased FP64 exponent of
+// the row, 0 for a zero row; the row is scaled by 2^(rexp - 1022)).
 void oz_split(cudaStream_t st, int R, int K, int s, const double* src, int lds, const double* scale, void* planes,
               bool is_a, int* rexp);
 
@@ -21,7 +22,10 @@ void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, l
 
 // D (M x N, column-major FP64, ldd) = A . B^t from split operands (A: M rows,
 // B: N rows, length K, s digits, 3 <= s <= 7).  *err (device) set on timeout.
+// part (part_cap doubles, may be null): split-K partials, used when the
+// output tiles alone cannot fill the GPU.
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
-                    const void* Bplanes, const int* eB, double* D, int ldd, int* err);
+                    const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part = nullptr,
+                    size_t part_cap = 0);
 
 }  // namespace ctm
