@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--modes", default="fp64,tf32,bf16",
+    ap.add_argument("--modes", default="ozaki64,fp64,tf32,bf16",
                     help="precision forms to time; the first one gives the headline value")
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--T", type=float, default=0.4398)
@@ -284,6 +284,11 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
     return g, res
 
 
+# the arithmetic each form computes in
+DTYPES = {"fp64": "f64", "ozaki64": "f64-emulated (bf16 x7 digit slices on tcgen05, FP32/double-float accumulation)",
+          "tf32": "tf32 (tcgen05) + f64", "bf16": "bf16 (tcgen05) + f64"}
+
+
 def accuracy_gate(args, blob, local):
     """The mixed forms against the FP64 form on the timed workload: load the
     same checkpointed state into one handle per form, step them side by side,
@@ -375,7 +380,7 @@ def run_ours(args):
             others[p] = {"error": f"{type(e).__name__}: {e}"}
     out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if primary == "fp64" else primary, "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPES.get(primary, primary), "data": "synthetic",
            "config": {"workload": res["workload"], "q": 20, "m": m, "T": args.T, "prec": primary,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (C~ is 210 MB FP64), no flush",

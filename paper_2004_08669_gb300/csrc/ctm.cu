@@ -624,8 +624,9 @@ void stage_extend(ctm_handle* h, const double* E1) {
     pwcontract(h, h->C, E1, &h->ctl->live, h->live);
 }
 
-// Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR2) or
-// 3 (shifted first pass, then CholQR2).  tmp is clobbered.
+// Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR,
+// then one Newton-Schulz correction) or 3 (shifted CholQR, CholQR, then the
+// correction).  tmp is clobbered.
 ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int passes) {
     const Layout& L = h->lay;
     const int N = L.N, b = L.b;
@@ -640,11 +641,20 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
         } else {
             pgemm(h, true, false, b, b, N, cur, N, cur, N, h->G, b, nullptr, gemm_splits(L, b, b, N));
         }
-        double shift_rel = (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
         cudaEvent_t a = prof_begin(h);
-        CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl));
-        ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
-        prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
+        if (i + 1 == passes && passes >= 2) {
+            // The last pass starts from a block orthonormal to ~eps cond^2
+            // (G = I + E, |E| far below 1e-8): Q = Y (3I - G)/2 is
+            // orthonormal to O(|E|^2) and needs no factorisation.
+            ctm::ns_coeff_f64(h->st, b, h->G, b, h->Linv, b);
+            prof_end(h, a, PC_CHOLQR, 1, 0.0, 8.0 * 2.0 * b * b);
+        } else {
+            double shift_rel =
+                (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
+            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl));
+            ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
+            prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
+        }
         if (is_oz(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {cur, 1, N, nullptr}, OZ_SA, true, {h->Linv, 1, b, nullptr}, OZ_SB, true,
                                  out, N);

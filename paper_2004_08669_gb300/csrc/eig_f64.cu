@@ -59,9 +59,12 @@ __device__ __forceinline__ bool jac_above(double app, double aqq, double apq, do
 // (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2),
 // s = t c.  The tangent is taken in FP32: an approximate angle leaves ~1e-7
 // of a_pq instead of zero, which the next sweep removes, so convergence is
-// unaffected.  c is made FP64-accurate from an FP32 reciprocal square root by
-// two Newton-Raphson steps y <- y (3 - x y^2) / 2, and s = t c: the rotation
-// is orthogonal to FP64 rounding, so the similarity transform stays exact.
+// unaffected.  c must be FP64-accurate for the rotation to be orthogonal to
+// FP64 rounding: an FP32 reciprocal square root y0 of x = 1 + t^2 is refined
+// by one Newton-Raphson step y <- y + y (1 - x y^2) / 2 in double-float
+// arithmetic on the FP32 pipe (x and y0^2 split exactly by FMA), and then by
+// one step in FP64; s = t c.  This keeps the dependent FP64 chain, slow on
+// this part, to a few operations.
 __device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, double eps, double floor_abs) {
     Rot R{1.0, 0.0, false};
     if (!jac_above(app, aqq, apq, eps, floor_abs)) return R;
@@ -75,9 +78,23 @@ __device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, doub
         const double tau = d / (2.0 * apq);
         t = fabs(tau) > 1e150 ? 0.5 / tau : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
     }
-    const double x = 1.0 + t * t;
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
+    const double x = fma(t, t, 1.0);
+    double y;
+    const float tf = (float)t;
+    if ((double)tf == t && fabsf(tf) <= 1.0f) {
+        // x = 1 + t^2 as xh + xl (exact: |t| <= 1, t^2 split by FMA)
+        const float t2 = tf * tf, t2e = fmaf(tf, tf, -t2);
+        const float xh = 1.0f + t2, xl = ((1.0f - xh) + t2) + t2e;
+        const float y0 = rsqrtf(xh);
+        // r = 1 - x y0^2 to ~2^-46 (y0^2 and xh y0^2 split by FMA)
+        const float p = y0 * y0, pe = fmaf(y0, y0, -p);
+        const float q = xh * p, qe = fmaf(xh, p, -q) + fmaf(xh, pe, xl * p);
+        const float r = (1.0f - q) - qe;
+        y = (double)y0 + (double)(0.5f * y0 * r);
+    } else {
+        y = (double)rsqrtf((float)x);
+        y = y * (1.5 - 0.5 * x * y * y);
+    }
     y = y * (1.5 - 0.5 * x * y * y);
     R.c = y;
     R.s = t * y;
@@ -395,74 +412,118 @@ __global__ void k_gather_ritz(int n, int npad, const int* __restrict__ rank, con
 // thread, held in registers, with the pivots' reciprocals taken once); the
 // trailing update then runs on 16 x 16 lower tiles, so that it spreads over
 // many SMs (FP64 throughput per SM is low on this part).
+// 1/sqrt(d) for d > 0: FP32 seed refined by two Newton-Raphson steps
+// y <- y (3 - d y^2) / 2 (FP64 square roots and divisions are slow on this
+// part); the library path outside FP32's comfortable range.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
 __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
     __shared__ double D[32][33];
     __shared__ double dinv[32];
+    __shared__ double dinv2[32];
     __shared__ double PI[32][17];  // panel rows of tile I (l-major)
     __shared__ double PJ[32][17];  // panel rows of tile J
+    __shared__ double s_red[8];
     int* err = &ctl->chol_status;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned full = 0xffffffffu;
     unsigned int epoch = 0;
-    double shift = 0.0;
     if (shift_rel > 0.0) {
-        for (int i = 0; i < n; ++i) shift += G[i + (size_t)ld * i];
-        shift *= shift_rel;
-    }
-    if (!grid_sync(&ctl->bar_count, epoch, err)) return;
-    if (shift != 0.0)
+        // trace(G), reduced in the same order in every block
+        double t = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) t += G[i + (size_t)ld * i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+        if (lane == 0) s_red[tid >> 5] = t;
+        __syncthreads();
+        double tr = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tr += s_red[w];
+        const double shift = tr * shift_rel;
+        if (!grid_sync(&ctl->bar_count, epoch, err)) return;
         for (long i = gtid; i < n; i += gstride) G[i + (size_t)ld * i] = __ldcg(G + i + (size_t)ld * i) + shift;
-    if (!grid_sync(&ctl->bar_count, epoch, err)) return;
+        if (!grid_sync(&ctl->bar_count, epoch, err)) return;
+    }
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int kb = min(32, n - k0);
-        // --- diagonal block, factored redundantly in every block
+        // --- diagonal block, factored redundantly in every block by all its
+        //     threads (FP64 work in one warp is slow on this part).  Columns
+        //     stay unscaled until the end: step j subtracts
+        //     D[i][j] D[l][j] / d_j from the trailing entries, and the thread
+        //     that updates the next pivot takes its reciprocal square root.
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int i = e % 32, j = e / 32;
-            D[i][j] = (i < kb && j < kb) ? __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j)) : 0.0;
+            D[i][j] = (i < kb && j < kb && j <= i) ? __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j)) : 0.0;
         }
         __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            if (tid == 0) {
-                double d = D[j][j];
-                if (!(d > 0.0) || !isfinite(d)) {
-                    if (blockIdx.x == 0) atomicMax(err, 1);
-                    d = 1.0;
-                }
-                const double sq = sqrt(d);
-                D[j][j] = sq;
-                dinv[j] = 1.0 / sq;
+        if (tid == 0) {
+            double d = D[0][0];
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (blockIdx.x == 0) atomicMax(err, 1);
+                d = 1.0;
+                D[0][0] = d;
             }
-            __syncthreads();
-            if (tid > j && tid < kb) D[tid][j] *= dinv[j];
-            __syncthreads();
-            for (int e = tid; e < kb * kb; e += blockDim.x) {
-                const int i = e % kb, l = e / kb;
-                if (l > j && i >= l) D[i][l] -= D[i][j] * D[l][j];
+            const double inv = rsqrt_nr(d);
+            dinv[0] = inv;
+            dinv2[0] = inv * inv;
+        }
+        __syncthreads();
+        for (int j = 0; j + 1 < kb; ++j) {
+            const double w = dinv2[j];
+            const int nt = kb - 1 - j;  // trailing order
+            for (int e = tid; e < nt * nt; e += blockDim.x) {
+                const int i = j + 1 + e % nt, l = j + 1 + e / nt;
+                if (l <= i) {
+                    double v = D[i][l] - D[i][j] * D[l][j] * w;
+                    if (i == j + 1 && l == j + 1) {  // the next pivot
+                        if (!(v > 0.0) || !isfinite(v)) {
+                            if (blockIdx.x == 0) atomicMax(err, 1);
+                            v = 1.0;
+                        }
+                        const double inv = rsqrt_nr(v);
+                        dinv[j + 1] = inv;
+                        dinv2[j + 1] = inv * inv;
+                    }
+                    D[i][l] = v;
+                }
             }
             __syncthreads();
         }
+        // scale: L[i][j] = D[i][j] / sqrt(d_j) (i > j), L[j][j] = d_j / sqrt(d_j)
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int i = e % 32, j = e / 32;
+            if (j < kb && i < kb && j <= i) D[i][j] *= dinv[j];
+        }
+        __syncthreads();
         if (blockIdx.x == 0)
             for (int e = tid; e < kb * kb; e += blockDim.x) {
                 const int i = e % kb, j = e / kb;
-                G[(k0 + i) + (size_t)ld * (k0 + j)] = (i >= j) ? D[i][j] : 0.0;
+                G[(k0 + i) + (size_t)ld * (k0 + j)] = D[i][j];
             }
         const int k1 = k0 + kb;
-        // --- panel rows below: L[i, k0:k1] = G[i, k0:k1] L_kk^{-t}
-        for (long i = k1 + gtid; i < n; i += gstride) {
-            double x[32];
+        // --- panel rows below: L[i, k0:k1] = G[i, k0:k1] L_kk^{-t}, one warp
+        //     per row (lane j holds column j), rows spread over the grid
+        {
+            const long gw = gtid >> 5, nw = gstride >> 5;
+            for (long i = k1 + gw; i < n; i += nw) {
+                double acc = (lane < kb) ? __ldcg(G + i + (size_t)ld * (k0 + lane)) : 0.0;
+                double x = 0.0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] = (j < kb) ? __ldcg(G + i + (size_t)ld * (k0 + j)) : 0.0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                double sacc = x[j];
-#pragma unroll
-                for (int l = 0; l < j; ++l) sacc -= x[l] * D[j][l];
-                x[j] = sacc * dinv[j];
+                for (int l = 0; l < 32; ++l) {
+                    if (l < kb) {
+                        const double xl = __shfl_sync(full, acc, l) * dinv[l];
+                        if (lane == l) x = xl;
+                        if (lane > l) acc -= xl * D[lane][l];
+                    }
+                }
+                if (lane < kb) G[i + (size_t)ld * (k0 + lane)] = x;
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < kb) G[i + (size_t)ld * (k0 + j)] = x[j];
         }
         if (!grid_sync(&ctl->bar_count, epoch, err)) return;
         if (k1 >= n) break;
@@ -529,49 +590,74 @@ __global__ void __launch_bounds__(32) k_trinv_diag(int n, const double* __restri
     for (int i = 0; i < 32; ++i) out[i] = x[i];
 }
 
-// X = L^{-1} (lower triangular), one warp per column j, by blocked forward
-// substitution over 32-row blocks: x_J = Dinv_J e_j, then for each later
-// block x_I = -Dinv_I (L_{I, J:I} x_{J:I}), reading L column by column
-// (coalesced over the lanes) against x held in shared memory.
-__global__ void __launch_bounds__(128) k_trinv_cols(int n, const double* __restrict__ L, int ld,
+// X = L^{-1} (lower triangular) by blocked forward substitution over 32-row
+// blocks, eight columns j per CTA (one warp each, all in the same block J):
+// x_J = Dinv_J e_j, then for each later block x_I = -Dinv_I (L_{I, J:I}
+// x_{J:I}).  The 32 x 32 tiles of L are staged in shared memory, shared by
+// the eight warps, with the next tile prefetched into registers.
+__global__ void __launch_bounds__(256) k_trinv_cols(int n, const double* __restrict__ L, int ld,
                                                     const double* __restrict__ Dinv, double* __restrict__ X,
                                                     int ldx) {
     extern __shared__ double tsh[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int npad = ((n + 31) / 32) * 32;
-    double* xs = tsh + (size_t)warp * (npad + 32);
-    double* ys = xs + npad;
-    const int j = blockIdx.x * 4 + warp;
-    if (j >= n) return;
-    const int J = j / 32, c = j % 32, nb = npad / 32;
-    for (int i = lane; i < 32 * J; i += 32) X[i + (size_t)ldx * j] = 0.0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npad = ((n + 31) / 32) * 32, nb = npad / 32;
+    double* xs = tsh + (size_t)warp * npad;  // this warp's column of X
+    double* Tt = tsh + (size_t)8 * npad;     // [2][32][33] tiles of L
+    double* Di = Tt + 2 * 32 * 33;           // [32][33] Dinv_I
+    double* ys = Di + 32 * 33;               // [8][32]
+    const int j0 = blockIdx.x * 8, j = j0 + warp;
+    const bool live_col = j < n;
+    const int J = j0 / 32, c = j % 32;
+    if (live_col)
+        for (int i = lane; i < 32 * J; i += 32) X[i + (size_t)ldx * j] = 0.0;
     {
-        const double v = Dinv[(size_t)1024 * J + 32 * c + lane];  // zero above row c
-        const int r = 32 * J + lane;
-        xs[r] = v;
-        if (r < n) X[r + (size_t)ldx * j] = v;
+        const double v = live_col ? Dinv[(size_t)1024 * J + 32 * c + lane] : 0.0;  // zero above row c
+        xs[32 * J + lane] = v;
+        if (live_col && 32 * J + lane < n) X[(32 * J + lane) + (size_t)ldx * j] = v;
     }
-    __syncwarp();
+    double reg[4];
     for (int I = J + 1; I < nb; ++I) {
-        const int r = 32 * I + lane;
-        const bool live = r < n;
-        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
-        const double* Lr = L + (live ? r : 0);
-        for (int col = 32 * J; col < 32 * I; col += 4) {
-            y0 = fma(live ? Lr[(size_t)ld * col] : 0.0, xs[col], y0);
-            y1 = fma(live ? Lr[(size_t)ld * (col + 1)] : 0.0, xs[col + 1], y1);
-            y2 = fma(live ? Lr[(size_t)ld * (col + 2)] : 0.0, xs[col + 2], y2);
-            y3 = fma(live ? Lr[(size_t)ld * (col + 3)] : 0.0, xs[col + 3], y3);
+        __syncthreads();  // Di and the tiles of the previous I are consumed
+        for (int e = tid; e < 1024; e += 256) Di[(e % 32) * 33 + e / 32] = Dinv[(size_t)1024 * I + e];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, r = 32 * I + (e % 32), col = 32 * J + e / 32;
+            reg[q] = (r < n) ? L[r + (size_t)ld * col] : 0.0;
         }
-        ys[lane] = (y0 + y1) + (y2 + y3);
+        double y0 = 0.0, y1 = 0.0;
+        for (int kb = J, buf = 0; kb < I; ++kb, buf ^= 1) {
+            double* T = Tt + buf * 32 * 33;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                T[(e % 32) * 33 + e / 32] = reg[q];
+            }
+            __syncthreads();
+            if (kb + 1 < I) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = tid + 256 * q, r = 32 * I + (e % 32), col = 32 * (kb + 1) + e / 32;
+                    reg[q] = (r < n) ? L[r + (size_t)ld * col] : 0.0;
+                }
+            }
+            const double* xk = xs + 32 * kb;
+#pragma unroll
+            for (int cc = 0; cc < 32; cc += 2) {
+                y0 = fma(T[lane * 33 + cc], xk[cc], y0);
+                y1 = fma(T[lane * 33 + cc + 1], xk[cc + 1], y1);
+            }
+        }
+        ys[warp * 32 + lane] = y0 + y1;
         __syncwarp();
-        const double* Di = Dinv + (size_t)1024 * I;
-        double xi = 0.0;
-#pragma unroll 8
-        for (int s2 = 0; s2 < 32; ++s2) xi = fma(Di[lane + 32 * s2], ys[s2], xi);
-        xi = -xi;
-        xs[r] = xi;
-        if (live) X[r + (size_t)ldx * j] = xi;
+        double xi0 = 0.0, xi1 = 0.0;
+#pragma unroll
+        for (int s2 = 0; s2 < 32; s2 += 2) {
+            xi0 = fma(Di[lane * 33 + s2], ys[warp * 32 + s2], xi0);
+            xi1 = fma(Di[lane * 33 + s2 + 1], ys[warp * 32 + s2 + 1], xi1);
+        }
+        const double xi = -(xi0 + xi1);
+        xs[32 * I + lane] = xi;
+        if (live_col && 32 * I + lane < n) X[(32 * I + lane) + (size_t)ldx * j] = xi;
         __syncwarp();
     }
 }
@@ -863,9 +949,29 @@ void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int l
     // scratch: ceil(n / 32) * 1024 doubles (the diagonal blocks' inverses)
     const int nb = (n + 31) / 32;
     k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch);
-    const size_t smem = 4 * (size_t)(nb * 32 + 32) * sizeof(double);
-    k_trinv_cols<<<(n + 3) / 4, 128, smem, st>>>(n, L, ld, scratch, X, ldx);
+    const size_t smem = ((size_t)8 * nb * 32 + 3 * 32 * 33 + 8 * 32) * sizeof(double);
+    static size_t attr = 48 * 1024;
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_trinv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_trinv_cols<<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx);
 }
+
+// X = (3 I - (G + G^t)/2) / 2.
+__global__ void k_ns_coeff(int b, const double* __restrict__ G, int ldg, double* __restrict__ X, int ldx) {
+    const size_t tot = (size_t)b * b;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % b), j = (int)(e / b);
+        const double g = 0.5 * (G[i + (size_t)ldg * j] + G[j + (size_t)ldg * i]);
+        X[i + (size_t)ldx * j] = (i == j ? 1.5 : 0.0) - 0.5 * g;
+    }
+}
+
+void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, int ldx) {
+    k_ns_coeff<<<grid_for((size_t)b * b), 256, 0, st>>>(b, G, ldg, X, ldx);
+}
+
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
                const double* theta, double* res) {
     if (ncol <= 0) return;

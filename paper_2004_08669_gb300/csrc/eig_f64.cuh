@@ -62,6 +62,10 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);
 
+// X = (3 I - (G + G^t)/2) / 2: the Newton-Schulz orthogonality correction
+// of a block whose Gram matrix G is close to I.
+void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, int ldx);
+
 // X = L^{-1} for lower-triangular L (upper part of X zeroed); scratch:
 // ceil(n / 32) * 1024 doubles.
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch);
