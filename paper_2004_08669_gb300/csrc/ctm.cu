@@ -577,13 +577,14 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
 
 inline bool is_oz(const ctm_handle* h) { return h->lay.prec == CTM_OZAKI64; }
 
-void pwcontract(ctm_handle* h, double* X, const double* E1, const int* live_dev, int live_host) {
+void pwcontract(ctm_handle* h, double* X, const double* E1, const int* live_dev, int live_host, bool sym = false) {
     const Layout& L = h->lay;
     cudaEvent_t a = prof_begin(h);
     // FP64 form: FP64; Ozaki form: double-float (its products carry ~2^-42);
     // TF32 / BF16 forms: FP32 (far below their operand rounding)
     const int arith = (L.prec == CTM_FP64) ? 0 : (L.prec == CTM_OZAKI64 ? 2 : 1);
-    ctm::wcontract_ar(h->st, arith, L.m, L.q, X, L.N, h->E, E1, live_dev);
+    // the symmetric variant needs a symmetric X and E1 = E
+    ctm::wcontract_ar(h->st, arith, L.m, L.q, X, L.N, h->E, E1, live_dev, sym && E1 == h->E);
     double nb = (double)live_host * live_host, q = L.q;
     prof_end(h, a, PC_WCONTRACT, 1, nb * 4.0 * q * q * q, nb * 2.0 * 8.0 * q * q);
 }
@@ -621,7 +622,7 @@ void stage_extend(ctm_handle* h, const double* E1) {
     } else {
         pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega);
     }
-    pwcontract(h, h->C, E1, &h->ctl->live, h->live);
+    pwcontract(h, h->C, E1, &h->ctl->live, h->live, true);  // X1 is symmetric
 }
 
 // Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR,

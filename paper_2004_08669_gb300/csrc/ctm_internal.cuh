@@ -91,12 +91,14 @@ int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, dou
 // Blockwise vertex-weight contraction, in place on an N x N matrix (spin-fastest
 // index): every q x q block X_{gamma gamma'} becomes E o (E (X o E1) E), where
 // E1 is E (plain weight) or E o h (bond impurity).  Blocks with gamma or
-// gamma' >= *live are zero and skipped.
+// gamma' >= *live are zero and skipped.  sym: X is symmetric and E1 = E, so
+// only the blocks gamma >= gamma' are contracted and their transposes written
+// (the result is then exactly symmetric).
 void wcontract_f64(cudaStream_t st, int m, int q, double* X, int ldx, const double* E,
-                   const double* E1, const int* live);
+                   const double* E1, const int* live, bool sym = false);
 
 // The same contraction with arithmetic 0 = FP64, 1 = FP32, 2 = double-float.
 void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, const double* E, const double* E1,
-                  const int* live);
+                  const int* live, bool sym = false);
 
 }  // namespace ctm

@@ -134,10 +134,25 @@ __global__ void k_splitk_reduce(int M, int N, int splits, const double* __restri
     }
 }
 
+// Block (g, g') of the blk-th contraction: all live^2 blocks, or with sym the
+// lower triangle g >= g' only (row by row), whose transposes are written too.
+__device__ __forceinline__ void wc_block(long blk, int live, bool sym, int& g, int& gp) {
+    if (!sym) {
+        g = (int)(blk % live);
+        gp = (int)(blk / live);
+        return;
+    }
+    int gg = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+    while (gg > 0 && (long)gg * (gg + 1) / 2 > blk) --gg;
+    while ((long)(gg + 1) * (gg + 2) / 2 <= blk) ++gg;
+    g = gg;
+    gp = (int)(blk - (long)gg * (gg + 1) / 2);
+}
+
 // One thread per element of nb q x q blocks at a time.
 __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
                             const double* __restrict__ E, const double* __restrict__ E1,
-                            const int* __restrict__ live_ptr) {
+                            const int* __restrict__ live_ptr, bool sym) {
     extern __shared__ double sh[];
     const int q2 = q * q;
     const int nb = max(1, (int)blockDim.x / q2);
@@ -150,7 +165,7 @@ __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
         sE1[e] = E1[e];
     }
     const int live = min(*live_ptr, m);
-    const long nblk = (long)live * live;
+    const long nblk = sym ? (long)live * (live + 1) / 2 : (long)live * live;
     const int jb = threadIdx.x / q2;       // local block slot
     const int el = threadIdx.x - jb * q2;  // element within the block
     const bool act = jb < nb;
@@ -159,10 +174,12 @@ __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
     for (long base = (long)blockIdx.x * nb; base < nblk; base += (long)gridDim.x * nb) {
         long blk = base + jb;
         bool ok = act && blk < nblk;
-        size_t off = 0;
+        size_t off = 0, offT = 0;
+        int g = 0, gp = 0;
         if (ok) {
-            int g = (int)(blk % live), gp = (int)(blk / live);
+            wc_block(blk, live, sym, g, gp);
             off = (size_t)q * g + (size_t)ldx * ((size_t)q * gp);
+            offT = (size_t)q * gp + (size_t)ldx * ((size_t)q * g);
             G[jb * q2 + el] = X[off + i + (size_t)ldx * j] * sE1[el];  // M o E1
         }
         __syncthreads();
@@ -175,7 +192,9 @@ __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
         if (ok) {  // out = E o (E T1)
             double s = 0.0;
             for (int k = 0; k < q; ++k) s = fma(sE[i + q * k], T1[jb * q2 + k + q * j], s);
-            X[off + i + (size_t)ldx * j] = sE[el] * s;
+            const double v = sE[el] * s;
+            X[off + i + (size_t)ldx * j] = v;
+            if (sym && g != gp) X[offT + j + (size_t)ldx * i] = v;
         }
         __syncthreads();
     }
@@ -187,11 +206,15 @@ __global__ void k_wcontract(int m, int q, double* __restrict__ X, int ldx,
 // pipe is 64 times faster than its FP64 pipe.
 struct ArF32 {
     using T = float;
+    struct Acc {
+        float s;
+    };
     __device__ static T load(double x) { return (float)x; }
     __device__ static double store(T a) { return (double)a; }
     __device__ static T mul(T a, T b) { return a * b; }
-    __device__ static T fma(T a, T b, T c) { return fmaf(a, b, c); }
-    __device__ static T zero() { return 0.f; }
+    __device__ static Acc acc0() { return Acc{0.f}; }
+    __device__ static void acc(Acc& c, T a, T b) { c.s = fmaf(a, b, c.s); }
+    __device__ static T fin(Acc c) { return c.s; }
 };
 
 struct ArDF {
@@ -218,13 +241,28 @@ struct ArDF {
         e += a.y + b.y;
         return quick(s, e);
     }
-    __device__ static T fma(T a, T b, T c) { return add(mul(a, b), c); }
-    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    // Dot products in the manner of Ogita, Rump and Oishi's Dot2: the high
+    // parts' products are summed by error-free two-sums, every low-order
+    // term into one float, normalised once at the end.
+    struct Acc {
+        float h, l;
+    };
+    __device__ static Acc acc0() { return Acc{0.f, 0.f}; }
+    __device__ static void acc(Acc& c, T a, T b) {
+        const float p = a.x * b.x;
+        const float pe = fmaf(a.x, b.x, -p);
+        const float sum = c.h + p;
+        const float bb = sum - c.h;
+        const float e = (c.h - (sum - bb)) + (p - bb);
+        c.h = sum;
+        c.l += (e + pe) + fmaf(a.x, b.y, a.y * b.x);
+    }
+    __device__ static T fin(Acc c) { return quick(c.h, c.l); }
 };
 
 template <class Ar>
 __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, const double* __restrict__ E,
-                               const double* __restrict__ E1, const int* __restrict__ live_ptr) {
+                               const double* __restrict__ E1, const int* __restrict__ live_ptr, bool sym) {
     using T = typename Ar::T;
     extern __shared__ __align__(16) unsigned char sh_raw[];
     T* sh = (T*)sh_raw;
@@ -239,7 +277,7 @@ __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, co
         sE1[e] = Ar::load(E1[e]);
     }
     const int live = min(*live_ptr, m);
-    const long nblk = (long)live * live;
+    const long nblk = sym ? (long)live * (live + 1) / 2 : (long)live * live;
     const int jb = threadIdx.x / q2;
     const int el = threadIdx.x - jb * q2;
     const bool act = jb < nb;
@@ -248,23 +286,27 @@ __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, co
     for (long base = (long)blockIdx.x * nb; base < nblk; base += (long)gridDim.x * nb) {
         long blk = base + jb;
         bool ok = act && blk < nblk;
-        size_t off = 0;
+        size_t off = 0, offT = 0;
+        int g = 0, gp = 0;
         if (ok) {
-            int g = (int)(blk % live), gp = (int)(blk / live);
+            wc_block(blk, live, sym, g, gp);
             off = (size_t)q * g + (size_t)ldx * ((size_t)q * gp);
+            offT = (size_t)q * gp + (size_t)ldx * ((size_t)q * g);
             G[jb * q2 + el] = Ar::mul(Ar::load(X[off + i + (size_t)ldx * j]), sE1[el]);
         }
         __syncthreads();
         if (ok) {
-            T s = Ar::zero();
-            for (int k = 0; k < q; ++k) s = Ar::fma(G[jb * q2 + i + q * k], sE[k + q * j], s);
-            T1[jb * q2 + el] = s;
+            typename Ar::Acc c = Ar::acc0();
+            for (int k = 0; k < q; ++k) Ar::acc(c, G[jb * q2 + i + q * k], sE[k + q * j]);
+            T1[jb * q2 + el] = Ar::fin(c);
         }
         __syncthreads();
         if (ok) {
-            T s = Ar::zero();
-            for (int k = 0; k < q; ++k) s = Ar::fma(sE[i + q * k], T1[jb * q2 + k + q * j], s);
-            X[off + i + (size_t)ldx * j] = Ar::store(Ar::mul(sE[el], s));
+            typename Ar::Acc c = Ar::acc0();
+            for (int k = 0; k < q; ++k) Ar::acc(c, sE[i + q * k], T1[jb * q2 + k + q * j]);
+            const double v = Ar::store(Ar::mul(sE[el], Ar::fin(c)));
+            X[off + i + (size_t)ldx * j] = v;
+            if (sym && g != gp) X[offT + j + (size_t)ldx * i] = v;
         }
         __syncthreads();
     }
@@ -273,9 +315,9 @@ __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, co
 }  // namespace
 
 void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, const double* E, const double* E1,
-                  const int* live) {
+                  const int* live, bool sym) {
     if (arith == 0) {
-        wcontract_f64(st, m, q, X, ldx, E, E1, live);
+        wcontract_f64(st, m, q, X, ldx, E, E1, live, sym);
         return;
     }
     int q2 = q * q;
@@ -288,10 +330,10 @@ void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, 
     if (grid < 1) grid = 1;
     if (arith == 1) {
         size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float);
-        k_wcontract_ar<ArF32><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live);
+        k_wcontract_ar<ArF32><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
     } else {
         size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float2);
-        k_wcontract_ar<ArDF><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live);
+        k_wcontract_ar<ArDF><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
     }
 }
 
@@ -325,7 +367,7 @@ int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, dou
 }
 
 void wcontract_f64(cudaStream_t st, int m, int q, double* X, int ldx, const double* E,
-                   const double* E1, const int* live) {
+                   const double* E1, const int* live, bool sym) {
     int q2 = q * q;
     int threads = q2 <= 256 ? 256 : ((q2 + 31) / 32) * 32;
     int nb = threads / q2;
@@ -335,7 +377,7 @@ void wcontract_f64(cudaStream_t st, int m, int q, double* X, int ldx, const doub
     long grid = (nblk + nb - 1) / nb;
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
-    k_wcontract<<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live);
+    k_wcontract<<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
 }
 
 }  // namespace ctm

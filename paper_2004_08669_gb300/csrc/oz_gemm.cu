@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256) k_oz_split(int R, int K, int s, const dou
                 const int shf = 7 * (s - 1 - i);
                 const long long d = (shf > 0) ? ((X + (1ll << (shf - 1))) >> shf) : X;
                 X -= d * (1ll << shf);
-                planes[((size_t)i * Rp + r) * ld + k] = __float2bfloat16_rn((float)d);
+                // |d| <= 128: an int32 conversion (int64 ones run on the slow FP64 pipe)
+                planes[((size_t)i * Rp + r) * ld + k] = __float2bfloat16_rn((float)(int)d);
             }
         }
     }
