@@ -258,25 +258,31 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
     ms_max = float(ms_t.item())
     kern = {k: v for k, v in prof.items() if k != "all" and v["ms"] > 0}
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    # roofline of the contraction kernel of this mode (the dominant one in the
-    # FP64 form): algorithmic FLOPs of its launches / their event-timed duration
-    ck = {"fp64": "gemm_f64", "ozaki64": "oz_gemm"}.get(prec, "tc_gemm")
-    d = kern[ck]
-    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    # roofline of the dominant kernel class (algorithmic FLOPs of its launches /
+    # their event-timed duration), and of the tensor-core contraction class
     workload = f"dodecahedron q=20 m={m} T={args.T} {prec}"
-    if prec == "fp64":
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
-        roof = {"kernel": ck, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for(ck, workload),
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock"}
-    else:
-        peak, src = tensor_peak(prec)
-        roof = {"kernel": ck, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for(ck, workload), "peak_source": src}
-    roof.update({"share_of_step": d["ms"] / ms, "launches": d["launches"], "dominant_kernel": dom})
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+
+    def roof_of(cls):
+        d = kern[cls]
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        if cls in ("oz_gemm", "tc_gemm"):
+            peak, src = tensor_peak(prec)
+            r = {"kernel": cls, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": traffic_for(cls, workload), "peak_source": src}
+        else:
+            peak = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+            r = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": traffic_for(cls, workload),
+                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock"}
+        r.update({"share_of_step": d["ms"] / ms, "launches": d["launches"]})
+        return r
+
+    roof = roof_of(dom)
+    tcls = {"ozaki64": "oz_gemm", "tf32": "tc_gemm", "bf16": "tc_gemm"}.get(prec)
+    roof_t = roof_of(tcls) if tcls in kern else None
     res = {"prec": prec, "value": world * timed_steps / (ms_max / 1e3), "ms_per_step": ms_max / timed_steps,
-           "roofline": roof, "gpu_launches": launches, "clocks": clk,
+           "roofline": roof, "roofline_tensor": roof_t, "gpu_launches": launches, "clocks": clk,
            "subspace_iters_mean": float(np.mean(iters)), "jacobi_sweeps_mean": float(np.mean(sweeps)),
            "rayleigh_ritz_paths": rr_paths,
            "kernels_ms_per_step": {k: round(v["ms"] / timed_steps, 3) for k, v in kern.items()},
@@ -373,7 +379,7 @@ def run_ours(args):
         try:
             g2, r2 = run_mode(args, p, local, world, barrier, args.steps)
             g2.close()
-            others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "gpu_launches",
+            others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "roofline_tensor", "gpu_launches",
                                             "subspace_iters_mean", "jacobi_sweeps_mean", "rayleigh_ritz_paths",
                                             "kernels_ms_per_step", "clocks")}
         except Exception as e:  # a failing form must not lose the others' numbers
@@ -388,7 +394,8 @@ def run_ours(args):
                       "subspace_iters_mean": res["subspace_iters_mean"],
                       "jacobi_sweeps_mean": res["jacobi_sweeps_mean"],
                       "rayleigh_ritz_paths": res["rayleigh_ritz_paths"], "prep_steps": args.prep},
-           "roofline": res["roofline"], "e2e": e2e, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
+           "roofline": res["roofline"], "roofline_tensor": res["roofline_tensor"], "e2e": e2e,
+           "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
            "kernels_ms_per_step": res["kernels_ms_per_step"]}
     if others:
         out["other_modes"] = others

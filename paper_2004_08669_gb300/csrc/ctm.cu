@@ -178,6 +178,7 @@ struct ctm_handle {
     double last_resid = 0.0;                  // last Ritz residual / |w_1|
     int rr_fail_streak = 0;                   // consecutive failed refinements
     double resid_rate = 0.5;                  // measured Ritz residual reduction per iteration
+    int jac_rec = -1;                         // profile record of the last Jacobi solve
     ctm::DevCtl* ctl;
     ctm::DevCtl* hctl = nullptr;  // pinned mirror
     // host-side iteration state
@@ -770,6 +771,8 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             ++h->rr_refined;
         }
         prof_end(h, ja, PC_JACOBI, nk_rr);
+        // the solve's algorithmic FLOPs are known after the next sync
+        h->jac_rec = (used < 0 && h->prof_on && ja) ? (int)h->recs.size() - 1 : -1;
         if (is_oz(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {h->V, 1, N, nullptr}, OZ_SA, true, {h->Sb, b, 1, nullptr}, OZ_SB, true,
                                  h->Z, N);
@@ -788,6 +791,15 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         ctm_status s = sync_ctl(h);
         if (s != CTM_OK) return s;
         h->last_resid = h->hctl->resid;
+        if (h->jac_rec >= 0 && h->jac_rec < (int)h->recs.size()) {
+            // a rotation of (p, q) updates rows p, q and columns p, q of A and
+            // columns p, q of S: 3 x 2 x npad elements at 3 FLOP each
+            long long nrot = 0;
+            for (int k = 0; k < 64; ++k) nrot += h->hctl->rot_count[k];
+            const int np = b + (b & 1);
+            h->recs[h->jac_rec].flops = 18.0 * np * (double)nrot;
+            h->jac_rec = -1;
+        }
         if (meas_here && r_meas > 0.0 && h->last_resid > 0.0 && it > it_meas) {
             const double rate = std::pow(h->last_resid / r_meas, 1.0 / (double)(it - it_meas));
             if (std::isfinite(rate)) h->resid_rate = std::min(0.999, std::max(1e-3, rate));
