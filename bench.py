@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling mode: prepare the first form's workload as the timed run does, then run this "
+                         "many steps between cudaProfilerStart/Stop (for ncu --profile-from-start off); "
+                         "prints no measurement")
     ap.add_argument("--gate-steps", type=int, default=20,
                     help="steps of the mixed-vs-FP64 comparison from the timed state (0: skip)")
     return ap.parse_args()
@@ -409,8 +413,33 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """The timed workload's steps bracketed for a profiler, nothing measured."""
+    import torch
+
+    from paper_2004_08669_gb300 import build, ctm, workloads as W
+    build.build()
+    prec = args.modes.split(",")[0]
+    g = ctm.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T, prec=prec, device="cuda:0",
+                  max_subspace_iters=args.subspace_iters)
+    g.step(args.prep)
+    for _ in range(max(args.warmup, 0)):
+        g.step(1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.profile_steps):
+        g.step(1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    g.close()
+    print(json.dumps({"profile_steps": args.profile_steps, "prec": prec, "m": args.m}))
+
+
 def main():
     args = parse()
+    if args.profile_steps > 0:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
