@@ -47,6 +47,29 @@ struct DevCtl {
     double oa_maxE;
 };
 
+// FP32 -> FP64 by bit construction (the conversion instruction runs on the
+// FP64 pipe, which is slow on this part); zero, subnormal and non-finite
+// inputs take the instruction.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t ex = (u >> 23) & 0xFFu;
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((uint64_t)(u >> 31) << 63));
+    if (ex == 0u || ex == 0xFFu) return (double)x;
+    return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | ((uint64_t)(ex + 896u) << 52) |
+                                            ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// v * 2^e by adding e to the exponent field; ldexp when the input or the
+// result is zero, subnormal, non-finite or out of range.
+__device__ __forceinline__ double scale_pow2(double v, int e) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FFu);
+    if ((b << 1) == 0u) return v;
+    const int ne = ex + e;
+    if (ex == 0 || ex == 0x7FF || ne <= 0 || ne >= 0x7FF) return ldexp(v, e);
+    return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((uint64_t)ne << 52)));
+}
+
 // Grid-wide barrier for cooperative launches on a monotonic arrival counter:
 // the host zeroes *count before the launch, and a block's e-th barrier waits
 // until e * gridDim.x arrivals are counted (one release-add per block, then

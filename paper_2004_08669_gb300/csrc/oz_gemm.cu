@@ -15,7 +15,7 @@
 // Pairs with i + j <= s + 1 are kept; pairs of equal t = i + j share one
 // TMEM accumulator.  Over a K-chunk of 512 the FP32 accumulation of every
 // group is exact (all partial sums are integers below 2^24 for s <= 6), so
-// after each chunk the four epilogue warps read the groups back, scale them
+// after each chunk the eight epilogue warps read the groups back, scale them
 // by 2^{-7t} (exact) and add them into a double-float (hi, lo) accumulator
 // per output element; the end result is written in FP64.  A producer warp
 // streams all digit planes of a 32-wide K-tile per stage (3-stage TMA ring,
@@ -210,7 +210,7 @@ struct OzStages {
 };
 
 template <int S>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
               int Mp, int Np, const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ D, int ldd,
               int kper, double* __restrict__ part, int* err) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, 128);
+        mbar_init(&acc_empty, 256);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 4) {
+    if (warp == 8) {
         // ---- producer: all digit planes of one K-tile per stage
         if (lane == 0) {
             int issued = 0;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int kt = (issued > kOzStages ? issued - kOzStages : 0); kt < issued; ++kt)
                 mbar_wait(&full_bar[kt % kOzStages], (kt / kOzStages) & 1, err);
         }
-    } else if (warp == 5) {
+    } else if (warp == 9) {
         // ---- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
@@ -323,10 +323,14 @@ __global__ void __launch_bounds__(192, 1)
             if (!ok) mma_commit(&acc_full);
         }
     } else {
-        // ---- epilogue warps 0..3: TMEM lanes 32 w .. 32 w + 31 = tile rows
-        float hi[kOzBN], lo[kOzBN];
+        // ---- epilogue warps 0..7: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        // (tile rows) and columns 32 (w / 4) .. + 31, so that each thread holds
+        // 32 double-float accumulators
+        const int quad = warp & 3, half = warp >> 2;
+        constexpr int EC = kOzBN / 2;
+        float hi[EC], lo[EC];
 #pragma unroll
-        for (int j = 0; j < kOzBN; ++j) {
+        for (int j = 0; j < EC; ++j) {
             hi[j] = 0.f;
             lo[j] = 0.f;
         }
@@ -340,27 +344,25 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll 1
             for (int g = 0; g < NG; ++g) {
                 const float sc = exp2f(-7.0f * (float)(g + 2));
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * kOzBN + half * EC), v);
 #pragma unroll
-                for (int cb = 0; cb < kOzBN; cb += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kOzBN + cb), v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) df_add(hi[cb + j], lo[cb + j], v[j] * sc);
-                }
+                for (int j = 0; j < EC; ++j) df_add(hi[j], lo[j], v[j] * sc);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&acc_empty);
         }
-        const int row = m0 + warp * 32 + lane;
+        const int row = m0 + quad * 32 + lane;
         if (ok && row < M) {
             const int er = oz_e(eA[row]);
             // split-K partials go to part + z M N (column-major, ld M)
             double* out = (gridDim.z > 1) ? part + (size_t)blockIdx.z * M * N : D;
             const size_t ldo = (gridDim.z > 1) ? (size_t)M : (size_t)ldd;
 #pragma unroll
-            for (int j = 0; j < kOzBN; ++j) {
-                const int col = n0 + j;
-                if (col < N) out[row + ldo * col] = ldexp((double)hi[j] + (double)lo[j], er + oz_e(eB[col]));
+            for (int j = 0; j < EC; ++j) {
+                const int col = n0 + half * EC + j;
+                if (col < N)
+                    out[row + ldo * col] = scale_pow2(f2d_bits(hi[j]) + f2d_bits(lo[j]), er + oz_e(eB[col]));
             }
         }
     }
@@ -420,7 +422,7 @@ cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
         attr = true;
     }
     dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN, splits);
-    k_oz_gemm<S><<<grid, 192, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err);
+    k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err);
     if (splits > 1) {
         const size_t total = (size_t)M * N;
         const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
