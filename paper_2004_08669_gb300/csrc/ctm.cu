@@ -764,7 +764,10 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             // Full FP64 accuracy: the corner is stored diagonal in the Ritz
             // basis, so any coupling left unrotated enters the next extension
             // at first order.
-            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl));
+            // the mixed-precision forms solve in double-float (FP32 pipe); the
+            // FP64 form in FP64
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, 0.0, 0.0,
+                                     h->lay.prec != CTM_FP64));
             nk_rr += 4;
             ++h->rr_jacobi;
         } else {

@@ -102,8 +102,113 @@ __device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, doub
     return R;
 }
 
+// Arithmetic of the Jacobi solver.  J64: FP64 throughout.  JDF: A and S held
+// as double-float pairs (hi + lo floats, ~48 significant bits) and all
+// arithmetic on the FP32 pipe (FP64 on this part is 64x slower in throughput
+// and 14x in latency); used by the mixed-precision forms, whose contractions
+// carry errors of the same order.
+struct J64 {
+    using T = double;
+    struct R {
+        T c, s;
+        bool on;
+    };
+    __device__ static T ld(const T* p) { return __ldcg(p); }
+    __device__ static T from(double x) { return x; }
+    __device__ static double to(T a) { return a; }
+    __device__ static T zero() { return 0.0; }
+    __device__ static T one() { return 1.0; }
+    __device__ static T neg(T a) { return -a; }
+    __device__ static T half(T a) { return 0.5 * a; }
+    __device__ static T add(T a, T b) { return a + b; }
+    __device__ static T lin(T a, T x, T b, T y) { return a * x - b * y; }  // a x - b y
+    __device__ static bool nz(T a) { return a != 0.0; }
+    __device__ static bool above(T app, T aqq, T apq, double eps, double floor_abs) {
+        return jac_above(app, aqq, apq, eps, floor_abs);
+    }
+    __device__ static R rot(T app, T aqq, T apq, double eps, double floor_abs) {
+        const Rot r = rot_fast(app, aqq, apq, eps, floor_abs);
+        return R{r.c, r.s, r.on};
+    }
+};
+
+struct JDF {
+    using T = float2;  // x = hi, y = lo
+    struct R {
+        T c, s;
+        bool on;
+    };
+    __device__ static T quick(float s, float e) {
+        const float h = s + e;
+        return make_float2(h, e - (h - s));
+    }
+    __device__ static T ld(const T* p) { return __ldcg(p); }
+    __device__ static T from(double x) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    }
+    __device__ static double to(T a) { return (double)a.x + (double)a.y; }
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    __device__ static T one() { return make_float2(1.f, 0.f); }
+    __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
+    __device__ static T half(T a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+    __device__ static T add(T a, T b) {  // Knuth's two-sum on the high parts
+        const float s = a.x + b.x, bb = s - a.x;
+        const float e = (a.x - (s - bb)) + (b.x - bb);
+        return quick(s, e + (a.y + b.y));
+    }
+    // a x - b y with both products' rounding errors kept (two-product by FMA)
+    // and the high parts summed by a two-sum, normalised once
+    __device__ static T lin(T a, T x, T b, T y) {
+        const float p1 = a.x * x.x, e1 = fmaf(a.x, x.x, -p1);
+        const float p2 = -b.x * y.x, e2 = fmaf(-b.x, y.x, -p2);
+        const float s = p1 + p2, bb = s - p1;
+        const float e = (p1 - (s - bb)) + (p2 - bb);
+        const float lo = ((e + e1) + e2) + (fmaf(a.x, x.y, a.y * x.x) - fmaf(b.x, y.y, b.y * y.x));
+        return quick(s, lo);
+    }
+    __device__ static bool nz(T a) { return a.x != 0.f; }
+    __device__ static T mul(T a, T b) {
+        const float p = a.x * b.x;
+        return quick(p, fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x));
+    }
+    __device__ static bool above(T app, T aqq, T apq, double eps, double floor_abs) {
+        if (apq.x == 0.f) return false;
+        const float a = fabsf(apq.x);
+        if (!(a > (float)floor_abs)) return false;
+        return a > (float)eps * sqrtf(fabsf(app.x)) * sqrtf(fabsf(aqq.x));
+    }
+    // The rotation of rot_fast in double-float: FP32 tangent, then c = 1/sqrt(1
+    // + t^2) from an FP32 seed by two double-float Newton steps, s = t c.
+    __device__ static R rot(T app, T aqq, T apq, double eps, double floor_abs) {
+        R out{one(), zero(), false};
+        if (!above(app, aqq, apq, eps, floor_abs)) return out;
+        const T d = add(aqq, neg(app));
+        const float tau = d.x / (2.0f * apq.x);
+        const float t = fabsf(tau) > 1e18f ? 0.5f / tau
+                                           : copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+        // x = 1 + t^2 exactly as a pair (|t| <= 1)
+        const float t2 = t * t, t2e = fmaf(t, t, -t2);
+        const float xh = 1.0f + t2;
+        const T x = quick(xh, ((1.0f - xh) + t2) + t2e);
+        T y = make_float2(rsqrtf(xh), 0.f);
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const T r = add(one(), neg(mul(x, mul(y, y))));  // 1 - x y^2, small
+            y = add(y, make_float2(0.5f * y.x * r.x, 0.f));
+        }
+        out.c = y;
+        const float sh = t * y.x;
+        out.s = quick(sh, fmaf(t, y.x, -sh) + t * y.y);
+        out.on = true;
+        return out;
+    }
+};
+
+template <class JA>
 __global__ void k_jacobi_init(int n, int npad, const double* __restrict__ H, int ldh,
-                              double* __restrict__ A0, double* __restrict__ S, int* __restrict__ act) {
+                              typename JA::T* __restrict__ A0, typename JA::T* __restrict__ S,
+                              int* __restrict__ act) {
     size_t tot = (size_t)npad * npad;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -111,8 +216,8 @@ __global__ void k_jacobi_init(int n, int npad, const double* __restrict__ H, int
         if (j == 0) act[i] = 0;
         double v = 0.0;
         if (i < n && j < n) v = 0.5 * (H[i + (size_t)ldh * j] + H[j + (size_t)ldh * i]);
-        A0[e] = v;
-        S[e] = (i == j) ? 1.0 : 0.0;
+        A0[e] = JA::from(v);
+        S[e] = (i == j) ? JA::one() : JA::zero();
     }
 }
 
@@ -153,13 +258,15 @@ constexpr int JS_ROWS = 32;  // rows of S per S unit (JT pairs x JS_ROWS rows)
 // issued before the rotations so that both memory round trips overlap.  A is
 // double-buffered (read from one buffer, written in full to the other); S is
 // updated in place (the round's column pairs are disjoint).
-__global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, double* A1, double* S,
-                                                double* __restrict__ diag, int* act, int max_sweeps, double eps,
-                                                double floor_rel, DevCtl* ctl) {
+template <class JA>
+__global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
+                                                typename JA::T* S, double* __restrict__ diag, int* act,
+                                                int max_sweeps, double eps, double floor_rel, DevCtl* ctl) {
+    using T = typename JA::T;
     extern __shared__ int jsh[];
     int* perm = jsh;         // npad: tagged indices first
     int* flg = jsh + npad;   // npad: tag flags of this sweep
-    __shared__ double u_c[2 * JT], u_s[2 * JT];
+    __shared__ T u_c[2 * JT], u_s[2 * JT];
     __shared__ int u_on[2 * JT];
     __shared__ double s_red[8];
     __shared__ int s_cnt;
@@ -176,7 +283,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
 
     // absolute floor relative to the largest diagonal entry (same in all blocks)
     double mx = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) mx = fmax(mx, fabs(__ldcg(A0 + i + (size_t)npad * i)));
+    for (int i = tid; i < n; i += blockDim.x) mx = fmax(mx, fabs(JA::to(JA::ld(A0 + i + (size_t)npad * i))));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((tid & 31) == 0) s_red[tid >> 5] = mx;
     __syncthreads();
@@ -192,15 +299,14 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
     int sweep = 0, my_rot = 0;
     bool converged = false;
     for (sweep = 0;; ++sweep) {
-        const double* Acur = (rt & 1) ? A1 : A0;
+        const T* Acur = (rt & 1) ? A1 : A0;
         const int tag = sweep + 1;
         for (long e = gtid; e < (long)npad * npad; e += gstride) {
             const int i = (int)(e % npad), j = (int)(e / npad);
             if (i < j) {
-                const double aij = __ldcg(Acur + i + (size_t)npad * j);
-                if (aij != 0.0 &&
-                    jac_above(__ldcg(Acur + i + (size_t)npad * i), __ldcg(Acur + j + (size_t)npad * j), aij, eps,
-                              floor_abs)) {
+                const T aij = JA::ld(Acur + i + (size_t)npad * j);
+                if (JA::nz(aij) && JA::above(JA::ld(Acur + i + (size_t)npad * i), JA::ld(Acur + j + (size_t)npad * j),
+                                             aij, eps, floor_abs)) {
                     act[i] = tag;
                     act[j] = tag;
                 }
@@ -240,8 +346,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
         if (4 * s2 > 3 * npad) s2 = npad;
         const int nh = s2 / 2;
         for (int r = 0; r < s2 - 1; ++r, ++rt) {
-            const double* Ac = (rt & 1) ? A1 : A0;
-            double* An = (rt & 1) ? A0 : A1;
+            const T* Ac = (rt & 1) ? A1 : A0;
+            T* An = (rt & 1) ? A0 : A1;
             for (int u = blockIdx.x; u < nU; u += gridDim.x) {
                 const bool isA = u < nA;
                 int kA0, kB0 = 0, rc = 0;
@@ -262,7 +368,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                 }
                 // item inputs first
                 int ka = -1, kb = -1, row = -1, p = 0, q = 0, pr = 0, pt = 0;
-                double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+                T x0 = JA::zero(), x1 = JA::zero(), x2 = JA::zero(), x3 = JA::zero();
                 if (isA) {
                     if (tid < JT * JT) {
                         const int a = tid % JT, b = tid / JT;
@@ -271,15 +377,15 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                             kb = kB0 + b;
                             jac_pair(r, ka, s2, perm, p, q);
                             if (ka == kb) {
-                                x0 = __ldcg(Ac + p + (size_t)npad * p);
-                                x1 = __ldcg(Ac + q + (size_t)npad * q);
-                                x2 = __ldcg(Ac + p + (size_t)npad * q);
+                                x0 = JA::ld(Ac + p + (size_t)npad * p);
+                                x1 = JA::ld(Ac + q + (size_t)npad * q);
+                                x2 = JA::ld(Ac + p + (size_t)npad * q);
                             } else {
                                 jac_pair(r, kb, s2, perm, pr, pt);
-                                x0 = __ldcg(Ac + p + (size_t)npad * pr);
-                                x1 = __ldcg(Ac + p + (size_t)npad * pt);
-                                x2 = __ldcg(Ac + q + (size_t)npad * pr);
-                                x3 = __ldcg(Ac + q + (size_t)npad * pt);
+                                x0 = JA::ld(Ac + p + (size_t)npad * pr);
+                                x1 = JA::ld(Ac + p + (size_t)npad * pt);
+                                x2 = JA::ld(Ac + q + (size_t)npad * pr);
+                                x3 = JA::ld(Ac + q + (size_t)npad * pt);
                             }
                         }
                     }
@@ -290,8 +396,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                         ka = kA0 + kk;
                         row = rw;
                         jac_pair(r, ka, s2, perm, p, q);
-                        x0 = __ldcg(S + row + (size_t)npad * p);
-                        x1 = __ldcg(S + row + (size_t)npad * q);
+                        x0 = JA::ld(S + row + (size_t)npad * p);
+                        x1 = JA::ld(S + row + (size_t)npad * q);
                     }
                 }
                 // the unit's rotations
@@ -299,12 +405,12 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                 const int rtid = isA ? tid - JT * JT : tid;  // A units: threads after the items
                 if (rtid >= 0 && rtid < nrot) {
                     const int k = rtid < JT ? kA0 + rtid : kB0 + rtid - JT;
-                    Rot R{1.0, 0.0, false};
+                    typename JA::R R{JA::one(), JA::zero(), false};
                     if (k < nh) {
                         int rp, rq;
                         jac_pair(r, k, s2, perm, rp, rq);
-                        R = rot_fast(__ldcg(Ac + rp + (size_t)npad * rp), __ldcg(Ac + rq + (size_t)npad * rq),
-                                     __ldcg(Ac + rp + (size_t)npad * rq), eps, floor_abs);
+                        R = JA::rot(JA::ld(Ac + rp + (size_t)npad * rp), JA::ld(Ac + rq + (size_t)npad * rq),
+                                    JA::ld(Ac + rp + (size_t)npad * rq), eps, floor_abs);
                     }
                     u_c[rtid] = R.c;
                     u_s[rtid] = R.s;
@@ -315,17 +421,18 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                 if (ka >= 0) {
                     if (isA) {
                         const int ia = ka - kA0, ib = JT + kb - kB0;
-                        const double ca = u_c[ia], sa = u_s[ia];
+                        const T ca = u_c[ia], sa = u_s[ia];
                         const bool ona = u_on[ia] != 0;
                         if (ka == kb) {
                             if (ona) {
                                 // J^t [[app, apq], [apq, aqq]] J with J = [[c, s], [-s, c]]
-                                const double app = x0, aqq = x1, apq = x2;
-                                const double y_pp = ca * app - sa * apq, y_pq = ca * apq - sa * aqq;
-                                const double y_qp = sa * app + ca * apq, y_qq = sa * apq + ca * aqq;
-                                const double npq = 0.5 * ((sa * y_pp + ca * y_pq) + (ca * y_qp - sa * y_qq));
-                                An[p + (size_t)npad * p] = ca * y_pp - sa * y_pq;
-                                An[q + (size_t)npad * q] = sa * y_qp + ca * y_qq;
+                                const T app = x0, aqq = x1, apq = x2, nca = JA::neg(ca);
+                                const T y_pp = JA::lin(ca, app, sa, apq), y_pq = JA::lin(ca, apq, sa, aqq);
+                                const T y_qp = JA::lin(sa, app, nca, apq), y_qq = JA::lin(sa, apq, nca, aqq);
+                                const T npq =
+                                    JA::half(JA::add(JA::lin(sa, y_pp, nca, y_pq), JA::lin(ca, y_qp, sa, y_qq)));
+                                An[p + (size_t)npad * p] = JA::lin(ca, y_pp, sa, y_pq);
+                                An[q + (size_t)npad * q] = JA::lin(sa, y_qp, nca, y_qq);
                                 An[p + (size_t)npad * q] = npq;
                                 An[q + (size_t)npad * p] = npq;
                             } else {
@@ -335,17 +442,18 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                                 An[q + (size_t)npad * p] = x2;
                             }
                         } else {
-                            const double cb = u_c[ib], sb = u_s[ib];
+                            const T cb = u_c[ib], sb = u_s[ib];
                             const bool onb = u_on[ib] != 0;
-                            double o_pr = x0, o_pt = x1, o_qr = x2, o_qt = x3;
+                            T o_pr = x0, o_pt = x1, o_qr = x2, o_qt = x3;
                             if (ona || onb) {
                                 // J_a^t from the left (rows p, q), J_b from the right (columns r, t)
-                                const double y_pr = ca * x0 - sa * x2, y_pt = ca * x1 - sa * x3;
-                                const double y_qr = sa * x0 + ca * x2, y_qt = sa * x1 + ca * x3;
-                                o_pr = cb * y_pr - sb * y_pt;
-                                o_pt = sb * y_pr + cb * y_pt;
-                                o_qr = cb * y_qr - sb * y_qt;
-                                o_qt = sb * y_qr + cb * y_qt;
+                                const T nca = JA::neg(ca), ncb = JA::neg(cb);
+                                const T y_pr = JA::lin(ca, x0, sa, x2), y_pt = JA::lin(ca, x1, sa, x3);
+                                const T y_qr = JA::lin(sa, x0, nca, x2), y_qt = JA::lin(sa, x1, nca, x3);
+                                o_pr = JA::lin(cb, y_pr, sb, y_pt);
+                                o_pt = JA::lin(sb, y_pr, ncb, y_pt);
+                                o_qr = JA::lin(cb, y_qr, sb, y_qt);
+                                o_qt = JA::lin(sb, y_qr, ncb, y_qt);
                             }
                             An[p + (size_t)npad * pr] = o_pr;
                             An[p + (size_t)npad * pt] = o_pt;
@@ -359,9 +467,9 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
                     } else {
                         const int ia = ka - kA0;
                         if (u_on[ia]) {
-                            const double c = u_c[ia], sn = u_s[ia];
-                            S[row + (size_t)npad * p] = c * x0 - sn * x1;
-                            S[row + (size_t)npad * q] = sn * x0 + c * x1;
+                            const T c = u_c[ia], sn = u_s[ia];
+                            S[row + (size_t)npad * p] = JA::lin(c, x0, sn, x1);
+                            S[row + (size_t)npad * q] = JA::lin(sn, x0, JA::neg(c), x1);
                         }
                     }
                 }
@@ -372,8 +480,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, double* A0, dou
         if (my_rot) atomicAdd(&ctl->rot_count[sweep < 64 ? sweep : 63], my_rot);
         my_rot = 0;
     }
-    const double* Af = (rt & 1) ? A1 : A0;
-    for (long i = gtid; i < n; i += gstride) diag[i] = __ldcg(Af + i + (size_t)npad * i);
+    const T* Af = (rt & 1) ? A1 : A0;
+    for (long i = gtid; i < n; i += gstride) diag[i] = JA::to(JA::ld(Af + i + (size_t)npad * i));
     if (gtid == 0) {
         ctl->jac_sweeps = sweep;
         if (!converged) atomicMax(err, 1);
@@ -395,13 +503,14 @@ __global__ void k_rank_ritz(int n, const double* __restrict__ diag, int* __restr
     }
 }
 
-__global__ void k_gather_ritz(int n, int npad, const int* __restrict__ rank, const double* __restrict__ S,
+template <class JA>
+__global__ void k_gather_ritz(int n, int npad, const int* __restrict__ rank, const typename JA::T* __restrict__ S,
                               double* __restrict__ Sout, int ldo) {
     size_t tot = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
          e += (size_t)gridDim.x * blockDim.x) {
         int row = (int)(e % n), j = (int)(e / n);
-        Sout[row + (size_t)ldo * rank[j]] = S[row + (size_t)npad * j];
+        Sout[row + (size_t)ldo * rank[j]] = JA::to(S[row + (size_t)npad * j]);
     }
 }
 
@@ -890,11 +999,17 @@ int coop_grid_limit(const void* fn, int block, size_t smem) {
     return sms * per;
 }
 
-cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
-                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol, double floor_rel) {
+template <class JA>
+cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta, double* Sout,
+                          int ldo, int max_sweeps, DevCtl* ctl, double eps, double floor_rel) {
+    using T = typename JA::T;
+    static_assert(sizeof(T) == sizeof(double), "A and S buffers hold one 8-byte element each");
     int npad = n + (n & 1);
     if (npad < 2) npad = 2;
-    k_jacobi_init<<<grid_for((size_t)npad * npad), 256, 0, st>>>(n, npad, H, ldh, w.A0, w.S, w.rank);
+    T* A0 = (T*)w.A0;
+    T* A1 = (T*)w.A1;
+    T* S = (T*)w.S;
+    k_jacobi_init<JA><<<grid_for((size_t)npad * npad), 256, 0, st>>>(n, npad, H, ldh, A0, S, w.rank);
     cudaMemsetAsync(&ctl->rot_count[0], 0, sizeof(ctl->rot_count), st);
     cudaMemsetAsync(&ctl->jac_status, 0, sizeof(int), st);
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
@@ -909,25 +1024,34 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     static size_t limit_smem = 0;
     if (limit == 0 || smem > limit_smem) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        limit = coop_grid_limit((const void*)k_jacobi, 256, smem);
+            cudaFuncSetAttribute(k_jacobi<JA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        limit = coop_grid_limit((const void*)k_jacobi<JA>, 256, smem);
         limit_smem = smem;
     }
     if (grid > limit) grid = limit;
     if (grid < 1) grid = 1;
-    double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16;
     double fl = floor_rel > 0.0 ? floor_rel : 0.0;
-    double* A0 = w.A0;
-    double* A1 = w.A1;
-    double* S = w.S;
     double* diag = w.diag;
     int* act = w.rank;  // the sweep tags; rank is rewritten by the sort below
     void* args[] = {&n, &npad, &A0, &A1, &S, &diag, &act, &max_sweeps, &eps, &fl, &ctl};
-    cudaError_t e = launch_coop((const void*)k_jacobi, grid, 256, args, smem, st);
+    cudaError_t e = launch_coop((const void*)k_jacobi<JA>, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);
-    k_gather_ritz<<<grid_for((size_t)n * n), 256, 0, st>>>(n, npad, w.rank, w.S, Sout, ldo);
+    k_gather_ritz<JA><<<grid_for((size_t)n * n), 256, 0, st>>>(n, npad, w.rank, S, Sout, ldo);
     return cudaGetLastError();
+}
+
+cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
+                       double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol, double floor_rel,
+                       bool df) {
+    if (df) {
+        // double-float: rotate while the coupling exceeds ~2^-46 of the
+        // diagonal scale (four times the pair's unit roundoff)
+        const double eps = rel_tol > 1.4210854715202004e-14 ? rel_tol : 1.4210854715202004e-14;
+        return jacobi_launch<JDF>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel);
+    }
+    const double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16;
+    return jacobi_launch<J64>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel);
 }
 
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl) {
@@ -1224,7 +1348,7 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
         return -1;
     }
     k_rank_ritz<<<gfor(b), 256, 0, st>>>(b, ew.diag, ew.rank, theta);
-    k_gather_ritz<<<gfor(bb), 256, 0, st>>>(b, b, ew.rank, w.X, Sout, ldo);
+    k_gather_ritz<J64><<<gfor(bb), 256, 0, st>>>(b, b, ew.rank, w.X, Sout, ldo);
     return it;
 }
 

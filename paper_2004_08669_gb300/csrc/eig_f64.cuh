@@ -55,9 +55,11 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
 // A pair is rotated while |a_pq| > max(rel_tol sqrt|a_pp a_qq|, floor_rel
 // max_i |h_ii|) (rel_tol is at least the FP64 unit roundoff; floor_rel 0
 // keeps the purely relative criterion).
+// df: hold A and S as double-float pairs and compute on the FP32 pipe (about
+// 48 significant bits; for the mixed-precision forms).
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
                        double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0,
-                       double floor_rel = 0.0);
+                       double floor_rel = 0.0, bool df = false);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);
