@@ -653,7 +653,7 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
         } else {
             double shift_rel =
                 (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
-            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl));
+            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl, h->lay.prec != CTM_FP64));
             ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
             prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
         }

@@ -532,12 +532,91 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
     return y;
 }
 
+// Arithmetic of the Cholesky factorisation (G stays FP64 in memory).  C64:
+// FP64.  CDF: double-float pairs on the FP32 pipe for the mixed-precision
+// forms, whose last orthonormalisation pass (Newton-Schulz) corrects the
+// factor's rounding to O(|E|^2).
+struct C64 {
+    using T = double;
+    __device__ static T from(double x) { return x; }
+    __device__ static double to(T a) { return a; }
+    __device__ static T zero() { return 0.0; }
+    __device__ static T mul(T a, T b) { return a * b; }
+    __device__ static T sub(T a, T b) { return a - b; }
+    __device__ static T rsq(T d) { return rsqrt_nr(d); }
+    __device__ static T shfl(T a, int l) { return __shfl_sync(0xffffffffu, a, l); }
+    struct Acc {
+        double a0, a1;
+    };
+    __device__ static Acc acc0() { return Acc{0.0, 0.0}; }
+    __device__ static void acc2(Acc& c, T x0, T y0, T x1, T y1) {
+        c.a0 = fma(x0, y0, c.a0);
+        c.a1 = fma(x1, y1, c.a1);
+    }
+    __device__ static T fin(Acc c) { return c.a0 + c.a1; }
+};
+
+struct CDF {
+    using T = float2;
+    __device__ static T quick(float s, float e) {
+        const float h = s + e;
+        return make_float2(h, e - (h - s));
+    }
+    __device__ static T from(double x) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    }
+    __device__ static double to(T a) { return f2d_bits(a.x) + f2d_bits(a.y); }
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    __device__ static T mul(T a, T b) {
+        const float p = a.x * b.x;
+        return quick(p, fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x));
+    }
+    __device__ static T add(T a, T b) {
+        const float s = a.x + b.x, bb = s - a.x;
+        const float e = (a.x - (s - bb)) + (b.x - bb);
+        return quick(s, e + (a.y + b.y));
+    }
+    __device__ static T sub(T a, T b) { return add(a, make_float2(-b.x, -b.y)); }
+    // 1/sqrt(d): FP32 seed, two double-float Newton steps y <- y + y (1 - d y^2)/2
+    __device__ static T rsq(T d) {
+        T y = make_float2(rsqrtf(d.x), 0.f);
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const T r = sub(make_float2(1.f, 0.f), mul(d, mul(y, y)));
+            y = add(y, make_float2(0.5f * y.x * r.x, 0.f));
+        }
+        return y;
+    }
+    __device__ static T shfl(T a, int l) {
+        return make_float2(__shfl_sync(0xffffffffu, a.x, l), __shfl_sync(0xffffffffu, a.y, l));
+    }
+    struct Acc {
+        float h, l;
+    };
+    __device__ static Acc acc0() { return Acc{0.f, 0.f}; }
+    __device__ static void acc1(Acc& c, T a, T b) {
+        const float p = a.x * b.x, pe = fmaf(a.x, b.x, -p);
+        const float s = c.h + p, bb = s - c.h;
+        const float e = (c.h - (s - bb)) + (p - bb);
+        c.h = s;
+        c.l += (e + pe) + fmaf(a.x, b.y, a.y * b.x);
+    }
+    __device__ static void acc2(Acc& c, T x0, T y0, T x1, T y1) {
+        acc1(c, x0, y0);
+        acc1(c, x1, y1);
+    }
+    __device__ static T fin(Acc c) { return quick(c.h, c.l); }
+};
+
+template <class CA>
 __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
-    __shared__ double D[32][33];
-    __shared__ double dinv[32];
-    __shared__ double dinv2[32];
-    __shared__ double PI[32][17];  // panel rows of tile I (l-major)
-    __shared__ double PJ[32][17];  // panel rows of tile J
+    using T = typename CA::T;
+    __shared__ T D[32][33];
+    __shared__ T dinv[32];
+    __shared__ T dinv2[32];
+    __shared__ T PI[32][17];  // panel rows of tile I (l-major)
+    __shared__ T PJ[32][17];  // panel rows of tile J
     __shared__ double s_red[8];
     int* err = &ctl->chol_status;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -568,36 +647,39 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
         //     that updates the next pivot takes its reciprocal square root.
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int i = e % 32, j = e / 32;
-            D[i][j] = (i < kb && j < kb && j <= i) ? __ldcg(G + (k0 + i) + (size_t)ld * (k0 + j)) : 0.0;
+            D[i][j] = (i < kb && j < kb && j <= i) ? CA::from(__ldcg(G + (k0 + i) + (size_t)ld * (k0 + j)))
+                                                   : CA::zero();
         }
         __syncthreads();
         if (tid == 0) {
-            double d = D[0][0];
-            if (!(d > 0.0) || !isfinite(d)) {
+            T d = D[0][0];
+            const double dd = CA::to(d);
+            if (!(dd > 0.0) || !isfinite(dd)) {
                 if (blockIdx.x == 0) atomicMax(err, 1);
-                d = 1.0;
+                d = CA::from(1.0);
                 D[0][0] = d;
             }
-            const double inv = rsqrt_nr(d);
+            const T inv = CA::rsq(d);
             dinv[0] = inv;
-            dinv2[0] = inv * inv;
+            dinv2[0] = CA::mul(inv, inv);
         }
         __syncthreads();
         for (int j = 0; j + 1 < kb; ++j) {
-            const double w = dinv2[j];
+            const T w = dinv2[j];
             const int nt = kb - 1 - j;  // trailing order
             for (int e = tid; e < nt * nt; e += blockDim.x) {
                 const int i = j + 1 + e % nt, l = j + 1 + e / nt;
                 if (l <= i) {
-                    double v = D[i][l] - D[i][j] * D[l][j] * w;
+                    T v = CA::sub(D[i][l], CA::mul(CA::mul(D[i][j], D[l][j]), w));
                     if (i == j + 1 && l == j + 1) {  // the next pivot
-                        if (!(v > 0.0) || !isfinite(v)) {
+                        const double vv = CA::to(v);
+                        if (!(vv > 0.0) || !isfinite(vv)) {
                             if (blockIdx.x == 0) atomicMax(err, 1);
-                            v = 1.0;
+                            v = CA::from(1.0);
                         }
-                        const double inv = rsqrt_nr(v);
+                        const T inv = CA::rsq(v);
                         dinv[j + 1] = inv;
-                        dinv2[j + 1] = inv * inv;
+                        dinv2[j + 1] = CA::mul(inv, inv);
                     }
                     D[i][l] = v;
                 }
@@ -607,13 +689,13 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
         // scale: L[i][j] = D[i][j] / sqrt(d_j) (i > j), L[j][j] = d_j / sqrt(d_j)
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int i = e % 32, j = e / 32;
-            if (j < kb && i < kb && j <= i) D[i][j] *= dinv[j];
+            if (j < kb && i < kb && j <= i) D[i][j] = CA::mul(D[i][j], dinv[j]);
         }
         __syncthreads();
         if (blockIdx.x == 0)
             for (int e = tid; e < kb * kb; e += blockDim.x) {
                 const int i = e % kb, j = e / kb;
-                G[(k0 + i) + (size_t)ld * (k0 + j)] = D[i][j];
+                G[(k0 + i) + (size_t)ld * (k0 + j)] = CA::to(D[i][j]);
             }
         const int k1 = k0 + kb;
         // --- panel rows below: L[i, k0:k1] = G[i, k0:k1] L_kk^{-t}, one warp
@@ -621,17 +703,17 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
         {
             const long gw = gtid >> 5, nw = gstride >> 5;
             for (long i = k1 + gw; i < n; i += nw) {
-                double acc = (lane < kb) ? __ldcg(G + i + (size_t)ld * (k0 + lane)) : 0.0;
-                double x = 0.0;
+                T acc = (lane < kb) ? CA::from(__ldcg(G + i + (size_t)ld * (k0 + lane))) : CA::zero();
+                T x = CA::zero();
 #pragma unroll
                 for (int l = 0; l < 32; ++l) {
                     if (l < kb) {
-                        const double xl = __shfl_sync(full, acc, l) * dinv[l];
+                        const T xl = CA::mul(CA::shfl(acc, l), dinv[l]);
                         if (lane == l) x = xl;
-                        if (lane > l) acc -= xl * D[lane][l];
+                        if (lane > l) acc = CA::sub(acc, CA::mul(xl, D[lane][l]));
                     }
                 }
-                if (lane < kb) G[i + (size_t)ld * (k0 + lane)] = x;
+                if (lane < kb) G[i + (size_t)ld * (k0 + lane)] = CA::to(x);
             }
         }
         if (!grid_sync(&ctl->bar_count, epoch, err)) return;
@@ -650,20 +732,19 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
             const int i0 = k1 + 16 * I, j0 = k1 + 16 * J;
             for (int e = tid; e < 16 * 32; e += blockDim.x) {
                 const int r = e & 15, l = e >> 4;
-                PI[l][r] = (l < kb && i0 + r < n) ? __ldcg(G + (i0 + r) + (size_t)ld * (k0 + l)) : 0.0;
-                PJ[l][r] = (l < kb && j0 + r < n) ? __ldcg(G + (j0 + r) + (size_t)ld * (k0 + l)) : 0.0;
+                PI[l][r] = (l < kb && i0 + r < n) ? CA::from(__ldcg(G + (i0 + r) + (size_t)ld * (k0 + l)))
+                                                  : CA::zero();
+                PJ[l][r] = (l < kb && j0 + r < n) ? CA::from(__ldcg(G + (j0 + r) + (size_t)ld * (k0 + l)))
+                                                  : CA::zero();
             }
             __syncthreads();
             const int i = i0 + tx, j = j0 + ty;
             if (i < n && j < n && j <= i) {
-                double a0 = 0.0, a1 = 0.0;
+                typename CA::Acc c = CA::acc0();
 #pragma unroll
-                for (int l = 0; l < 32; l += 2) {
-                    a0 = fma(PI[l][tx], PJ[l][ty], a0);
-                    a1 = fma(PI[l + 1][tx], PJ[l + 1][ty], a1);
-                }
+                for (int l = 0; l < 32; l += 2) CA::acc2(c, PI[l][tx], PJ[l][ty], PI[l + 1][tx], PJ[l + 1][ty]);
                 double* g = G + i + (size_t)ld * j;
-                *g = __ldcg(g) - (a0 + a1);
+                *g = CA::to(CA::sub(CA::from(__ldcg(g)), CA::fin(c)));
             }
             __syncthreads();
         }
@@ -1054,19 +1135,21 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     return jacobi_launch<J64>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel);
 }
 
-cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl) {
+cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl, bool df) {
     // shift is relative: the kernel adds shift * trace(G) to the diagonal.
     // ctl->chol_status is sticky (atomicMax): the caller clears it.
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
     static int limit = 0;
-    if (limit == 0) limit = coop_grid_limit((const void*)k_cholesky, 256, 0);
+    if (limit == 0)
+        limit = std::min(coop_grid_limit((const void*)k_cholesky<C64>, 256, 0),
+                         coop_grid_limit((const void*)k_cholesky<CDF>, 256, 0));
     const long T = (n + 15) / 16;
     int grid = (int)std::max<long>(T * (T + 1) / 2, (n + 255) / 256);
     if (grid > limit) grid = limit;
     if (grid > 2 * 152) grid = 2 * 152;
     if (grid < 1) grid = 1;
     void* args[] = {&n, &G, &ld, &shift, &ctl};
-    return launch_coop((const void*)k_cholesky, grid, 256, args, 0, st);
+    return launch_coop(df ? (const void*)k_cholesky<CDF> : (const void*)k_cholesky<C64>, grid, 256, args, 0, st);
 }
 
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch) {

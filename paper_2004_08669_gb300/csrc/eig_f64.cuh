@@ -62,7 +62,8 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
                        double floor_rel = 0.0, bool df = false);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
-cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl);
+// df: double-float arithmetic on the FP32 pipe (mixed-precision forms).
+cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl, bool df = false);
 
 // X = (3 I - (G + G^t)/2) / 2: the Newton-Schulz orthogonality correction
 // of a block whose Gram matrix G is close to I.
