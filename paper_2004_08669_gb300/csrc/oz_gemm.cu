@@ -4,7 +4,9 @@
 //   D (M x N, column-major FP64) = A . B^t,  A: M x K, B: N x K (FP64, rows
 //   contiguous in K after k_oz_split).
 //
-// Splitting (k_oz_split): each row r of an operand is scaled by a power of
+// Splitting (k_oz_split_rows for row-contiguous operands, one CTA per row;
+// k_oz_split in two passes over 32 x 32 tiles otherwise): each row r of an
+// operand is scaled by a power of
 // two 2^-e_r so that |x| < 1, rounded to a 7s-bit fixed-point integer X, and
 // written as s balanced base-2^7 digits, X = sum_i d_i 2^{7(s-i)}, with
 // |d_1| <= 128 and |d_i| <= 64 after: every digit is an integer that bf16
@@ -197,6 +199,84 @@ __global__ void __launch_bounds__(256) k_oz_split(int R, int K, int s, const dou
                 X -= d * (1ll << shf);
                 // |d| <= 128: an int32 conversion (int64 ones run on the slow FP64 pipe)
                 planes[((size_t)i * Rp + r) * ld + k] = __float2bfloat16_rn((float)(int)d);
+            }
+        }
+    }
+}
+
+// Shared pieces of the single-kernel splits below.
+__device__ __forceinline__ int oz_raw_exp(double v) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(v);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    return ((bits & 0x7FFFFFFFFFFFFFFFull) != 0) ? (E == 0 ? 1 : E) : 0;
+}
+
+// round(|v| 2^(fbits - e_r)) with v's sign, e_r = raw - 1022 (integer operations only)
+__device__ __forceinline__ long long oz_fixed(double v, int raw, int fbits) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(v);
+    int E = (int)((bits >> 52) & 0x7FF);
+    uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+    if (E != 0) mant |= (1ull << 52);
+    else E = 1;
+    const int sh = E - 1075 - (raw - 1022) + fbits;
+    uint64_t mag;
+    if (sh >= 0) mag = mant << sh;
+    else if (sh > -64) mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else mag = 0;
+    const long long X = (long long)mag;
+    return (bits >> 63) ? -X : X;
+}
+
+// digit i of X's balanced base-2^7 expansion (most significant first)
+__device__ __forceinline__ __nv_bfloat16 oz_digit(long long& X, int s, int i) {
+    const int shf = 7 * (s - 1 - i);
+    const long long d = (shf > 0) ? ((X + (1ll << (shf - 1))) >> shf) : X;
+    X -= d * (1ll << shf);
+    return __float2bfloat16_rn((float)(int)d);
+}
+
+// Single-kernel split of operands whose rows are contiguous (ks = 1): one CTA
+// per row holds the row in registers (VPT values per thread), reduces the
+// exponent and writes all digit planes, coalesced along k.
+template <int VPT>
+__global__ void __launch_bounds__(256) k_oz_split_rows(int R, int K, int s, const double* __restrict__ src, long rs,
+                                                       const double* __restrict__ scale,
+                                                       __nv_bfloat16* __restrict__ planes, int Rp, int ld,
+                                                       int* __restrict__ rexp) {
+    __shared__ int red[8];
+    const int tid = threadIdx.x;
+    const size_t pstride = (size_t)Rp * ld;
+    const int fbits = 7 * s;
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        const double* row = src + rs * (long)r;
+        double v[VPT];
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const int k = tid + 256 * j;
+            double x = 0.0;
+            if (k < K) {
+                x = row[k];
+                if (scale) x *= scale[k];
+            }
+            v[j] = x;
+            e = max(e, oz_raw_exp(x));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if ((tid & 31) == 0) red[tid >> 5] = e;
+        __syncthreads();
+        int raw = red[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) raw = max(raw, red[w]);
+        __syncthreads();  // red is reused by the next row
+        if (tid == 0) rexp[r] = raw;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const int k = tid + 256 * j;
+            if (k < ld) {
+                long long X = (k < K && raw != 0) ? oz_fixed(v[j], raw, fbits) : 0;
+                for (int i = 0; i < s; ++i) planes[i * pstride + (size_t)r * ld + k] = oz_digit(X, s, i);
             }
         }
     }
@@ -446,10 +526,24 @@ void oz_split(cudaStream_t st, int R, int K, int s, const double* src, int lds, 
     oz_split_strided(st, R, K, s, src, lds, 1, scale, planes, is_a, rexp);
 }
 
+template <int VPT>
+void oz_launch_rows(cudaStream_t st, int R, int K, int s, const double* src, long rs, const double* scale,
+                    void* planes, int Rp, int ld, int* rexp) {
+    const int grid = std::min(R, 152 * 16);
+    k_oz_split_rows<VPT><<<grid, 256, 0, st>>>(R, K, s, src, rs, scale, (__nv_bfloat16*)planes, Rp, ld, rexp);
+}
+
 void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, long rs, long ks,
                       const double* scale, void* planes, bool is_a, int* rexp) {
     if (R <= 0) return;
     const int Rp = oz_rows_pad(R, is_a ? kOzBM : kOzBN), ld = oz_ld(K);
+    // rows contiguous: one kernel (a CTA per row); otherwise two passes over tiles
+    if (ks == 1 && ld <= 256 * 24) {
+        if (ld <= 256 * 2) oz_launch_rows<2>(st, R, K, s, src, rs, scale, planes, Rp, ld, rexp);
+        else if (ld <= 256 * 8) oz_launch_rows<8>(st, R, K, s, src, rs, scale, planes, Rp, ld, rexp);
+        else oz_launch_rows<24>(st, R, K, s, src, rs, scale, planes, Rp, ld, rexp);
+        return;
+    }
     cudaMemsetAsync(rexp, 0, sizeof(int) * (size_t)R, st);
     const dim3 blk(32, 8);
     k_oz_split<false><<<dim3((K + 31) / 32, (R + 31) / 32), blk, 0, st>>>(R, K, s, src, rs, ks, scale,
