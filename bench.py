@@ -55,6 +55,17 @@ def parse():
                          "prints no measurement")
     ap.add_argument("--gate-steps", type=int, default=20,
                     help="steps of the mixed-vs-FP64 comparison from the timed state (0: skip)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default tensor-core GEMM launch shapes (no autotuning)")
+    ap.add_argument("--scan", action="store_true",
+                    help="time the temperature scan instead: q=20, m=128, 32 T uniform in [0.40, 0.48], TF32; "
+                         "--steps / --warmup are steps per beta; betas are sharded across ranks")
+    ap.add_argument("--scan-m", type=int, default=128)
+    ap.add_argument("--scan-nbeta", type=int, default=32)
+    ap.add_argument("--scan-prec", default="tf32")
+    ap.add_argument("--scan-workers", type=int, default=8)
+    ap.add_argument("--scan-compare-workers", type=int, default=1,
+                    help="also time the scan with this many workers (0: skip) for the concurrency gain")
     return ap.parse_args()
 
 
@@ -228,6 +239,8 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
     g = ctm.CTMRG(W.dodecahedron(), m, beta, prec=prec, device=f"cuda:{local}",
                   max_subspace_iters=args.subspace_iters)
     stream = g.stream
+    # tensor-core forms: time every launch shape of the step's GEMMs first
+    tune = None if args.no_tune else ctm.ctm_tune(g.h, 5)
     g.step(args.prep)
     for _ in range(max(args.warmup, 0)):
         g.step(1)
@@ -290,7 +303,7 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
            "subspace_iters_mean": float(np.mean(iters)), "jacobi_sweeps_mean": float(np.mean(sweeps)),
            "rayleigh_ritz_paths": rr_paths,
            "kernels_ms_per_step": {k: round(v["ms"] / timed_steps, 3) for k, v in kern.items()},
-           "workload": workload}
+           "workload": workload, "tuned_shapes": tune or None}
     return g, res
 
 
@@ -385,7 +398,7 @@ def run_ours(args):
             g2.close()
             others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "roofline_tensor", "gpu_launches",
                                             "subspace_iters_mean", "jacobi_sweeps_mean", "rayleigh_ritz_paths",
-                                            "kernels_ms_per_step", "clocks")}
+                                            "kernels_ms_per_step", "clocks", "tuned_shapes")}
         except Exception as e:  # a failing form must not lose the others' numbers
             others[p] = {"error": f"{type(e).__name__}: {e}"}
     out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -393,7 +406,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": DTYPES.get(primary, primary), "data": "synthetic",
            "config": {"workload": res["workload"], "q": 20, "m": m, "T": args.T, "prec": primary,
                       "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "inputs larger than L2 (C~ is 210 MB FP64), no flush",
+                      "l2": f"inputs larger than L2 (C~ is {8 * (20 * m) ** 2 / 1e6:.0f} MB FP64), no flush",
                       "subspace_iters_cap": args.subspace_iters,
                       "subspace_iters_mean": res["subspace_iters_mean"],
                       "jacobi_sweeps_mean": res["jacobi_sweeps_mean"],
@@ -413,6 +426,172 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+SCAN_METRIC = "CTMRG beta-steps/s, temperature scan q=20 m=128, 32 T uniform in [0.40, 0.48]"
+
+
+def scan_roofline(profs, wall_ms, prec, sm_max):
+    """Dominant kernel class of the scan, summed over its betas' handles: its
+    algorithmic FLOPs over the summed launch durations (launches of different
+    betas overlap, so the sum can exceed the wall time)."""
+    agg = {}
+    for p in profs:
+        for k, v in p.items():
+            if k == "all":
+                continue
+            a = agg.setdefault(k, {"ms": 0.0, "flops": 0.0, "launches": 0})
+            a["ms"] += v["ms"]
+            a["flops"] += v["flops"]
+            a["launches"] += v["launches"]
+    agg = {k: v for k, v in agg.items() if v["ms"] > 0}
+    if not agg:
+        return None, {}
+    dom = max(agg, key=lambda k: agg[k]["ms"])
+    d = agg[dom]
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    if dom in ("oz_gemm", "tc_gemm"):
+        peak, src = tensor_peak(prec)
+        bound = "tensor"
+    else:
+        peak = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src, bound = "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock", "alu"
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src, "launches": d["launches"],
+            "summed_ms_over_wall_ms": d["ms"] / wall_ms}
+    return roof, {k: round(v["ms"], 2) for k, v in agg.items()}
+
+
+def run_scan(args):
+    """Temperature scan: every beta of this rank's block stepped by the
+    library's worker pool (ctm_scan_*); betas sharded across ranks."""
+    import numpy as np
+    import torch
+
+    from paper_2004_08669_gb300 import build
+    from paper_2004_08669_gb300.scan import gather_results, shard_range
+    world, rank, local = dist_env()
+    gloo = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        gloo = dist.new_group(backend="gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2004_08669_gb300 import ctm, workloads as W
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    m, prec = args.scan_m, args.scan_prec
+    temps = np.linspace(0.40, 0.48, args.scan_nbeta)
+    lo, hi = shard_range(len(temps), rank, world)
+    betas = 1.0 / temps[lo:hi]
+
+    def one(workers, steps, with_extras):
+        sc = ctm.Scan(W.dodecahedron(), m, betas, workers=workers, prec=prec, device=f"cuda:{local}",
+                      max_subspace_iters=args.subspace_iters)
+        tune = None if args.no_tune else sc.tune(5)
+        sc.run(args.prep)
+        sc.run(max(args.warmup, 0))
+        hs = [ctm.ctm_scan_handle(sc.s, i) for i in range(len(betas))]
+        l0 = sum(ctm.ctm_launch_count(h) for h in hs)
+        if with_extras:
+            for h in hs:
+                ctm.ctm_profile(h, True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier()
+        t0 = time.perf_counter()
+        done, conv = sc.run(steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        clk = clocks.stop()
+        launches = sum(ctm.ctm_launch_count(h) for h in hs) - l0
+        profs = [ctm.ctm_profile_read(h) for h in hs] if with_extras else []
+        t = torch.tensor([wall, float(done.sum())], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            tw = t[:1].clone()
+            torch.distributed.all_reduce(tw, op=torch.distributed.ReduceOp.MAX)
+            tn = t[1:].clone()
+            torch.distributed.all_reduce(tn)
+            t = torch.cat([tw, tn])
+        wall_max, steps_all = float(t[0]), float(t[1])
+        res = {"value": steps_all / wall_max, "wall_s": wall_max, "beta_steps": steps_all, "gpu_launches": launches,
+               "clocks": clk, "tuned_shapes": tune, "converged_in_window": int(conv.sum()),
+               "steps_per_beta": done.tolist()}
+        return sc, res, profs
+
+    sc, res, profs = one(args.scan_workers, args.steps, True)
+    roof, kern = scan_roofline(profs, 1e3 * res["wall_s"], prec, res["clocks"].get("sm_max_mhz") or 2070.0)
+    # end to end through the public API: one scan step per beta, then every
+    # beta's spectrum read back to pinned host memory
+    import ctypes
+    spec = torch.empty(len(betas) * m, dtype=torch.float64, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctm._check(ctm.lib.ctm_scan_run(sc.s, 1, None, None), (ctm.CTM_OK, ctm.CTM_ENOTCONVERGED))
+        for i in range(len(betas)):
+            ptr = ctypes.cast(spec.data_ptr() + 8 * m * i, ctm._dp)
+            ctm._check(ctm.lib.ctm_scan_get_spectrum(sc.s, i, ptr))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    obs = None
+    if args.steps > 0:
+        obs_local = [dict(o, T=float(1.0 / b)) for o, b in zip(sc.observables(), betas)]
+        obs = gather_results(obs_local, rank, world, gloo)
+    sc.close()
+    cmp = None
+    if args.scan_compare_workers > 0 and args.scan_compare_workers != args.scan_workers:
+        sc2, r2, _ = one(args.scan_compare_workers, args.steps, False)
+        sc2.close()
+        cmp = {"workers": args.scan_compare_workers, "value": r2["value"], "wall_s": r2["wall_s"]}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        P, om = W.random_state(m, 20, m, seed=2004086690)
+        c = O.CTMRG(W.dodecahedron(), m, float(betas[0]))
+        c.set_state(P, np.concatenate([om[:m], np.zeros(m * 20 - m)]), m)
+        t = time.perf_counter()
+        c.step()
+        el = time.perf_counter() - t
+        cpu = {"value": 1.0 / el, "unit": "beta-steps/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"1 oracle step at q=20 m={m} T={temps[0]:.4f} from a seeded full-size state "
+                         f"(full dense diagonalisation, N={m * 20}), {el:.1f} s"}
+    out = {"metric": SCAN_METRIC, "value": res["value"], "unit": "beta-steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["wall_s"] / max(1, args.steps),
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+           "dtype": DTYPES.get(prec, prec), "data": "synthetic",
+           "config": {"workload": f"dodecahedron q=20 m={m}, {args.scan_nbeta} T uniform in [0.40, 0.48], {prec}",
+                      "q": 20, "m": m, "nbeta": args.scan_nbeta, "prec": prec, "workers": args.scan_workers,
+                      "parallelism": f"beta-sharded x{world}" if world > 1 else "single",
+                      "timing": "host wall clock around the synchronous ctm_scan_run (several streams)",
+                      "l2": "C~ of each beta is 52 MB FP64 and 32 betas rotate through L2; no flush",
+                      "subspace_iters_cap": args.subspace_iters, "prep_steps": args.prep,
+                      "steps_per_beta": res["steps_per_beta"], "converged_in_window": res["converged_in_window"]},
+           "roofline": roof, "kernels_ms_summed": kern,
+           "e2e": {"value": world * len(betas) * args.e2e_steps / e2e_s, "unit": "beta-steps/s",
+                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * m * len(betas)},
+           "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "tuned_shapes": res["tuned_shapes"]}
+    if cmp:
+        out["compare_workers"] = cmp
+    if cpu:
+        out["cpu_baseline"] = cpu
+    if obs is not None and rank == 0:
+        out["observables"] = [{k: (round(v, 12) if isinstance(v, float) else v) for k, v in o.items()} for o in obs]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_profile(args):
     """The timed workload's steps bracketed for a profiler, nothing measured."""
     import torch
@@ -422,6 +601,8 @@ def run_profile(args):
     prec = args.modes.split(",")[0]
     g = ctm.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T, prec=prec, device="cuda:0",
                   max_subspace_iters=args.subspace_iters)
+    if not args.no_tune:
+        ctm.ctm_tune(g.h, 5)
     g.step(args.prep)
     for _ in range(max(args.warmup, 0)):
         g.step(1)
@@ -442,6 +623,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.scan:
+        run_scan(args)
     else:
         run_ours(args)
 

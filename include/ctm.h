@@ -49,8 +49,10 @@ typedef enum {
 } ctm_status;
 
 /* Arithmetic of the contractions (extension, C~ V products, P update).
- * The Rayleigh-Ritz eigensolve, the CholQR2 re-orthonormalisation and the
- * normalisations are FP64 in every mode. */
+ * The Rayleigh-Ritz eigensolve and the Cholesky factor of the CholQR2
+ * re-orthonormalisation are FP64 in CTM_FP64 and double-float (an unevaluated
+ * sum of two FP32 words, unit roundoff 2^-46, on the FP32 pipe) in the other
+ * modes; the normalisations are FP64 in every mode. */
 typedef enum {
     CTM_FP64 = 0,     /* plain FP64 on the CUDA cores                         */
     CTM_TF32 = 1,     /* tcgen05 kind::tf32, FP32 accumulate                  */
@@ -242,6 +244,73 @@ ctm_status ctm_profile_read(ctm_handle* h, ctm_prof_entry* out, int max_entries,
 
 /* Kernels launched by this handle since ctm_init. */
 ctm_status ctm_launch_count(ctm_handle* h, long long* launches);
+
+/* Autotuner of the tensor-core GEMM (CTM_TF32 / CTM_BF16 handles; a no-op
+ * with *n_out = 0 for the others).  For each of the three products of the
+ * step -- X1 = P^t Omega P (N x N x m), C~ V (N x b x N) and U^t X
+ * (m x N x N), N = m q -- it times every launch shape (tile width 64, 128
+ * or 256 columns; 1 to 8 K slices, whose partial tiles fit the handle's
+ * split-K buffer of 4 N b doubles) with CUDA events on the handle's stream,
+ * reps launches each (<= 0: 5), on zeroed operands, and keeps the fastest
+ * for every later GEMM of that shape and precision in this process (all
+ * handles).  Uses only scratch buffers: call it between steps.  out (host,
+ * may be NULL) receives up to max_out entries, *n_out their count.  Split
+ * shapes sum their K slices in a fixed order, so results stay deterministic
+ * but change in the last bits of the FP32 accumulation when the shape
+ * changes. */
+typedef struct {
+    int M, N, K;         /* GEMM D (M x N) = A (M x K) . B^t                  */
+    int bn, splits;      /* chosen tile width and K slices                     */
+    double ms_default;   /* time per launch of the untuned shape               */
+    double ms_best;      /* time per launch of the chosen shape                */
+    int candidates;      /* shapes timed                                       */
+} ctm_tune_entry;
+ctm_status ctm_tune(ctm_handle* h, int reps, ctm_tune_entry* out, int max_out, int* n_out);
+
+/* The process-wide table of launch shapes that ctm_tune fills, also read by
+ * ctm_contract: pin (bn in {64, 128, 256}, splits 1..16) or clear
+ * (splits = 0) the shape of the TF32 / BF16 GEMM D (M x N) = A (M x K) B^t,
+ * or read the shape in force (*splits: the K slices it launches).
+ * ctm_contract_workspace_size includes the partial tiles of the shape in
+ * force when it is called. */
+ctm_status ctm_tc_plan_set(ctm_precision prec, int M, int N, int K, int bn, int splits);
+ctm_status ctm_tc_plan_get(ctm_precision prec, int M, int N, int K, int* bn, int* splits);
+
+/* Temperature scan: nbeta independent runs of Algorithm 3 that differ only
+ * in beta (the paper's temperature sweeps, Figs. 3-5).  Each beta gets its
+ * own handle and workspace; a pool of `workers` host threads (1..64), each
+ * with its own non-blocking CUDA stream, takes the betas in order and steps
+ * each one until it converges (delta < tol_spectrum) or has taken max_steps
+ * steps in this call, so betas converge independently with uneven step
+ * counts and the kernels of different betas overlap on the GPU.
+ *  - ctm_scan_init: base is the configuration of every beta except beta
+ *    itself (betas: host, nbeta entries, each validated as in ctm_init).
+ *    base->workspace NULL: the scan allocates all workspaces; otherwise it
+ *    must hold ctm_scan_workspace_size bytes (caller-owned).  cuda_stream is
+ *    synchronised once so that work queued on the workspace comes first;
+ *    the scan then uses its own streams.  Uses the device current at init.
+ *  - ctm_scan_run: steps every not-yet-converged beta; steps_done and
+ *    converged (host, nbeta entries each, may be NULL) receive the steps
+ *    taken in this call and the convergence flags.  Returns the first hard
+ *    error of any beta (with "beta[i]:" in the message), else
+ *    CTM_ENOTCONVERGED if a subspace iteration hit its cap, else CTM_OK.
+ *    Returns after every beta's work has finished.
+ *  - ctm_scan_observables: ctm_observables of every beta (out: nbeta).
+ *  - ctm_scan_handle: the handle of one beta (owned by the scan) for the
+ *    per-handle calls; ctm_scan_get_spectrum: its Omega (m entries).
+ *  - ctm_scan_tune: ctm_tune on the first beta's handle (the shapes are
+ *    the same for all).
+ * A scan is not thread-safe: one host thread at a time per scan. */
+typedef struct ctm_scan ctm_scan;
+ctm_status ctm_scan_workspace_size(const ctm_config* base, int nbeta, size_t* bytes);
+ctm_status ctm_scan_init(ctm_scan** s, const ctm_config* base, int nbeta, const double* betas, int workers,
+                         void* cuda_stream);
+ctm_status ctm_scan_tune(ctm_scan* s, int reps, ctm_tune_entry* out, int max_out, int* n_out);
+ctm_status ctm_scan_run(ctm_scan* s, int max_steps, int* steps_done, int* converged);
+ctm_status ctm_scan_observables(ctm_scan* s, ctm_obs* out);
+ctm_status ctm_scan_handle(ctm_scan* s, int ibeta, ctm_handle** h);
+ctm_status ctm_scan_get_spectrum(ctm_scan* s, int ibeta, double* omega);
+void ctm_scan_destroy(ctm_scan* s);
 
 const char* ctm_last_error(void);
 void ctm_destroy(ctm_handle* h);

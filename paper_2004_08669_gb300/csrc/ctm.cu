@@ -18,7 +18,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -53,7 +56,8 @@ struct Layout {
         off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
         off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
         off_ozSA, off_ozSB, off_ozeP, off_ozeBig, off_ozeSA, off_ozeSB, off_oaX, off_oaW1, off_oaS, off_oaR, off_oaE,
-        off_oapart, off_oaclus, total;
+        off_oapart, off_oaclus, off_tcpart, total;
+    size_t tcpart_cap;  // doubles of the split-K partial buffer of the tensor-core GEMM
     int slices;     // digit planes of the FP64-emulating form
     int prec;       // ctm_precision
     int esz;        // operand element bytes (2 bf16, 4 tf32; 0 in FP64 form)
@@ -135,6 +139,18 @@ Layout make_layout(const ctm_config& c) {
         L.off_opUp = take(N * L.ldm * e);
         L.off_opU = take(m * L.ldN * e);
         L.off_tcerr = take(sizeof(int));
+        // split-K partial tiles: up to 4 slices of the N x b product
+        L.tcpart_cap = 4 * N * b;
+        L.off_tcpart = take(L.tcpart_cap * d);
+        // digit-plane slots of the FP64-emulated small products (N x b x b,
+        // b x b x N) of the Rayleigh-Ritz and Cholesky QR steps
+        const int S = L.slices, Ni = L.N, bi = L.b;
+        auto opA = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, true); };
+        auto opB = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, false); };
+        L.off_ozSA = take(std::max(opA(Ni, bi), opA(bi, Ni)));
+        L.off_ozSB = take(std::max(opB(bi, Ni), opB(bi, bi)));
+        L.off_ozeSA = take(N * sizeof(int));
+        L.off_ozeSB = take(N * sizeof(int));
     }
     if (c.prec == CTM_OZAKI64) {
         // digit-plane slots: P (A role, kept from the extension to the P
@@ -170,6 +186,7 @@ struct ctm_handle {
     int* mfull;
     void *opP = nullptr, *opPw = nullptr, *opC = nullptr, *opV = nullptr, *opUp = nullptr, *opU = nullptr;
     int* tcerr = nullptr;
+    double* tcpart = nullptr;
     void *ozP = nullptr, *ozBig = nullptr, *ozSA = nullptr, *ozSB = nullptr;
     int *ozeP = nullptr, *ozeBig = nullptr, *ozeSA = nullptr, *ozeSB = nullptr;
     ctm::EigWork ew;
@@ -514,15 +531,39 @@ void pconvert(ctm_handle* h, int R, int K, const double* src, int lds, const dou
     prof_end(h, a, PC_CONVERT, 1, 0.0, (double)R * K * 8.0 + (double)R * ldo * h->lay.esz);
 }
 
+// Launch shapes picked by ctm_tune, per (operand bytes, M, N, K); shared by
+// every handle of the process (the best shape depends on the GEMM, not on
+// the data).
+struct TcKey {
+    int esz, M, N, K;
+    bool operator<(const TcKey& o) const {
+        if (esz != o.esz) return esz < o.esz;
+        if (M != o.M) return M < o.M;
+        if (N != o.N) return N < o.N;
+        return K < o.K;
+    }
+};
+std::mutex g_tc_mu;
+std::map<TcKey, ctm::TcPlan> g_tc_plans;
+
+ctm::TcPlan tc_plan_for(int esz, int M, int N, int K) {
+    std::lock_guard<std::mutex> g(g_tc_mu);
+    auto it = g_tc_plans.find(TcKey{esz, M, N, K});
+    if (it != g_tc_plans.end()) return it->second;
+    return ctm::tc_default_plan(M, N, K, esz == 2);
+}
+
 // Profiled tensor-core GEMM D = A B^t (operands already converted).
 ctm_status ptc(ctm_handle* h, int M, int N, int K, const void* A, int lda, const void* B, int ldb, double* D,
                int ldd) {
     cudaEvent_t a = prof_begin(h);
-    cudaError_t e = ctm::tc_gemm(h->st, h->lay.esz == 2, M, N, K, 1.0, A, lda, B, ldb, 0.0, D, ldd, h->tcerr);
+    const ctm::TcPlan plan = tc_plan_for(h->lay.esz, M, N, K);
+    cudaError_t e = ctm::tc_gemm(h->st, h->lay.esz == 2, M, N, K, 1.0, A, lda, B, ldb, 0.0, D, ldd, h->tcerr, &plan,
+                                 h->tcpart, h->lay.tcpart_cap);
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("tc_gemm: ") + cudaGetErrorString(e));
     double fl = 2.0 * M * (double)N * K;
     double by = (double)h->lay.esz * ((double)M * K + (double)K * N) + 8.0 * (double)M * N;
-    prof_end(h, a, PC_TCGEMM, 1, fl, by);
+    prof_end(h, a, PC_TCGEMM, ctm::tc_plan_slices(plan, K, h->lay.esz == 2, nullptr) > 1 ? 2 : 1, fl, by);
     return CTM_OK;
 }
 
@@ -577,6 +618,12 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
 }
 
 inline bool is_oz(const ctm_handle* h) { return h->lay.prec == CTM_OZAKI64; }
+
+// The N x b x b and b x b x N products of the Rayleigh-Ritz and Cholesky QR
+// steps must be FP64-accurate in every form: the mixed-precision forms run
+// them as FP64 emulated on the tensor cores (their slots SA / SB exist in
+// every form but FP64), the FP64 form on the FP64 cores.
+inline bool oz_small(const ctm_handle* h) { return h->lay.prec != CTM_FP64; }
 
 void pwcontract(ctm_handle* h, double* X, const double* E1, const int* live_dev, int live_host, bool sym = false) {
     const Layout& L = h->lay;
@@ -636,7 +683,7 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
     double* cur = src;
     for (int i = 0; i < passes; ++i) {
         double* out = bufs[(passes - 1 - i) % 2];
-        if (is_oz(h)) {
+        if (oz_small(h)) {
             ctm_status s0 = ozmm(h, b, b, N, {cur, N, 1, nullptr}, OZ_SA, true, {cur, N, 1, nullptr}, OZ_SB, true,
                                  h->G, b);
             if (s0 != CTM_OK) return s0;
@@ -657,7 +704,7 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
             ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
             prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
         }
-        if (is_oz(h)) {
+        if (oz_small(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {cur, 1, N, nullptr}, OZ_SA, true, {h->Linv, 1, b, nullptr}, OZ_SB, true,
                                  out, N);
             if (s0 != CTM_OK) return s0;
@@ -732,8 +779,11 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             pconvert(h, b, N, h->V, N, nullptr, h->opV, L.ldN);
             ctm_status s0 = ptc(h, N, b, N, h->opC, L.ldN, h->opV, L.ldN, h->Y, N);
             if (s0 != CTM_OK) return s0;
-            if (!skip_rr)
-                pgemm(h, true, false, b, b, N, h->V, N, h->Y, N, h->H, b, nullptr, gemm_splits(L, b, b, N));
+            if (!skip_rr) {
+                s0 = ozmm(h, b, b, N, {h->V, N, 1, nullptr}, OZ_SA, true, {h->Y, N, 1, nullptr}, OZ_SB, true, h->H,
+                          b);
+                if (s0 != CTM_OK) return s0;
+            }
         } else {
             pgemm(h, false, false, N, b, N, h->C, N, h->V, N, h->Y, N);
             if (!skip_rr)
@@ -776,7 +826,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         prof_end(h, ja, PC_JACOBI, nk_rr);
         // the solve's algorithmic FLOPs are known after the next sync
         h->jac_rec = (used < 0 && h->prof_on && ja) ? (int)h->recs.size() - 1 : -1;
-        if (is_oz(h)) {
+        if (oz_small(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {h->V, 1, N, nullptr}, OZ_SA, true, {h->Sb, b, 1, nullptr}, OZ_SB, true,
                                  h->Z, N);
             if (s0 != CTM_OK) return s0;
@@ -890,7 +940,8 @@ ctm_status step_once(ctm_handle* h) {
     if (h->hctl->numeric_bad) return fail(CTM_ENUMERIC, "non-finite values in the renormalisation");
     if (h->tcerr) {
         int e = 0;
-        CTM_CUDA(cudaMemcpy(&e, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+        CTM_CUDA(cudaMemcpyAsync(&e, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CTM_CUDA(cudaStreamSynchronize(h->st));
         if (e) return fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
     }
     // the warm start for the next step is this step's aligned Ritz block
@@ -995,6 +1046,11 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
         h->opUp = h->ws + L.off_opUp;
         h->opU = h->ws + L.off_opU;
         h->tcerr = (int*)(h->ws + L.off_tcerr);
+        h->tcpart = D(L.off_tcpart);
+        h->ozSA = h->ws + L.off_ozSA;
+        h->ozSB = h->ws + L.off_ozSB;
+        h->ozeSA = (int*)(h->ws + L.off_ozeSA);
+        h->ozeSB = (int*)(h->ws + L.off_ozeSB);
     }
     if (L.prec == CTM_OZAKI64) {
         h->ozP = h->ws + L.off_ozP;
@@ -1165,7 +1221,11 @@ size_t contract_ws(ctm_precision prec, int slices, int M, int N, int K) {
                align256((size_t)M * sizeof(int)) + align256((size_t)N * sizeof(int)) + 256;
     size_t esz = (prec == CTM_BF16) ? 2 : 4;
     size_t ld = (size_t)ctm::tc_ld(K);
-    return align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz) + 256;
+    // the split-K partial tiles of the launch shape in force for this GEMM
+    const ctm::TcPlan p = tc_plan_for((int)esz, M, N, K);
+    const int sl = ctm::tc_plan_slices(p, K, esz == 2, nullptr);
+    const size_t part = sl > 1 ? align256((size_t)sl * M * N * sizeof(double)) : 0;
+    return align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz) + 256 + part;
 }
 bool contract_prec_ok(ctm_precision p) {
     return p == CTM_FP64 || p == CTM_TF32 || p == CTM_BF16 || p == CTM_OZAKI64;
@@ -1221,15 +1281,42 @@ ctm_status ctm_contract(ctm_precision prec, int ozaki_slices, int M, int N, int 
         void* Aop = ws;
         void* Bop = ws + align256((size_t)M * ld * esz);
         err = (int*)(ws + align256((size_t)M * ld * esz) + align256((size_t)N * ld * esz));
+        double* part = (double*)((char*)err + 256);
+        const size_t cap = (workspace_bytes - ((char*)part - ws)) / sizeof(double);
+        const ctm::TcPlan plan = tc_plan_for((int)esz, M, N, K);
         CTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         ctm::to_operand(st, bf16, M, K, A, lda, nullptr, Aop, ld);
         ctm::to_operand(st, bf16, N, K, B, ldb, nullptr, Bop, ld);
-        CTM_CUDA(ctm::tc_gemm(st, bf16, M, N, K, 1.0, Aop, ld, Bop, ld, 0.0, D, ldd, err));
+        CTM_CUDA(ctm::tc_gemm(st, bf16, M, N, K, 1.0, Aop, ld, Bop, ld, 0.0, D, ldd, err, &plan, part, cap));
     }
     int herr = 0;
     CTM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CTM_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
+    return CTM_OK;
+}
+
+ctm_status ctm_tc_plan_set(ctm_precision prec, int M, int N, int K, int bn, int splits) {
+    if (prec != CTM_TF32 && prec != CTM_BF16) return fail(CTM_EINVAL, "launch shapes exist for TF32 / BF16 only");
+    if (M < 1 || N < 1 || K < 1) return fail(CTM_EINVAL, "bad sizes");
+    const int esz = prec == CTM_BF16 ? 2 : 4;
+    std::lock_guard<std::mutex> g(g_tc_mu);
+    if (splits == 0) {
+        g_tc_plans.erase(TcKey{esz, M, N, K});
+        return CTM_OK;
+    }
+    if (bn != 64 && bn != 128 && bn != 256) return fail(CTM_EINVAL, "bn must be 64, 128 or 256");
+    if (splits < 1 || splits > 16) return fail(CTM_EINVAL, "splits must be in [1, 16] (0 clears)");
+    g_tc_plans[TcKey{esz, M, N, K}] = ctm::TcPlan{bn, splits};
+    return CTM_OK;
+}
+
+ctm_status ctm_tc_plan_get(ctm_precision prec, int M, int N, int K, int* bn, int* splits) {
+    if (prec != CTM_TF32 && prec != CTM_BF16) return fail(CTM_EINVAL, "launch shapes exist for TF32 / BF16 only");
+    if (!bn || !splits) return fail(CTM_EINVAL, "NULL argument");
+    const ctm::TcPlan p = tc_plan_for(prec == CTM_BF16 ? 2 : 4, M, N, K);
+    *bn = p.bn;
+    *splits = ctm::tc_plan_slices(p, K, prec == CTM_BF16, nullptr);
     return CTM_OK;
 }
 
@@ -1478,6 +1565,303 @@ ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out) {
     }
     CTM_CUDA(cudaStreamSynchronize(h->st));
     return conv ? CTM_OK : fail(CTM_ENOTCONVERGED, "subspace iteration reached its cap");
+}
+
+// ------------------------------------------------------------- autotuner
+ctm_status ctm_tune(ctm_handle* h, int reps, ctm_tune_entry* out, int max_out, int* n_out) {
+    if (!h) return fail(CTM_EINVAL, "handle is NULL");
+    if (n_out) *n_out = 0;
+    const Layout& L = h->lay;
+    if (!L.esz) return CTM_OK;  // only the tensor-core GEMM of the TF32 / BF16 forms has launch shapes
+    if (reps <= 0) reps = 5;
+    const bool bf16 = L.esz == 2;
+    struct Shape {
+        int M, N, K;
+        const void *A, *B;
+        int lda, ldb;
+        double* D;
+        int ldd;
+    };
+    // the three products of a step: X1 = P^t Omega P (and X1' = P^t U'),
+    // C~ V, and P_new = U^t X
+    const Shape sh[3] = {{L.N, L.N, L.m, h->opP, h->opPw, L.ldm, L.ldm, h->C, L.N},
+                         {L.N, L.b, L.N, h->opC, h->opV, L.ldN, L.ldN, h->Y, L.N},
+                         {L.m, L.N, L.N, h->opU, h->opC, L.ldN, L.ldN, h->Pn, L.m}};
+    // operand copies, C, Y and Pn are scratch between steps; time on zeros
+    const size_t e = L.esz;
+    CTM_CUDA(cudaMemsetAsync(h->opP, 0, (size_t)L.N * L.ldm * e, h->st));
+    CTM_CUDA(cudaMemsetAsync(h->opPw, 0, (size_t)L.N * L.ldm * e, h->st));
+    CTM_CUDA(cudaMemsetAsync(h->opC, 0, (size_t)L.N * L.ldN * e, h->st));
+    CTM_CUDA(cudaMemsetAsync(h->opV, 0, (size_t)L.b * L.ldN * e, h->st));
+    CTM_CUDA(cudaMemsetAsync(h->opU, 0, (size_t)L.m * L.ldN * e, h->st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CTM_CUDA(cudaEventCreate(&e0));
+    CTM_CUDA(cudaEventCreate(&e1));
+    auto done = [&](ctm_status st) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    };
+    int n = 0;
+    for (const Shape& S : sh) {
+        std::vector<ctm::TcPlan> cand{ctm::tc_default_plan(S.M, S.N, S.K, bf16)};
+        for (int bn : {64, 128, 256})
+            for (int sp : {1, 2, 3, 4, 6, 8}) cand.push_back({bn, sp});
+        std::vector<std::pair<int, int>> seen;
+        double best_ms = 1e30, def_ms = 0.0;
+        ctm::TcPlan best = cand[0];
+        int timed = 0;
+        for (size_t ci = 0; ci < cand.size(); ++ci) {
+            ctm::TcPlan p = cand[ci];
+            const int sl = ctm::tc_plan_slices(p, S.K, bf16, nullptr);
+            if (sl > 1 && (size_t)sl * S.M * S.N > L.tcpart_cap) continue;
+            if (std::find(seen.begin(), seen.end(), std::make_pair(p.bn, sl)) != seen.end()) continue;
+            seen.push_back({p.bn, sl});
+            p.splits = sl;
+            auto launch = [&]() {
+                return ctm::tc_gemm(h->st, bf16, S.M, S.N, S.K, 1.0, S.A, S.lda, S.B, S.ldb, 0.0, S.D, S.ldd,
+                                    h->tcerr, &p, h->tcpart, L.tcpart_cap);
+            };
+            cudaError_t ce = launch();  // warm-up
+            if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("tune: ") + cudaGetErrorString(ce)));
+            cudaEventRecord(e0, h->st);
+            for (int r = 0; r < reps; ++r) launch();
+            cudaEventRecord(e1, h->st);
+            ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("tune: ") + cudaGetErrorString(ce)));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = (double)ms / reps;
+            if (ci == 0) def_ms = per;
+            if (per < best_ms) {
+                best_ms = per;
+                best = p;
+            }
+            ++timed;
+        }
+        {
+            std::lock_guard<std::mutex> g(g_tc_mu);
+            g_tc_plans[TcKey{L.esz, S.M, S.N, S.K}] = best;
+        }
+        if (out && n < max_out) out[n] = ctm_tune_entry{S.M, S.N, S.K, best.bn, best.splits, def_ms, best_ms, timed};
+        ++n;
+    }
+    int err = 0;
+    CTM_CUDA(cudaMemcpyAsync(&err, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    if (n_out) *n_out = std::min(n, max_out);
+    if (err) return done(fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up while tuning"));
+    return done(CTM_OK);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- temperature scan
+// One handle per beta (own workspace); a pool of host threads, each with its
+// own non-blocking stream, takes the betas in order and steps each one until
+// it converges or reaches the step cap.  The handles share nothing on the
+// device, so the betas' kernels overlap on the GPU wherever one beta's
+// launches leave SMs idle (the latency-bound eigensolver and the host
+// round trips of the subspace iteration).
+struct ctm_scan {
+    int dev = 0;
+    int workers = 1;
+    cudaStream_t caller = nullptr;
+    std::vector<double> betas;
+    std::vector<ctm_handle*> hs;
+    std::vector<cudaStream_t> streams;
+    char* ws = nullptr;  // owned block of all workspaces (NULL if the caller gave one)
+};
+
+extern "C" {
+
+ctm_status ctm_scan_workspace_size(const ctm_config* base, int nbeta, size_t* bytes) {
+    if (!bytes) return fail(CTM_EINVAL, "bytes is NULL");
+    if (nbeta < 1) return fail(CTM_EINVAL, "nbeta must be >= 1");
+    size_t one = 0;
+    ctm_status s = ctm_workspace_size(base, &one);
+    if (s != CTM_OK) return s;
+    *bytes = align256(one) * (size_t)nbeta;
+    return CTM_OK;
+}
+
+void ctm_scan_destroy(ctm_scan* sc) {
+    if (!sc) return;
+    for (ctm_handle* h : sc->hs) ctm_destroy(h);
+    for (cudaStream_t st : sc->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    if (sc->ws) cudaFree(sc->ws);
+    delete sc;
+}
+
+ctm_status ctm_scan_init(ctm_scan** out, const ctm_config* base, int nbeta, const double* betas, int workers,
+                         void* cuda_stream) {
+    if (!out) return fail(CTM_EINVAL, "scan pointer is NULL");
+    *out = nullptr;
+    if (!base || !betas) return fail(CTM_EINVAL, "NULL argument");
+    if (nbeta < 1 || nbeta > 4096) return fail(CTM_EINVAL, "nbeta must be in [1, 4096]");
+    if (workers < 1 || workers > 64) return fail(CTM_EINVAL, "workers must be in [1, 64]");
+    for (int i = 0; i < nbeta; ++i) {
+        ctm_config c = *base;
+        c.beta = betas[i];
+        c.workspace = nullptr;
+        ctm_status s = validate(&c);
+        if (s != CTM_OK) return s;
+    }
+    size_t one = 0;
+    {
+        ctm_config c = *base;
+        c.workspace = nullptr;
+        ctm_status s = ctm_workspace_size(&c, &one);
+        if (s != CTM_OK) return s;
+    }
+    const size_t per = align256(one);
+    if (base->workspace && base->workspace_bytes < per * (size_t)nbeta)
+        return fail(CTM_ENOMEM, "workspace smaller than ctm_scan_workspace_size");
+    ctm_scan* sc = new ctm_scan();
+    sc->caller = (cudaStream_t)cuda_stream;
+    sc->workers = std::min(workers, nbeta);
+    sc->betas.assign(betas, betas + nbeta);
+    auto bail = [&](ctm_status st, const std::string& msg) {
+        ctm_scan_destroy(sc);
+        return fail(st, msg);
+    };
+    if (cudaGetDevice(&sc->dev) != cudaSuccess) return bail(CTM_ECUDA, "cudaGetDevice failed");
+    // work already queued on the caller's stream (e.g. on the workspace) first
+    if (cudaStreamSynchronize(sc->caller) != cudaSuccess) return bail(CTM_ECUDA, "caller stream sync failed");
+    char* ws = (char*)base->workspace;
+    if (!ws) {
+        if (cudaMalloc(&sc->ws, per * (size_t)nbeta) != cudaSuccess)
+            return bail(CTM_ENOMEM, "cudaMalloc of the scan workspaces failed");
+        ws = sc->ws;
+    }
+    for (int w = 0; w < sc->workers; ++w) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(CTM_ECUDA, "cudaStreamCreate failed");
+        sc->streams.push_back(st);
+    }
+    for (int i = 0; i < nbeta; ++i) {
+        ctm_config c = *base;
+        c.beta = betas[i];
+        c.workspace = ws + per * (size_t)i;
+        c.workspace_bytes = per;
+        ctm_handle* h = nullptr;
+        ctm_status s = ctm_init(&h, &c, sc->streams[i % sc->workers]);
+        if (s != CTM_OK) {
+            std::string msg = g_err;
+            ctm_scan_destroy(sc);
+            return fail(s, "beta[" + std::to_string(i) + "]: " + msg);
+        }
+        sc->hs.push_back(h);
+    }
+    *out = sc;
+    return CTM_OK;
+}
+
+ctm_status ctm_scan_tune(ctm_scan* sc, int reps, ctm_tune_entry* out, int max_out, int* n_out) {
+    if (!sc) return fail(CTM_EINVAL, "scan is NULL");
+    // every handle has the same layout: one tuning serves them all
+    return ctm_tune(sc->hs[0], reps, out, max_out, n_out);
+}
+
+ctm_status ctm_scan_run(ctm_scan* sc, int max_steps, int* steps_done, int* converged) {
+    if (!sc) return fail(CTM_EINVAL, "scan is NULL");
+    if (max_steps < 0) return fail(CTM_EINVAL, "max_steps < 0");
+    const int nb = (int)sc->hs.size();
+    std::vector<int> done(nb, 0);
+    std::vector<ctm_status> stat(nb, CTM_OK);
+    std::vector<std::string> msg(nb);
+    std::atomic<int> next{0};
+    std::atomic<int> dev_fail{0};
+    int caller_dev = 0;
+    cudaGetDevice(&caller_dev);
+    auto worker = [&](int w) {
+        if (cudaSetDevice(sc->dev) != cudaSuccess) {
+            // no beta is taken by this worker; the others finish the queue
+            dev_fail.store(1);
+            return;
+        }
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nb) break;
+            ctm_handle* h = sc->hs[i];
+            if (h->last.converged || max_steps == 0) continue;
+            h->st = sc->streams[w];  // the previous owner synchronised its stream
+            int d = 0;
+            stat[i] = ctm_step(h, max_steps, &d, nullptr);
+            done[i] = d;
+            if (stat[i] != CTM_OK) msg[i] = g_err;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < sc->workers; ++w) pool.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : pool) t.join();
+    cudaSetDevice(caller_dev);
+    if (dev_fail.load() && next.load() < nb) return fail(CTM_ECUDA, "no worker could select the scan's device");
+    ctm_status worst = CTM_OK;
+    int worst_i = -1;
+    for (int i = 0; i < nb; ++i) {
+        if (steps_done) steps_done[i] = done[i];
+        if (converged) converged[i] = sc->hs[i]->last.converged;
+        if (stat[i] == CTM_OK) continue;
+        const bool hard = stat[i] != CTM_ENOTCONVERGED;
+        if (worst_i < 0 || (hard && worst == CTM_ENOTCONVERGED)) {
+            worst = stat[i];
+            worst_i = i;
+        }
+    }
+    if (worst_i >= 0) return fail(worst, "beta[" + std::to_string(worst_i) + "]: " + msg[worst_i]);
+    return CTM_OK;
+}
+
+ctm_status ctm_scan_observables(ctm_scan* sc, ctm_obs* out) {
+    if (!sc || !out) return fail(CTM_EINVAL, "NULL argument");
+    const int nb = (int)sc->hs.size();
+    std::vector<ctm_status> stat(nb, CTM_OK);
+    std::vector<std::string> msg(nb);
+    std::atomic<int> next{0};
+    int caller_dev = 0;
+    cudaGetDevice(&caller_dev);
+    auto worker = [&](int w) {
+        if (cudaSetDevice(sc->dev) != cudaSuccess) return;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nb) break;
+            sc->hs[i]->st = sc->streams[w];
+            stat[i] = ctm_observables(sc->hs[i], &out[i]);
+            if (stat[i] != CTM_OK) msg[i] = g_err;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < sc->workers; ++w) pool.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : pool) t.join();
+    cudaSetDevice(caller_dev);
+    if (next.load() < nb) return fail(CTM_ECUDA, "no worker could select the scan's device");
+    for (int i = 0; i < nb; ++i)
+        if (stat[i] != CTM_OK && stat[i] != CTM_ENOTCONVERGED)
+            return fail(stat[i], "beta[" + std::to_string(i) + "]: " + msg[i]);
+    for (int i = 0; i < nb; ++i)
+        if (stat[i] != CTM_OK) return fail(stat[i], "beta[" + std::to_string(i) + "]: " + msg[i]);
+    return CTM_OK;
+}
+
+ctm_status ctm_scan_handle(ctm_scan* sc, int ibeta, ctm_handle** h) {
+    if (!sc || !h) return fail(CTM_EINVAL, "NULL argument");
+    if (ibeta < 0 || ibeta >= (int)sc->hs.size()) return fail(CTM_EINVAL, "ibeta out of range");
+    *h = sc->hs[ibeta];
+    return CTM_OK;
+}
+
+ctm_status ctm_scan_get_spectrum(ctm_scan* sc, int ibeta, double* omega) {
+    ctm_handle* h = nullptr;
+    ctm_status s = ctm_scan_handle(sc, ibeta, &h);
+    if (s != CTM_OK) return s;
+    return ctm_get_spectrum(h, omega);
 }
 
 }  // extern "C"

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace ctm {
 
@@ -1101,15 +1102,21 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
     int grid = (int)nU;
     const size_t smem = 2 * (size_t)npad * sizeof(int);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    static std::mutex mu;  // host threads may drive handles concurrently
     static int limit = 0;
     static size_t limit_smem = 0;
-    if (limit == 0 || smem > limit_smem) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_jacobi<JA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        limit = coop_grid_limit((const void*)k_jacobi<JA>, 256, smem);
-        limit_smem = smem;
+    int lim;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (limit == 0 || smem > limit_smem) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(k_jacobi<JA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            limit = coop_grid_limit((const void*)k_jacobi<JA>, 256, smem);
+            limit_smem = smem;
+        }
+        lim = limit;
     }
-    if (grid > limit) grid = limit;
+    if (grid > lim) grid = lim;
     if (grid < 1) grid = 1;
     double fl = floor_rel > 0.0 ? floor_rel : 0.0;
     double* diag = w.diag;
@@ -1139,10 +1146,8 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
     // shift is relative: the kernel adds shift * trace(G) to the diagonal.
     // ctl->chol_status is sticky (atomicMax): the caller clears it.
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
-    static int limit = 0;
-    if (limit == 0)
-        limit = std::min(coop_grid_limit((const void*)k_cholesky<C64>, 256, 0),
-                         coop_grid_limit((const void*)k_cholesky<CDF>, 256, 0));
+    static const int limit = std::min(coop_grid_limit((const void*)k_cholesky<C64>, 256, 0),
+                                      coop_grid_limit((const void*)k_cholesky<CDF>, 256, 0));
     const long T = (n + 15) / 16;
     int grid = (int)std::max<long>(T * (T + 1) / 2, (n + 255) / 256);
     if (grid > limit) grid = limit;
@@ -1157,10 +1162,14 @@ void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int l
     const int nb = (n + 31) / 32;
     k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch);
     const size_t smem = ((size_t)8 * nb * 32 + 3 * 32 * 33 + 8 * 32) * sizeof(double);
+    static std::mutex mu;
     static size_t attr = 48 * 1024;
-    if (smem > attr) {
-        cudaFuncSetAttribute(k_trinv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (smem > attr) {
+            cudaFuncSetAttribute(k_trinv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = smem;
+        }
     }
     k_trinv_cols<<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx);
 }

@@ -496,11 +496,11 @@ cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
                       const int* eA, const int* eB, double* D, int ldd, int kper, int splits, double* part,
                       int* err) {
     const size_t smem = 1024 + (size_t)OzStages<S>::value * S * (kOzBM * kOzKT * 2 + kOzBN * kOzKT * 2);
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {
         cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN, splits);
     k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err);
     if (splits > 1) {

@@ -6,7 +6,9 @@
 //   A: M x K, B: N x K, both K-major (row r of the operand is contiguous in k),
 //   stored as BF16 or FP32 with a leading dimension that is a multiple of 64.
 //
-// One CTA computes a 128 x BN tile (BN = 128 or 256).  Warp 0 (one lane)
+// One CTA computes a 128 x BN tile (BN = 64, 128 or 256) over one slice of
+// K (split-K: blockIdx.z; partial tiles go to an FP64 buffer that a second
+// kernel sums in a fixed order).  Warp 0 (one lane)
 // streams K-tiles of A and B into a 4-stage shared-memory ring with TMA
 // (128-byte swizzle); warp 1 (one lane) issues tcgen05.mma into a TMEM
 // accumulator and releases each stage with tcgen05.commit; then all four
@@ -128,7 +130,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 template <int KIND, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-              int K, double alpha, double beta, double* __restrict__ D, int ldd, int* err) {
+              int K, double alpha, double beta, double* __restrict__ D, int ldd, int kchunk,
+              double* __restrict__ part, int* err) {
     // K elements per 128-byte swizzle row: 64 (bf16) or 32 (fp32 / tf32)
     constexpr int KT = (KIND == 0) ? 64 : 32;
     constexpr int KMMA = (KIND == 0) ? 16 : 8;  // K per instruction (32 bytes)
@@ -146,7 +149,10 @@ __global__ void __launch_bounds__(128, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const int nk = (K + KT - 1) / KT;
+    // this CTA's K-tiles: [kt0, kt0 + nk); the host makes every slice non-empty
+    const int nk_all = (K + KT - 1) / KT;
+    const int kt0 = blockIdx.z * kchunk;
+    const int nk = max(0, min(nk_all - kt0, kchunk));
 
     if (threadIdx.x == 0) {
         s_fail = 0;
@@ -180,8 +186,8 @@ __global__ void __launch_bounds__(128, 1)
                 }
             }
             mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &mapA, &full_bar[s], kt * KT, m0);
-            tma_load_2d(sB + s * B_BYTES, &mapB, &full_bar[s], kt * KT, n0);
+            tma_load_2d(sA + s * A_BYTES, &mapA, &full_bar[s], (kt0 + kt) * KT, m0);
+            tma_load_2d(sB + s * B_BYTES, &mapB, &full_bar[s], (kt0 + kt) * KT, n0);
             ++issued_tma;
         }
     } else if (warp == 1 && lane == 0) {
@@ -217,8 +223,12 @@ __global__ void __launch_bounds__(128, 1)
             mbar_wait(&full_bar[s], (kt / kStages) & 1, err);
         }
     }
-    if (ok && !s_fail) {
+    if (ok && !s_fail && nk > 0) {
         const int row = m0 + warp * 32 + lane;
+        // split-K: slice z of the partial buffer (M x N, leading dimension M)
+        double* out = part ? part + (size_t)blockIdx.z * M * N : D;
+        const size_t ldo = part ? (size_t)M : (size_t)ldd;
+        const double bet = part ? 0.0 : beta;
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
             float v[32];
@@ -228,9 +238,9 @@ __global__ void __launch_bounds__(128, 1)
                 for (int j = 0; j < 32; ++j) {
                     int col = n0 + c + j;
                     if (col < N) {
-                        double* d = D + row + (size_t)ldd * col;
+                        double* d = out + row + ldo * col;
                         double val = alpha * (double)v[j];
-                        if (beta != 0.0) val += beta * (*d);
+                        if (bet != 0.0) val += bet * (*d);
                         *d = val;
                     }
                 }
@@ -243,6 +253,19 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
                      : "memory");
+    }
+}
+
+// D = sum_z part[z] + beta * D, the slices summed in order z = 0, 1, ...
+__global__ void k_tc_reduce(int M, int N, int splits, const double* __restrict__ part, double beta,
+                            double* __restrict__ D, int ldd) {
+    const size_t tot = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        double s = part[e];
+        for (int z = 1; z < splits; ++z) s += part[(size_t)z * tot + e];
+        double* d = D + (e % M) + (size_t)ldd * (e / M);
+        if (beta != 0.0) s += beta * (*d);
+        *d = s;
     }
 }
 
@@ -273,15 +296,16 @@ __global__ void k_to_operand(int R, int K, const double* __restrict__ src, int l
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // resolved once (thread-safe initialisation of a local static)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -302,16 +326,30 @@ bool make_map(CUtensorMap* map, const void* base, bool bf16, int K, int rows, in
 
 template <int KIND, int BN>
 cudaError_t launch_tc(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, double alpha,
-                      double beta, double* D, int ldd, int* err) {
+                      double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err) {
     const size_t smem = 1024 + (size_t)kStages * (kBM * 128 + BN * 128);
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&]() {
         cudaFuncSetAttribute(k_tc_gemm<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        return true;
+    }();
+    (void)attr;
+    dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
+    k_tc_gemm<KIND, BN><<<grid, 128, smem, st>>>(a, b, M, N, K, alpha, beta, D, ldd, kchunk,
+                                                  splits > 1 ? part : nullptr, err);
+    if (splits > 1) {
+        const size_t total = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
+        k_tc_reduce<<<blocks, 256, 0, st>>>(M, N, splits, part, beta, D, ldd);
     }
-    dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN);
-    k_tc_gemm<KIND, BN><<<grid, 128, smem, st>>>(a, b, M, N, K, alpha, beta, D, ldd, err);
     return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_bn(int bn, cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
+                      double alpha, double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err) {
+    if (bn == 64) return launch_tc<KIND, 64>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
+    if (bn == 128) return launch_tc<KIND, 128>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
+    return launch_tc<KIND, 256>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
 }
 
 }  // namespace
@@ -329,20 +367,37 @@ void to_operand(cudaStream_t st, bool bf16, int R, int K, const double* src, int
         k_to_operand<float><<<grid, 256, 0, st>>>(R, K, src, lds, scale, (float*)dst, ldo);
 }
 
+TcPlan tc_default_plan(int M, int N, int K, bool bf16) {
+    (void)M;
+    (void)K;
+    (void)bf16;
+    return TcPlan{N > 128 ? 256 : 128, 1};
+}
+
+int tc_plan_slices(const TcPlan& p, int K, bool bf16, int* kchunk) {
+    const int KT = bf16 ? 64 : 32;
+    const int nk = (K + KT - 1) / KT;
+    int s = std::max(1, std::min(p.splits, nk));
+    const int ch = (nk + s - 1) / s;
+    if (kchunk) *kchunk = ch;
+    return (nk + ch - 1) / ch;  // no slice is left empty
+}
+
 cudaError_t tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, double alpha, const void* A, int lda,
-                    const void* B, int ldb, double beta, double* D, int ldd, int* err) {
+                    const void* B, int ldb, double beta, double* D, int ldd, int* err, const TcPlan* plan,
+                    double* part, size_t part_cap) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if ((lda % 64) || (ldb % 64)) return cudaErrorInvalidValue;
-    const int BN = (N > 128) ? 256 : 128;
+    const TcPlan p = plan ? *plan : tc_default_plan(M, N, K, bf16);
+    if (p.bn != 64 && p.bn != 128 && p.bn != 256) return cudaErrorInvalidValue;
+    int kchunk = 0;
+    const int splits = tc_plan_slices(p, K, bf16, &kchunk);
+    if (splits > 1 && (!part || (size_t)splits * M * N > part_cap)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, bf16, K, M, lda, kBM) || !make_map(&mb, B, bf16, K, N, ldb, BN))
+    if (!make_map(&ma, A, bf16, K, M, lda, kBM) || !make_map(&mb, B, bf16, K, N, ldb, p.bn))
         return cudaErrorInvalidValue;
-    if (bf16) {
-        if (BN == 256) return launch_tc<0, 256>(st, ma, mb, M, N, K, alpha, beta, D, ldd, err);
-        return launch_tc<0, 128>(st, ma, mb, M, N, K, alpha, beta, D, ldd, err);
-    }
-    if (BN == 256) return launch_tc<1, 256>(st, ma, mb, M, N, K, alpha, beta, D, ldd, err);
-    return launch_tc<1, 128>(st, ma, mb, M, N, K, alpha, beta, D, ldd, err);
+    if (bf16) return launch_bn<0>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
+    return launch_bn<1>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
 }
 
 }  // namespace ctm

@@ -62,6 +62,15 @@ class ctm_prof_entry(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class ctm_tune_entry(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("bn", ctypes.c_int),
+                ("splits", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class CtmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS[status] if 0 <= status < len(_STATUS) else status}: {msg}")
@@ -90,6 +99,17 @@ def _load():
         "ctm_profile": [H, ctypes.c_int],
         "ctm_profile_read": [H, ctypes.POINTER(ctm_prof_entry), ctypes.c_int, _ip],
         "ctm_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
+        "ctm_tune": [H, ctypes.c_int, ctypes.POINTER(ctm_tune_entry), ctypes.c_int, _ip],
+        "ctm_tc_plan_set": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "ctm_tc_plan_get": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip],
+        "ctm_scan_workspace_size": [ctypes.POINTER(ctm_config), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "ctm_scan_init": [ctypes.POINTER(H), ctypes.POINTER(ctm_config), ctypes.c_int, _dp, ctypes.c_int,
+                          ctypes.c_void_p],
+        "ctm_scan_tune": [H, ctypes.c_int, ctypes.POINTER(ctm_tune_entry), ctypes.c_int, _ip],
+        "ctm_scan_run": [H, ctypes.c_int, _ip, _ip],
+        "ctm_scan_observables": [H, ctypes.POINTER(ctm_obs)],
+        "ctm_scan_handle": [H, ctypes.c_int, ctypes.POINTER(H)],
+        "ctm_scan_get_spectrum": [H, ctypes.c_int, _dp],
         "ctm_symeig_workspace_size": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
         "ctm_symeig_noalloc": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
@@ -109,6 +129,8 @@ def _load():
     L.ctm_last_error.argtypes = []
     L.ctm_destroy.restype = None
     L.ctm_destroy.argtypes = [H]
+    L.ctm_scan_destroy.restype = None
+    L.ctm_scan_destroy.argtypes = [H]
     return L
 
 
@@ -245,6 +267,75 @@ def ctm_launch_count(h) -> int:
     n = ctypes.c_longlong(0)
     _check(lib.ctm_launch_count(h, ctypes.byref(n)))
     return n.value
+
+
+def ctm_tune(h, reps: int = 5) -> list:
+    arr = (ctm_tune_entry * 8)()
+    n = ctypes.c_int(0)
+    _check(lib.ctm_tune(h, int(reps), arr, 8, ctypes.byref(n)))
+    return [arr[i].to_dict() for i in range(n.value)]
+
+
+def ctm_tc_plan_set(prec: str, M: int, N: int, K: int, bn: int, splits: int):
+    _check(lib.ctm_tc_plan_set(PRECISIONS[prec], int(M), int(N), int(K), int(bn), int(splits)))
+
+
+def ctm_tc_plan_get(prec: str, M: int, N: int, K: int) -> tuple:
+    bn, sp = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.ctm_tc_plan_get(PRECISIONS[prec], int(M), int(N), int(K), ctypes.byref(bn), ctypes.byref(sp)))
+    return bn.value, sp.value
+
+
+def ctm_scan_workspace_size(cfg: ctm_config, nbeta: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib.ctm_scan_workspace_size(ctypes.byref(cfg), int(nbeta), ctypes.byref(n)))
+    return n.value
+
+
+def ctm_scan_init(cfg: ctm_config, betas, workers: int, stream: int = 0):
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    s = ctypes.c_void_p()
+    _check(lib.ctm_scan_init(ctypes.byref(s), ctypes.byref(cfg), len(b), _dptr(b), int(workers),
+                             ctypes.c_void_p(stream)))
+    return s
+
+
+def ctm_scan_tune(s, reps: int = 5) -> list:
+    arr = (ctm_tune_entry * 8)()
+    n = ctypes.c_int(0)
+    _check(lib.ctm_scan_tune(s, int(reps), arr, 8, ctypes.byref(n)))
+    return [arr[i].to_dict() for i in range(n.value)]
+
+
+def ctm_scan_run(s, nbeta: int, max_steps: int):
+    done = np.zeros(nbeta, dtype=np.int32)
+    conv = np.zeros(nbeta, dtype=np.int32)
+    st = _check(lib.ctm_scan_run(s, int(max_steps), done.ctypes.data_as(_ip), conv.ctypes.data_as(_ip)),
+                (CTM_OK, CTM_ENOTCONVERGED))
+    return done, conv, st
+
+
+def ctm_scan_observables(s, nbeta: int):
+    arr = (ctm_obs * nbeta)()
+    st = _check(lib.ctm_scan_observables(s, arr), (CTM_OK, CTM_ENOTCONVERGED))
+    return [arr[i].to_dict() for i in range(nbeta)], st
+
+
+def ctm_scan_handle(s, ibeta: int):
+    h = ctypes.c_void_p()
+    _check(lib.ctm_scan_handle(s, int(ibeta), ctypes.byref(h)))
+    return h
+
+
+def ctm_scan_get_spectrum(s, ibeta: int, m: int) -> np.ndarray:
+    om = np.zeros(m)
+    _check(lib.ctm_scan_get_spectrum(s, int(ibeta), _dptr(om)))
+    return om
+
+
+def ctm_scan_destroy(s):
+    if s:
+        lib.ctm_scan_destroy(s)
 
 
 def ctm_symeig_workspace_size(n: int) -> int:
@@ -384,3 +475,55 @@ class CTMRG:
 
     def load(self, blob: bytes):
         ctm_load(self.h, blob)
+
+
+class Scan:
+    """A temperature scan on the GPU: one handle per beta inside the library,
+    stepped concurrently by its native worker pool; the workspaces come from
+    torch."""
+
+    def __init__(self, spins, m: int, betas, workers: int = 8, boundary_spin: int = 0, prec: str = "fp64",
+                 device: str = "cuda:0", **kw):
+        import torch
+        self.device = torch.device(device)
+        self.betas = np.ascontiguousarray(betas, dtype=np.float64)
+        self.nbeta = len(self.betas)
+        self.cfg, self._spins = make_config(spins, m, 0.0, boundary_spin, prec, **kw)
+        self.m, self.q = m, self._spins.shape[0]
+        nbytes = ctm_scan_workspace_size(self.cfg, self.nbeta)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.cfg.workspace = ctypes.c_void_p(self._ws.data_ptr())
+        self.cfg.workspace_bytes = nbytes
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device)
+            self.s = ctm_scan_init(self.cfg, self.betas, workers, stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "s", None):
+            ctm_scan_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, reps: int = 5) -> list:
+        return ctm_scan_tune(self.s, reps)
+
+    def run(self, max_steps: int):
+        """Step every beta until it converges or takes max_steps steps;
+        returns (steps per beta, converged flags)."""
+        done, conv, st = ctm_scan_run(self.s, self.nbeta, max_steps)
+        return done, conv
+
+    def observables(self) -> list:
+        obs, st = ctm_scan_observables(self.s, self.nbeta)
+        return obs
+
+    def spectrum(self, ibeta: int) -> np.ndarray:
+        return ctm_scan_get_spectrum(self.s, ibeta, self.m)
+
+    def launch_count(self) -> int:
+        return sum(ctm_launch_count(ctm_scan_handle(self.s, i)) for i in range(self.nbeta))
