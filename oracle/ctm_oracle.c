@@ -640,3 +640,57 @@ int or_observables(or_state* s, double* out) {
     free(Z);
     return 0;
 }
+
+/* ---------------------------------------------------------------------
+ * Effective correlation length (Sec. II): the renormalised row-to-row
+ * transfer matrix reconstructed from P~.  A row through the centre is the
+ * left half-row P, the centre vertex W and the right half-row P; its legs
+ * are the upper block legs of the two halves with the centre's upper spin,
+ * and the lower ones (reading R9):
+ *   T[(a, t, a'), (g, u, g')] = sum_{s, s'} P[a, g + m s] W(s, t, s', u) P[a', g' + m s'],
+ * with W's arguments in the cyclic corner order of Eq. (1); by reading R1,
+ * W(s, t, s', u) = w[s + q t, u + q s'].  Row index a + m t + m q a'.
+ * ------------------------------------------------------------------- */
+void or_row_transfer(int m, int q, const double* P, const double* w, double* T) {
+    const size_t n = (size_t)m * q * m;
+#pragma omp parallel for schedule(static)
+    for (long col = 0; col < (long)n; ++col) {
+        const int g = (int)(col % m), u = (int)((col / m) % q), g2 = (int)(col / ((size_t)m * q));
+        for (size_t row = 0; row < n; ++row) {
+            const int a = (int)(row % m), t = (int)((row / m) % q), a2 = (int)(row / ((size_t)m * q));
+            double acc = 0.0;
+            for (int s = 0; s < q; ++s) {
+                const double pl = P[a + (size_t)m * (g + (size_t)m * s)];
+                if (pl == 0.0) continue;
+                for (int s2 = 0; s2 < q; ++s2) {
+                    const double W = w[(s + (size_t)q * t) + (size_t)q * q * (u + (size_t)q * s2)];
+                    acc += pl * W * P[a2 + (size_t)m * (g2 + (size_t)m * s2)];
+                }
+            }
+            T[row + n * col] = acc;
+        }
+    }
+}
+
+/* The k eigenvalues of T of largest modulus (sorted by |lambda| descending)
+ * from a full dense diagonalisation; returns -1 if the eigensolver failed. */
+int or_row_transfer_spectrum(const or_state* s, int k, double* lam) {
+    const int m = s->m, q = s->q;
+    const size_t n = (size_t)m * q * m;
+    double* T = (double*)malloc(n * n * sizeof(double));
+    double* Z = (double*)malloc(n * n * sizeof(double));
+    double* ev = (double*)malloc(n * sizeof(double));
+    or_row_transfer(m, q, s->P, s->w, T);
+    /* symmetric by the reflection of the row (P[a, g, s] = P[g, a, s]) */
+    for (size_t i = 0; i < n; ++i)
+        for (size_t j = i + 1; j < n; ++j) {
+            double v = 0.5 * (T[i + n * j] + T[j + n * i]);
+            T[i + n * j] = T[j + n * i] = v;
+        }
+    int st = or_eigh((int)n, T, ev, Z);
+    for (int i = 0; i < k; ++i) lam[i] = i < (int)n ? ev[i] : 0.0;
+    free(T);
+    free(Z);
+    free(ev);
+    return st;
+}

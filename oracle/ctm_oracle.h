@@ -103,6 +103,18 @@ void or_get_state(const or_state* s, double* P, double* omega, int* live);
 void or_set_state(or_state* s, const double* P, const double* omega, int live);
 int  or_steps_done(const or_state* s);
 
+/* Effective correlation length (Sec. II, reading R9): the renormalised
+ * row-to-row transfer matrix T built from P and the vertex weight,
+ *   T[(a, t, a'), (g, u, g')] = sum_{s,s'} P[a, g + m s] W(s, t, s', u) P[a', g' + m s'],
+ * (m^2 q) x (m^2 q), row index a + m t + m q a', W in the cyclic order of
+ * Eq. (1) (w[s + q t, u + q s'] by reading R1).  T is symmetric. */
+void or_row_transfer(int m, int q, const double* P, const double* w, double* T);
+
+/* The k largest-modulus eigenvalues of T for the current P (full dense
+ * diagonalisation, sorted by |lambda| descending; xi_e = 1 / ln|l0/l1|).
+ * Returns 0, or -1 on eigensolver failure. */
+int or_row_transfer_spectrum(const or_state* s, int k, double* lam);
+
 /* Replace the weight matrices (q^2 x q^2 each, either may be NULL).  Used by
  * the tests that plant a mistake in the oracle and check that a pin fails. */
 void or_set_weights(or_state* s, const double* w, const double* wh);

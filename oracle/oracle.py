@@ -68,6 +68,9 @@ def lib():
             L.or_get_state.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
             L.or_set_state.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
             L.or_set_weights.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.or_row_transfer.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+            L.or_row_transfer_spectrum.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+            L.or_row_transfer_spectrum.restype = ctypes.c_int
             L.or_steps_done.argtypes = [ctypes.c_void_p]
             L.or_steps_done.restype = ctypes.c_int
             _lib = L
@@ -134,6 +137,16 @@ def ctilde_entries(P, omega, w, m: int, q: int, rows, cols) -> np.ndarray:
     return out
 
 
+def row_transfer(P: np.ndarray, w: np.ndarray, m: int, q: int) -> np.ndarray:
+    """The renormalised row-to-row transfer matrix (m^2 q square) built from
+    P (m x m q) and the weight matrix w (reading R9)."""
+    P, w = _f64(P), _f64(w)
+    n = m * q * m
+    T = np.zeros((n, n), order="F")
+    lib().or_row_transfer(m, q, _p(P), _p(w), _p(T))
+    return T
+
+
 def eigh(A: np.ndarray):
     """All eigenpairs of a symmetric matrix, sorted by |eigenvalue| descending."""
     A = np.array(A, dtype=np.float64, order="F", copy=True)
@@ -197,6 +210,20 @@ class CTMRG:
         if lib().or_observables(self._h, out.ctypes.data_as(_dp)) != 0:
             raise RuntimeError("oracle observables failed")
         return dict(zip(self.OBS_KEYS, out.tolist()))
+
+    def row_transfer_spectrum(self, k: int = 4) -> np.ndarray:
+        """k largest-modulus eigenvalues of the row-to-row transfer matrix
+        of the current state (full dense diagonalisation)."""
+        lam = np.zeros(k)
+        if lib().or_row_transfer_spectrum(self._h, int(k), lam.ctypes.data_as(_dp)) != 0:
+            raise RuntimeError("oracle eigensolver did not converge")
+        return lam
+
+    def xi(self) -> float:
+        """Effective correlation length xi_e = 1 / ln|l0 / l1| in units of
+        the vertex-row spacing."""
+        lam = self.row_transfer_spectrum(2)
+        return 1.0 / np.log(abs(lam[0] / lam[1]))
 
     def extend(self) -> np.ndarray:
         out = np.zeros((self.N, self.N), order="F")
