@@ -141,6 +141,32 @@ ctm_status ctm_observables(ctm_handle* h, ctm_obs* out);
  * respect to beta.  Not built yet: returns CTM_EUNSUPPORTED. */
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
 
+/* Effective correlation length (Sec. II): the leading eigenvalues of the
+ * renormalised row-to-row transfer matrix reconstructed from the current P
+ * (the row through the centre: half-row P, centre vertex W, half-row P),
+ *   T[(a, t, a'), (g, u, g')] = sum_{s,s'} P(a, g, s) W(s, t, s', u) P(a', g', s'),
+ * W in the cyclic corner order of Eq. (1), of order m^2 q and symmetric.
+ * T is applied implicitly (two GEMMs and a centre-vertex contraction per
+ * application, all FP64) inside a Lanczos iteration with full
+ * reorthogonalisation from a seeded Gaussian vector; the Ritz values of
+ * its tridiagonal matrix come from the library's Jacobi solver.  It stops
+ * when the residual bounds of the two leading Ritz pairs fall below
+ * tol * |lambda_0| (tol <= 0: 1e-12), checked every 4 iterations, or at
+ * max_iters (<= 0: 64; at most 120; at most m^2 q).  xi = 1 / ln|lambda_0 /
+ * lambda_1| in units of the spacing of vertex rows (one diagonal of the
+ * spin lattice).  Call it at a converged state (after ctm_step); it
+ * allocates about (max_iters + 3) m^2 q doubles of scratch for the call and
+ * overwrites the handle's C~ buffer (scratch between steps).  Returns
+ * CTM_ENOTCONVERGED at max_iters (the result is still written). */
+typedef struct {
+    double lambda[4];    /* leading Ritz values, sorted by |lambda| descending */
+    double residual[4];  /* their residual bounds / |lambda_0|                 */
+    double xi;           /* 1 / ln|lambda_0 / lambda_1|                        */
+    int iterations;      /* Lanczos iterations                                 */
+    int converged;
+} ctm_xi_result;
+ctm_status ctm_xi(ctm_handle* h, int max_iters, double tol, ctm_xi_result* out);
+
 /* Normalised kept spectrum Omega (host, m entries; zeros past m_eff). */
 ctm_status ctm_get_spectrum(ctm_handle* h, double* omega);
 

@@ -646,7 +646,7 @@ int or_observables(or_state* s, double* out) {
  * transfer matrix reconstructed from P~.  A row through the centre is the
  * left half-row P, the centre vertex W and the right half-row P; its legs
  * are the upper block legs of the two halves with the centre's upper spin,
- * and the lower ones (reading R9):
+ * and the lower ones (reading R10):
  *   T[(a, t, a'), (g, u, g')] = sum_{s, s'} P[a, g + m s] W(s, t, s', u) P[a', g' + m s'],
  * with W's arguments in the cyclic corner order of Eq. (1); by reading R1,
  * W(s, t, s', u) = w[s + q t, u + q s'].  Row index a + m t + m q a'.

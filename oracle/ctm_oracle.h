@@ -36,6 +36,11 @@
  *      - same (step k-1) | over i < m and |kappa_k/kappa_{k-1} - 1|; the
  *      normalised spectrum settles many steps before kappa (and so f) does.
  *      The paper's c = |1 - S_E/S| is reported too.
+ *  R10 Effective correlation length (Sec. II, "row-to-row transfer matrices
+ *      reconstructed from P~"): the row through the centre is the left
+ *      half-row P, the centre vertex W and the right half-row P, joined at
+ *      the opposite (side) corners of W; xi_e = 1 / ln|l0 / l1| of that
+ *      matrix, in units of the vertex-row spacing.
  */
 #ifndef CTM_ORACLE_H
 #define CTM_ORACLE_H
@@ -103,7 +108,7 @@ void or_get_state(const or_state* s, double* P, double* omega, int* live);
 void or_set_state(or_state* s, const double* P, const double* omega, int live);
 int  or_steps_done(const or_state* s);
 
-/* Effective correlation length (Sec. II, reading R9): the renormalised
+/* Effective correlation length (Sec. II, reading R10): the renormalised
  * row-to-row transfer matrix T built from P and the vertex weight,
  *   T[(a, t, a'), (g, u, g')] = sum_{s,s'} P[a, g + m s] W(s, t, s', u) P[a', g' + m s'],
  * (m^2 q) x (m^2 q), row index a + m t + m q a', W in the cyclic order of

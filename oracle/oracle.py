@@ -139,7 +139,7 @@ def ctilde_entries(P, omega, w, m: int, q: int, rows, cols) -> np.ndarray:
 
 def row_transfer(P: np.ndarray, w: np.ndarray, m: int, q: int) -> np.ndarray:
     """The renormalised row-to-row transfer matrix (m^2 q square) built from
-    P (m x m q) and the weight matrix w (reading R9)."""
+    P (m x m q) and the weight matrix w (reading R10)."""
     P, w = _f64(P), _f64(w)
     n = m * q * m
     T = np.zeros((n, n), order="F")

@@ -30,6 +30,7 @@
 #include "eig_f64.cuh"
 #include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
+#include "xi.cuh"
 
 namespace {
 
@@ -475,10 +476,12 @@ inline int grid_for(size_t work, int cap = 152 * 8) {
 
 // --------------------------------------------------------------- profiling
 enum ProfClass {
-    PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_TCGEMM, PC_CONVERT, PC_OZGEMM, PC_OZSPLIT, PC_SMALL, PC_COUNT
+    PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_TCGEMM, PC_CONVERT, PC_OZGEMM, PC_OZSPLIT, PC_SMALL,
+    PC_XI_W, PC_XI_VEC, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT + 1] = {"gemm_f64", "wcontract_f64", "jacobi_f64", "cholqr_f64", "tc_gemm",
-                                              "to_operand", "oz_gemm", "oz_split", "small", "all"};
+                                              "to_operand", "oz_gemm",  "oz_split",    "small",      "xi_wcontract",
+                                              "xi_lanczos", "all"};
 
 cudaEvent_t take_event(ctm_handle* h) {
     if (h->evnext == h->evpool.size()) {
@@ -756,14 +759,17 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         // on the rotation within span(V), so a later solve extracts the same
         // Ritz pairs.  The residual is predicted from the last measured one
         // and the measured rate per iteration; a solve is taken at the last
-        // allowed iteration, when the prediction reaches 10x the tolerance,
+        // allowed iteration, when the prediction reaches 10x the tolerance
+        // (or the tolerance itself once the residual has stalled: a rate
+        // above 1/2 means it sits near the rounding floor of the operands),
         // and at least every 16 iterations.  Skipped blocks are scaled by the
         // previous Ritz values (their columns are last Ritz vectors) and
         // re-orthonormalised by shifted Cholesky QR.
         bool skip_rr = false;
         if (!cold && it + 1 < max_iters && it - it_meas < 16) {
             const double pred = r_meas * std::pow(h->resid_rate, (double)(it - it_meas));
-            skip_rr = pred > 10.0 * h->cfg.subspace_tol;
+            const double tol = h->cfg.subspace_tol;
+            skip_rr = pred > 10.0 * tol || (h->resid_rate > 0.5 && pred > tol);
         }
         if (is_oz(h)) {
             // C~ is split once per eigen stage (first iteration), V every iteration
@@ -1294,6 +1300,122 @@ ctm_status ctm_contract(ctm_precision prec, int ozaki_slices, int M, int N, int 
     CTM_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(CTM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
     return CTM_OK;
+}
+
+// Effective correlation length (Sec. II): Lanczos with full
+// reorthogonalisation on the row-to-row transfer matrix T of the current P,
+// applied as Phat X (GEMM), the centre-vertex contraction, and A2 P^t (GEMM).
+ctm_status ctm_xi(ctm_handle* h, int max_iters, double tol, ctm_xi_result* out) {
+    if (!h || !out) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    const int m = L.m, q = L.q;
+    const size_t mq = (size_t)m * q, n = mq * m;
+    int K = max_iters <= 0 ? 64 : max_iters;
+    if (K > 120) return fail(CTM_EINVAL, "max_iters must be <= 120");
+    if ((size_t)K > n) K = (int)n;
+    if (!(tol > 0.0)) tol = 1e-12;
+    size_t smem_ta = ctm::xi_w_smem(q, nullptr);
+    if (smem_ta > 200 * 1024) return fail(CTM_EINVAL, "q too large for the centre-vertex contraction");
+    const int npad = (K + 1) + ((K + 1) & 1);
+    const int nb = ctm::xi_dots_blocks(n);
+    // scratch (A1 reuses the N x N corner buffer, scratch between steps)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = off;
+        off = align256(off + bytes);
+        return r;
+    };
+    const size_t d = sizeof(double);
+    const size_t o_A2 = take(mq * mq * d), o_V = take(n * (size_t)(K + 1) * d), o_w = take(n * d),
+                 o_part = take((size_t)(K + 1) * nb * d), o_c = take((size_t)(K + 1) * d),
+                 o_alpha = take((size_t)(K + 1) * d), o_beta = take((size_t)(K + 1) * d),
+                 o_nrm = take(d), o_Tk = take((size_t)K * K * d), o_Sk = take((size_t)K * K * d),
+                 o_th = take((size_t)npad * d), o_A0 = take((size_t)npad * npad * d),
+                 o_B1 = take((size_t)npad * npad * d), o_S = take((size_t)npad * npad * d),
+                 o_dg = take((size_t)npad * d), o_rk = take((size_t)npad * sizeof(int));
+    char* scratch = nullptr;
+    if (cudaMalloc(&scratch, off) != cudaSuccess) return fail(CTM_ENOMEM, "cudaMalloc of the Lanczos scratch failed");
+    auto Dp = [&](size_t o) { return (double*)(scratch + o); };
+    double *A1 = h->C, *A2 = Dp(o_A2), *V = Dp(o_V), *w = Dp(o_w), *part = Dp(o_part), *c = Dp(o_c),
+           *alpha = Dp(o_alpha), *beta = Dp(o_beta), *nrm = Dp(o_nrm), *Tk = Dp(o_Tk), *Sk = Dp(o_Sk),
+           *theta = Dp(o_th);
+    ctm::EigWork ew{};
+    ew.A0 = Dp(o_A0);
+    ew.A1 = Dp(o_B1);
+    ew.S = Dp(o_S);
+    ew.diag = Dp(o_dg);
+    ew.rank = (int*)(scratch + o_rk);
+    auto done = [&](ctm_status st) {
+        cudaStreamSynchronize(h->st);
+        cudaFree(scratch);
+        return st;
+    };
+    cudaStream_t st = h->st;
+    auto vec = [&](int j) { return V + n * (size_t)j; };
+    // seeded Gaussian start vector, normalised
+    ctm::randn_block(st, (int)n, 1, vec(0), (int)n, h->seed ^ 0x5851f42d4c957f2dull);
+    ctm::xi_dots(st, n, 1, vec(0), n, vec(0), part, nrm);
+    ctm::xi_normalise(st, n, vec(0), nrm, vec(0), c);
+    count_small(h, 4);
+    double lam[4] = {0, 0, 0, 0}, res[4] = {0, 0, 0, 0};
+    int it = 0, conv = 0;
+    for (int j = 0; j < K; ++j) {
+        // w = T v_j
+        pgemm(h, false, false, (int)mq, (int)mq, m, h->P, (int)mq, vec(j), m, A1, (int)mq);
+        cudaEvent_t a = prof_begin(h);
+        cudaError_t ce = ctm::xi_wcontract(st, m, q, A1, h->E, A2);
+        if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("xi_wcontract: ") + cudaGetErrorString(ce)));
+        prof_end(h, a, PC_XI_W, 1, 4.0 * q * q * (double)q * m * m, 2.0 * d * mq * mq);
+        pgemm(h, false, true, (int)mq, m, (int)mq, A2, (int)mq, h->P, m, w, (int)mq);
+        // alpha_j = v_j . w (first pass), then two passes of classical
+        // Gram-Schmidt against v_0..v_j, then beta_j = ||w||, v_{j+1} = w / beta_j
+        a = prof_begin(h);
+        ctm::xi_dots(st, n, j + 1, V, n, w, part, c);
+        CTM_CUDA(cudaMemcpyAsync(alpha + j, c + j, d, cudaMemcpyDeviceToDevice, st));
+        ctm::xi_sub_multi(st, n, j + 1, V, n, c, w);
+        ctm::xi_dots(st, n, j + 1, V, n, w, part, c);
+        ctm::xi_sub_multi(st, n, j + 1, V, n, c, w);
+        ctm::xi_dots(st, n, 1, w, n, w, part, nrm);
+        ctm::xi_normalise(st, n, w, nrm, vec(j + 1), beta + j);
+        prof_end(h, a, PC_XI_VEC, 9, 0.0, d * n * (4.0 * (j + 1) + 6.0));
+        it = j + 1;
+        if (it % 4 != 0 && it != K) continue;
+        // Ritz values of the tridiagonal matrix, sorted by |theta|
+        ctm::xi_tridiag(st, it, alpha, beta, Tk);
+        ce = ctm::jacobi_f64(st, it, Tk, it, ew, theta, Sk, it, 40, h->ctl);
+        count_small(h, 5);
+        if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("jacobi_f64: ") + cudaGetErrorString(ce)));
+        double hb[8];
+        const int nr = std::min(4, it);
+        std::vector<double> last(nr);
+        CTM_CUDA(cudaMemcpyAsync(hb, theta, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        for (int i = 0; i < nr; ++i)
+            CTM_CUDA(cudaMemcpyAsync(&last[i], Sk + (it - 1) + (size_t)it * i, d, cudaMemcpyDeviceToHost, st));
+        double bj = 0.0;
+        CTM_CUDA(cudaMemcpyAsync(&bj, beta + j, d, cudaMemcpyDeviceToHost, st));
+        ctm_status s0 = sync_ctl(h);
+        if (s0 != CTM_OK) return done(s0);
+        if (h->hctl->jac_status == 2) return done(fail(CTM_ETIMEOUT, "a device-side barrier timed out"));
+        for (int i = 0; i < 4; ++i) {
+            lam[i] = i < nr ? hb[i] : 0.0;
+            res[i] = i < nr ? fabs(bj * last[i]) : 0.0;
+        }
+        const double scale = fabs(lam[0]) > 0.0 ? fabs(lam[0]) : 1.0;
+        for (int i = 0; i < 4; ++i) res[i] /= scale;
+        const bool invariant = bj <= 1e-14 * scale;
+        if (invariant || (res[0] <= tol && (nr < 2 || res[1] <= tol))) {
+            conv = 1;
+            break;
+        }
+    }
+    out->iterations = it;
+    out->converged = conv;
+    for (int i = 0; i < 4; ++i) {
+        out->lambda[i] = lam[i];
+        out->residual[i] = res[i];
+    }
+    out->xi = (lam[1] != 0.0) ? 1.0 / log(fabs(lam[0] / lam[1])) : 0.0;
+    return done(conv ? CTM_OK : fail(CTM_ENOTCONVERGED, "Lanczos reached max_iters"));
 }
 
 ctm_status ctm_tc_plan_set(ctm_precision prec, int M, int N, int K, int bn, int splits) {

@@ -62,6 +62,15 @@ class ctm_prof_entry(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class ctm_xi_result(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double * 4), ("residual", ctypes.c_double * 4), ("xi", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int)]
+
+    def to_dict(self):
+        return {"lambda": list(self.lambda_), "residual": list(self.residual), "xi": self.xi,
+                "iterations": self.iterations, "converged": self.converged}
+
+
 class ctm_tune_entry(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("bn", ctypes.c_int),
                 ("splits", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
@@ -89,6 +98,7 @@ def _load():
         "ctm_observables": [H, ctypes.POINTER(ctm_obs)],
         "ctm_step_backward": [H, ctypes.POINTER(ctm_obs), _dp],
         "ctm_get_spectrum": [H, _dp],
+        "ctm_xi": [H, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctm_xi_result)],
         "ctm_get_state": [H, _dp, _dp, _ip],
         "ctm_set_state": [H, _dp, _dp, ctypes.c_int],
         "ctm_save": [H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -195,6 +205,12 @@ def ctm_step_backward(h, grad_obs: ctm_obs):
     g = np.zeros(1)
     _check(lib.ctm_step_backward(h, ctypes.byref(grad_obs), _dptr(g)))
     return g
+
+
+def ctm_xi(h, max_iters: int = 0, tol: float = 0.0) -> tuple:
+    r = ctm_xi_result()
+    st = _check(lib.ctm_xi(h, int(max_iters), float(tol), ctypes.byref(r)), (CTM_OK, CTM_ENOTCONVERGED))
+    return r.to_dict(), st
 
 
 def ctm_get_spectrum(h, m: int) -> np.ndarray:
@@ -444,6 +460,11 @@ class CTMRG:
 
     def spectrum(self) -> np.ndarray:
         return ctm_get_spectrum(self.h, self.m)
+
+    def xi(self, max_iters: int = 0, tol: float = 0.0) -> dict:
+        """Effective correlation length and the leading eigenvalues of the
+        row-to-row transfer matrix of the current state."""
+        return ctm_xi(self.h, max_iters, tol)[0]
 
     def get_state(self):
         return ctm_get_state(self.h, self.m, self.q)

@@ -1,5 +1,5 @@
 """Pins of the oracle's effective correlation length (Sec. II): the
-renormalised row-to-row transfer matrix T built from P and W (reading R9).
+renormalised row-to-row transfer matrix T built from P and W (reading R10).
 
 - Brute force: while nothing is truncated (q^k <= m), the half-row P after
   k steps is the exact half row of k vertices in an orthonormal basis, so T
