@@ -55,7 +55,7 @@ struct Layout {
     size_t off_spins, off_E, off_Eh, off_mag, off_P, off_Pn, off_omega, off_prev, off_C, off_V, off_Y,
         off_Z, off_T, off_Zprev, off_U, off_Up, off_H, off_Sb, off_G, off_Linv, off_theta, off_res,
         off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
-        off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
+        off_S1, off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
         off_ozSA, off_ozSB, off_ozeP, off_ozeBig, off_ozeSA, off_ozeSB, off_oaX, off_oaW1, off_oaS, off_oaR, off_oaE,
         off_oapart, off_oaclus, off_tcpart, total;
     size_t tcpart_cap;  // doubles of the split-K partial buffer of the tensor-core GEMM
@@ -111,6 +111,7 @@ Layout make_layout(const ctm_config& c) {
     L.off_A0 = take(np * np * d);
     L.off_A1 = take(np * np * d);
     L.off_S = take(np * np * d);
+    L.off_S1 = take(np * np * d);
     L.off_diag = take(np * d);
     L.off_rank = take(np * sizeof(int));
     L.off_gd = take(3 * np * d);
@@ -1072,6 +1073,7 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
     h->ew.A0 = D(L.off_A0);
     h->ew.A1 = D(L.off_A1);
     h->ew.S = D(L.off_S);
+    h->ew.S1 = D(L.off_S1);  // double-buffered S: two Jacobi rounds per grid barrier
     h->ew.diag = D(L.off_diag);
     h->ew.rank = (int*)(h->ws + L.off_rank);
     h->ew.gdots = D(L.off_gd);

@@ -238,7 +238,302 @@ __device__ __forceinline__ void jac_pair(int r, int k, int s2, const int* perm, 
 }
 
 constexpr int JT = 8;        // pairs per side of an A unit (JT x JT 2x2 blocks)
-constexpr int JS_ROWS = 32;  // rows of S per S unit (JT pairs x JS_ROWS rows)
+constexpr int JS_ROWS = 32;  // rows of S per pass of an S unit (JT pairs x JS_ROWS rows)
+constexpr int JS_PASS = 2;   // passes per S unit: each thread owns JS_PASS rows, JS_ROWS apart
+
+// The pair of index x in round r of the tournament over the first s2 entries
+// of perm (inv: positions in perm): its partner y, the pair's slot k (as in
+// jac_pair; k >= s2 / 2 is a fixed pair that is never rotated) and whether x
+// is the pair's first index p.
+struct JPartner {
+    int y, k;
+    bool isp;
+};
+__device__ __forceinline__ JPartner jac_partner(int r, int x, int s2, const int* perm, const int* inv) {
+    const int a = inv[x];
+    if (a >= s2) {
+        const int o = a - s2;
+        return JPartner{perm[s2 + (o ^ 1)], (s2 >> 1) + (o >> 1), (o & 1) == 0};
+    }
+    const int n1 = s2 - 1;
+    if (a == n1) return JPartner{perm[r], 0, true};
+    if (a == r) return JPartner{perm[n1], 0, false};
+    int d = a - r;
+    if (d < 0) d += n1;
+    if (d <= (n1 - 1) / 2) {  // a = r + d: x is p of pair d, q sits at r - d
+        int b = r - d;
+        if (b < 0) b += n1;
+        return JPartner{perm[b], d, true};
+    }
+    const int k = n1 - d;  // a = r - k: x is q of pair k, p sits at r + k
+    int b = r + k;
+    if (b >= n1) b -= n1;
+    return JPartner{perm[b], k, false};
+}
+
+// alpha u + beta v
+template <class JA>
+__device__ __forceinline__ typename JA::T jcomb(typename JA::T al, typename JA::T u, typename JA::T be,
+                                                typename JA::T v) {
+    return JA::lin(al, u, JA::neg(be), v);
+}
+
+// Entry (x, y) of J^t A J for one round, J acting on x as x' = ax x + bx pi(x)
+// (and likewise on y): from A[x][y], A[x][pi y], A[pi x][y], A[pi x][pi y].
+template <class JA>
+__device__ __forceinline__ typename JA::T jprime(typename JA::T ax, typename JA::T bx, typename JA::T ay,
+                                                 typename JA::T by, typename JA::T a_xy, typename JA::T a_xpy,
+                                                 typename JA::T a_pxy, typename JA::T a_pxpy) {
+    return jcomb<JA>(ay, jcomb<JA>(ax, a_xy, bx, a_pxy), by, jcomb<JA>(ax, a_xpy, bx, a_pxpy));
+}
+
+// Two consecutive rounds r, r + 1 of the tournament between two grid
+// barriers.  Each output entry of round r + 1, A''[x][y] with x, y in the
+// round's pairs, is a combination of the 2 x 2 block of A' (the state after
+// round r) on those pairs, and each entry of A' one of a 2 x 2 block of A
+// on the round-r partners: 16 reads of A per 2 x 2 output block instead of 4.
+// A unit recomputes the round-r rotations of all indices in its pairs and the
+// round-(r + 1) rotations of its pairs (whose inputs, the diagonal blocks of
+// A', it forms from A the same way), so one barrier, one round of reads and
+// two rotation chains replace two of each.  S reads the four columns of the
+// round-r partners and writes the other buffer.
+// Thread roles in an A unit (JT x JT tile of round-(r + 1) pair blocks):
+//   [0, 2 JT^2)             one row of a 2 x 2 output block each (its row of
+//                           A' goes through shared memory to the other row);
+//   [2 JT^2, 2 JT^2 + 4 JT) the round-r rotation of one index of the tile's pairs;
+//   [.., + 2 JT)            the round-(r + 1) rotation of one of the tile's pairs.
+// In an S unit (JT pairs x JS_PASS JS_ROWS rows) every thread owns JS_PASS rows of a pair
+// and threads [0, 2 JT) / [2 JT, 3 JT) also take the rotations.
+template <class JA>
+__device__ __forceinline__ void jac_fused(int r, int s2, int nh, int npad, int half, int nT, int nA, int nRC, int nU,
+                                          const int* perm, const int* inv, const typename JA::T* Ac,
+                                          typename JA::T* An, const typename JA::T* Sc, typename JA::T* Sn,
+                                          double eps, double floor_abs, int& my_rot, typename JA::T* f_al,
+                                          typename JA::T* f_be, typename JA::T* f_c, typename JA::T* f_s,
+                                          int* f_on, typename JA::T* f_ap) {
+    using T = typename JA::T;
+    const int tid = threadIdx.x;
+    for (int u = blockIdx.x; u < nU; u += gridDim.x) {
+        const bool isA = u < nA;
+        int kA0 = 0, kB0 = 0, rc = 0;
+        bool diagT = false;
+        if (isA) {
+            int I = 0, rem = u;
+            while (rem >= nT - I) {
+                rem -= nT - I;
+                ++I;
+            }
+            kA0 = JT * I;
+            kB0 = JT * (I + rem);
+            diagT = rem == 0;
+        } else {
+            const int v = u - nA;
+            kA0 = JT * (v / nRC);
+            rc = v % nRC;
+        }
+        // ---- reads first (every role), so that all round trips overlap.  One
+        // buffer serves all roles: an A-unit thread has one role; an S-unit
+        // thread keeps its row in L[0..3] and a rotation's inputs after it.
+        T L[20];
+        int X0 = 0, X1 = 0, Y0 = 0, Y1 = 0, row = -1;
+        int ka = -1, kb = -1, kk = -1, xi = 0, blk = 0;
+        int rslot = -1, nslot = -1;  // round-r index slot, round-(r + 1) pair slot of this thread
+        bool rrot = false, risp = true, nrot = false;
+        const int nslots_r = isA ? 4 * JT : 2 * JT;
+        const int base_r = isA ? 2 * JT * JT : 0;
+        const int base_n = isA ? 2 * JT * JT + 4 * JT : 2 * JT;
+        const int nslots_n = isA ? 2 * JT : JT;
+        if (isA) {
+            if (tid < 2 * JT * JT) {
+                blk = tid >> 1;
+                xi = tid & 1;
+                const int a = blk % JT, b = blk / JT;
+                if (kA0 + a < half && kB0 + b < half && (!diagT || a <= b)) {
+                    ka = kA0 + a;
+                    kb = kB0 + b;
+                    jac_pair(r + 1, ka, s2, perm, X0, X1);
+                    jac_pair(r + 1, kb, s2, perm, Y0, Y1);
+                    const int x = xi ? X1 : X0;
+                    const int px = jac_partner(r, x, s2, perm, inv).y;
+                    const int ys[2] = {Y0, Y1};
+                    const int py[2] = {jac_partner(r, Y0, s2, perm, inv).y, jac_partner(r, Y1, s2, perm, inv).y};
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        L[4 * j + 0] = JA::ld(Ac + x + (size_t)npad * ys[j]);
+                        L[4 * j + 1] = JA::ld(Ac + x + (size_t)npad * py[j]);
+                        L[4 * j + 2] = JA::ld(Ac + px + (size_t)npad * ys[j]);
+                        L[4 * j + 3] = JA::ld(Ac + px + (size_t)npad * py[j]);
+                    }
+                }
+            }
+        } else {
+            kk = tid / JS_ROWS;
+            const int rw = rc * JS_ROWS * JS_PASS + tid % JS_ROWS;
+            if (kk < JT && kA0 + kk < half && rw < npad) {
+                ka = kA0 + kk;
+                row = rw;
+                jac_pair(r + 1, ka, s2, perm, X0, X1);
+                const int p0 = jac_partner(r, X0, s2, perm, inv).y, p1 = jac_partner(r, X1, s2, perm, inv).y;
+                L[0] = JA::ld(Sc + row + (size_t)npad * X0);
+                L[1] = JA::ld(Sc + row + (size_t)npad * p0);
+                L[2] = JA::ld(Sc + row + (size_t)npad * X1);
+                L[3] = JA::ld(Sc + row + (size_t)npad * p1);
+                if (row + JS_ROWS < npad) {
+                    L[16] = JA::ld(Sc + row + JS_ROWS + (size_t)npad * X0);
+                    L[17] = JA::ld(Sc + row + JS_ROWS + (size_t)npad * p0);
+                    L[18] = JA::ld(Sc + row + JS_ROWS + (size_t)npad * X1);
+                    L[19] = JA::ld(Sc + row + JS_ROWS + (size_t)npad * p1);
+                }
+            }
+        }
+        // round-r rotation of one index of the unit's round-(r + 1) pairs
+        if (tid >= base_r && tid < base_r + nslots_r) {
+            rslot = tid - base_r;
+            const int ps = rslot >> 1;
+            const int k1 = ps < JT ? kA0 + ps : kB0 + ps - JT;
+            if (k1 < half) {
+                int p1, q1;
+                jac_pair(r + 1, k1, s2, perm, p1, q1);
+                const int x = (rslot & 1) ? q1 : p1;
+                const JPartner P = jac_partner(r, x, s2, perm, inv);
+                if (P.k < nh) {
+                    const int rp = P.isp ? x : P.y, rq = P.isp ? P.y : x;
+                    const T v0 = JA::ld(Ac + rp + (size_t)npad * rp);
+                    const T v1 = JA::ld(Ac + rq + (size_t)npad * rq);
+                    const T v2 = JA::ld(Ac + rp + (size_t)npad * rq);
+                    if (isA) {
+                        L[0] = v0;
+                        L[1] = v1;
+                        L[2] = v2;
+                    } else {
+                        L[4] = v0;
+                        L[5] = v1;
+                        L[6] = v2;
+                    }
+                    rrot = true;
+                    risp = P.isp;
+                }
+            }
+        }
+        // round-(r + 1) rotation of one of the unit's pairs: its diagonal block of A'
+        int np1 = 0, nq1 = 0;
+        if (tid >= base_n && tid < base_n + nslots_n) {
+            nslot = tid - base_n;
+            const int k1 = nslot < JT ? kA0 + nslot : kB0 + nslot - JT;
+            if (k1 < half && k1 < nh) {
+                jac_pair(r + 1, k1, s2, perm, np1, nq1);
+                const int pp = jac_partner(r, np1, s2, perm, inv).y, pq = jac_partner(r, nq1, s2, perm, inv).y;
+                const int ra[10] = {np1, np1, pp, nq1, nq1, pq, np1, np1, pp, pp};
+                const int cb[10] = {np1, pp, pp, nq1, pq, pq, nq1, pq, nq1, pq};
+                if (isA) {
+#pragma unroll
+                    for (int i = 0; i < 10; ++i) L[i] = JA::ld(Ac + ra[i] + (size_t)npad * cb[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 10; ++i) L[4 + i] = JA::ld(Ac + ra[i] + (size_t)npad * cb[i]);
+                }
+                nrot = true;
+            }
+        }
+        // ---- phase 1: round-r coefficients (x' = al x + be pi(x))
+        if (rslot >= 0) {
+            T al = JA::one(), be = JA::zero();
+            if (rrot) {
+                const T v0 = isA ? L[0] : L[4], v1 = isA ? L[1] : L[5], v2 = isA ? L[2] : L[6];
+                const typename JA::R R = JA::rot(v0, v1, v2, eps, floor_abs);
+                if (R.on) {
+                    al = R.c;
+                    be = risp ? JA::neg(R.s) : R.s;
+                    if (!isA && rc == 0 && risp) ++my_rot;
+                }
+            }
+            f_al[rslot] = al;
+            f_be[rslot] = be;
+        }
+        __syncthreads();
+        // ---- phase 2: round-(r + 1) rotations from A' = (round r applied to A),
+        // and each block row's entries of A'
+        if (isA && ka >= 0) {
+            const int a = ka - kA0, b = kb - kB0;
+            const int sx = 2 * a + xi, sy = 2 * (JT + b);  // round-r slots of this row and of Y0
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                f_ap[4 * blk + 2 * xi + j] =
+                    jprime<JA>(f_al[sx], f_be[sx], f_al[sy + j], f_be[sy + j], L[4 * j], L[4 * j + 1], L[4 * j + 2],
+                               L[4 * j + 3]);
+        }
+        if (nslot >= 0) {
+            typename JA::R R{JA::one(), JA::zero(), false};
+            if (nrot) {
+                const T ap = f_al[2 * nslot], bp = f_be[2 * nslot];
+                const T aq = f_al[2 * nslot + 1], bq = f_be[2 * nslot + 1];
+                T nv[10];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) nv[i] = isA ? L[i] : L[4 + i];
+                const T app = jprime<JA>(ap, bp, ap, bp, nv[0], nv[1], nv[1], nv[2]);
+                const T aqq = jprime<JA>(aq, bq, aq, bq, nv[3], nv[4], nv[4], nv[5]);
+                const T apq = jprime<JA>(ap, bp, aq, bq, nv[6], nv[7], nv[8], nv[9]);
+                R = JA::rot(app, aqq, apq, eps, floor_abs);
+                if (R.on && !isA && rc == 0) ++my_rot;
+            }
+            f_c[nslot] = R.c;
+            f_s[nslot] = R.s;
+            f_on[nslot] = R.on ? 1 : 0;
+        }
+        __syncthreads();
+        // ---- phase 3: outputs
+        if (ka >= 0) {
+            if (isA) {
+                const int a = ka - kA0, b = kb - kB0;
+                const T* ap = f_ap + 4 * blk;  // A' on rows {X0, X1} x cols {Y0, Y1}, row-major
+                // round r + 1: x' = al x + be partner, (al, be) = (c, -s) for p, (c, s) for q
+                const bool ona = f_on[a] != 0, onb = f_on[JT + b] != 0;
+                const T ca = ona ? f_c[a] : JA::one(), sa = ona ? f_s[a] : JA::zero();
+                const T cb = onb ? f_c[JT + b] : JA::one(), sb = onb ? f_s[JT + b] : JA::zero();
+                const T bx = xi ? sa : JA::neg(sa);
+                const T by[2] = {JA::neg(sb), sb};
+                const int i = xi;
+                T o[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    o[j] = jprime<JA>(ca, bx, cb, by[j], ap[2 * i + j], ap[2 * i + 1 - j], ap[2 * (1 - i) + j],
+                                      ap[2 * (1 - i) + 1 - j]);
+                const int x = xi ? X1 : X0;
+                if (ka == kb) {
+                    if (xi == 0) {
+                        An[X0 + (size_t)npad * X0] = o[0];
+                        An[X0 + (size_t)npad * X1] = o[1];
+                        An[X1 + (size_t)npad * X0] = o[1];
+                    } else {
+                        An[X1 + (size_t)npad * X1] = o[1];
+                    }
+                } else {
+                    An[x + (size_t)npad * Y0] = o[0];
+                    An[Y0 + (size_t)npad * x] = o[0];
+                    An[x + (size_t)npad * Y1] = o[1];
+                    An[Y1 + (size_t)npad * x] = o[1];
+                }
+            } else {
+                const int sx = 2 * kk;
+                const bool on = f_on[kk] != 0;
+                const T c = on ? f_c[kk] : JA::one(), sn = on ? f_s[kk] : JA::zero();
+                {
+                    const T s0 = jcomb<JA>(f_al[sx], L[0], f_be[sx], L[1]);
+                    const T s1 = jcomb<JA>(f_al[sx + 1], L[2], f_be[sx + 1], L[3]);
+                    Sn[row + (size_t)npad * X0] = jcomb<JA>(c, s0, JA::neg(sn), s1);
+                    Sn[row + (size_t)npad * X1] = jcomb<JA>(c, s1, sn, s0);
+                }
+                if (row + JS_ROWS < npad) {
+                    const T s0 = jcomb<JA>(f_al[sx], L[16], f_be[sx], L[17]);
+                    const T s1 = jcomb<JA>(f_al[sx + 1], L[18], f_be[sx + 1], L[19]);
+                    Sn[row + JS_ROWS + (size_t)npad * X0] = jcomb<JA>(c, s0, JA::neg(sn), s1);
+                    Sn[row + JS_ROWS + (size_t)npad * X1] = jcomb<JA>(c, s1, sn, s0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
 
 // Cooperative: all blocks co-resident (cudaLaunchAttributeCooperative).
 //
@@ -254,27 +549,32 @@ constexpr int JS_ROWS = 32;  // rows of S per S unit (JT pairs x JS_ROWS rows)
 // A round is split into units of similar FP64 cost, one or more per block:
 // an A unit is a JT x JT tile of the upper triangle of 2x2 blocks of A (the
 // transposed block is written from the same values, so A stays exactly
-// symmetric); an S unit is JT column pairs x JS_ROWS rows of S.  A unit
+// symmetric); an S unit is JT column pairs x JS_PASS x JS_ROWS rows of S.  A unit
 // computes only the (at most 2 JT) rotations it needs, with its input loads
 // issued before the rotations so that both memory round trips overlap.  A is
 // double-buffered (read from one buffer, written in full to the other); S is
 // updated in place (the round's column pairs are disjoint).
 template <class JA>
-__global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
-                                                typename JA::T* S, double* __restrict__ diag, int* act,
-                                                int max_sweeps, double eps, double floor_rel, DevCtl* ctl) {
+__global__ void __launch_bounds__(256, 2) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
+                                                typename JA::T* S, typename JA::T* S1, double* __restrict__ diag,
+                                                int* act, int max_sweeps, double eps, double floor_rel,
+                                                DevCtl* ctl) {
     using T = typename JA::T;
     extern __shared__ int jsh[];
-    int* perm = jsh;         // npad: tagged indices first
-    int* flg = jsh + npad;   // npad: tag flags of this sweep
+    int* perm = jsh;             // npad: tagged indices first
+    int* flg = jsh + npad;       // npad: tag flags of this sweep
+    int* inv = jsh + 2 * npad;   // npad: position of each index in perm
     __shared__ T u_c[2 * JT], u_s[2 * JT];
     __shared__ int u_on[2 * JT];
+    // fused rounds: round-r coefficients per index slot, round-(r+1) rotations per pair slot
+    __shared__ T f_al[4 * JT], f_be[4 * JT], f_c[2 * JT], f_s[2 * JT], f_ap[4 * JT * JT];
+    __shared__ int f_on[2 * JT];
     __shared__ double s_red[8];
     __shared__ int s_cnt;
     const int half = npad / 2;
     const int nT = (half + JT - 1) / JT;
     const int nA = nT * (nT + 1) / 2;
-    const int nRC = (npad + JS_ROWS - 1) / JS_ROWS;
+    const int nRC = (npad + JS_ROWS * JS_PASS - 1) / (JS_ROWS * JS_PASS);
     const int nU = nA + nT * nRC;
     const long gtid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const long gstride = (long)gridDim.x * blockDim.x;
@@ -337,6 +637,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T*
             if (tid == 0) s_cnt = ntag;
         }
         __syncthreads();
+        for (int a = tid; a < npad; a += blockDim.x) inv[perm[a]] = a;
+        __syncthreads();
         const int ntag = s_cnt;
         if (ntag == 0) {
             converged = true;
@@ -346,9 +648,22 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T*
         int s2 = ntag + (ntag & 1);  // ntag odd => ntag < npad: an untagged index exists
         if (4 * s2 > 3 * npad) s2 = npad;
         const int nh = s2 / 2;
-        for (int r = 0; r < s2 - 1; ++r, ++rt) {
+        for (int r = 0; r < s2 - 1;) {
             const T* Ac = (rt & 1) ? A1 : A0;
             T* An = (rt & 1) ? A0 : A1;
+            // S is double-buffered when S1 is given (a fused pair of rounds
+            // reads columns that other units write), else updated in place
+            const T* Sc = (S1 && (rt & 1)) ? S1 : S;
+            T* Sn = S1 ? ((rt & 1) ? S : S1) : S;
+            const bool fuse = S1 != nullptr && r + 2 <= s2 - 1;
+            if (fuse) {
+                jac_fused<JA>(r, s2, nh, npad, half, nT, nA, nRC, nU, perm, inv, Ac, An, Sc, Sn, eps, floor_abs,
+                              my_rot, f_al, f_be, f_c, f_s, f_on, f_ap);
+                r += 2;
+                ++rt;
+                if (!grid_sync(&ctl->bar_count, epoch, err)) return;
+                continue;
+            }
             for (int u = blockIdx.x; u < nU; u += gridDim.x) {
                 const bool isA = u < nA;
                 int kA0, kB0 = 0, rc = 0;
@@ -391,14 +706,19 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T*
                         }
                     }
                 } else {
+                    // rows rw and rw + JS_ROWS (x0, x1 and x2, x3)
                     const int kk = tid / JS_ROWS;
-                    const int rw = rc * JS_ROWS + tid % JS_ROWS;
+                    const int rw = rc * JS_ROWS * JS_PASS + tid % JS_ROWS;
                     if (kk < JT && kA0 + kk < half && rw < npad) {
                         ka = kA0 + kk;
                         row = rw;
                         jac_pair(r, ka, s2, perm, p, q);
-                        x0 = JA::ld(S + row + (size_t)npad * p);
-                        x1 = JA::ld(S + row + (size_t)npad * q);
+                        x0 = JA::ld(Sc + row + (size_t)npad * p);
+                        x1 = JA::ld(Sc + row + (size_t)npad * q);
+                        if (row + JS_ROWS < npad) {
+                            x2 = JA::ld(Sc + row + JS_ROWS + (size_t)npad * p);
+                            x3 = JA::ld(Sc + row + JS_ROWS + (size_t)npad * q);
+                        }
                     }
                 }
                 // the unit's rotations
@@ -467,15 +787,29 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T*
                         }
                     } else {
                         const int ia = ka - kA0;
+                        const bool two = row + JS_ROWS < npad;
                         if (u_on[ia]) {
                             const T c = u_c[ia], sn = u_s[ia];
-                            S[row + (size_t)npad * p] = JA::lin(c, x0, sn, x1);
-                            S[row + (size_t)npad * q] = JA::lin(sn, x0, JA::neg(c), x1);
+                            Sn[row + (size_t)npad * p] = JA::lin(c, x0, sn, x1);
+                            Sn[row + (size_t)npad * q] = JA::lin(sn, x0, JA::neg(c), x1);
+                            if (two) {
+                                Sn[row + JS_ROWS + (size_t)npad * p] = JA::lin(c, x2, sn, x3);
+                                Sn[row + JS_ROWS + (size_t)npad * q] = JA::lin(sn, x2, JA::neg(c), x3);
+                            }
+                        } else if (Sn != Sc) {
+                            Sn[row + (size_t)npad * p] = x0;
+                            Sn[row + (size_t)npad * q] = x1;
+                            if (two) {
+                                Sn[row + JS_ROWS + (size_t)npad * p] = x2;
+                                Sn[row + JS_ROWS + (size_t)npad * q] = x3;
+                            }
                         }
                     }
                 }
                 __syncthreads();
             }
+            ++r;
+            ++rt;
             if (!grid_sync(&ctl->bar_count, epoch, err)) return;
         }
         if (my_rot) atomicAdd(&ctl->rot_count[sweep < 64 ? sweep : 63], my_rot);
@@ -483,6 +817,9 @@ __global__ void __launch_bounds__(256) k_jacobi(int n, int npad, typename JA::T*
     }
     const T* Af = (rt & 1) ? A1 : A0;
     for (long i = gtid; i < n; i += gstride) diag[i] = JA::to(JA::ld(Af + i + (size_t)npad * i));
+    // the eigenvectors end in S (every block passed the last barrier)
+    if (S1 && (rt & 1))
+        for (long e = gtid; e < (long)npad * npad; e += gstride) S[e] = JA::ld(S1 + e);
     if (gtid == 0) {
         ctl->jac_sweeps = sweep;
         if (!converged) atomicMax(err, 1);
@@ -1098,9 +1435,9 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
     if (max_sweeps > 64) max_sweeps = 64;
     const long half = npad / 2;
     const long nT = (half + JT - 1) / JT;
-    const long nU = nT * (nT + 1) / 2 + nT * ((npad + JS_ROWS - 1) / JS_ROWS);
+    const long nU = nT * (nT + 1) / 2 + nT * ((npad + JS_ROWS * JS_PASS - 1) / (JS_ROWS * JS_PASS));
     int grid = (int)nU;
-    const size_t smem = 2 * (size_t)npad * sizeof(int);
+    const size_t smem = 3 * (size_t)npad * sizeof(int);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     static std::mutex mu;  // host threads may drive handles concurrently
     static int limit = 0;
@@ -1121,7 +1458,8 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
     double fl = floor_rel > 0.0 ? floor_rel : 0.0;
     double* diag = w.diag;
     int* act = w.rank;  // the sweep tags; rank is rewritten by the sort below
-    void* args[] = {&n, &npad, &A0, &A1, &S, &diag, &act, &max_sweeps, &eps, &fl, &ctl};
+    T* S1 = (T*)w.S1;  // NULL: one round per barrier, S in place
+    void* args[] = {&n, &npad, &A0, &A1, &S, &S1, &diag, &act, &max_sweeps, &eps, &fl, &ctl};
     cudaError_t e = launch_coop((const void*)k_jacobi<JA>, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);

@@ -13,6 +13,7 @@ struct EigWork {
     double* A0;     // npad x npad (Jacobi, two buffers)
     double* A1;
     double* S;      // npad x npad accumulated rotations
+    double* S1;     // npad x npad second buffer of S, or NULL (then one round per grid barrier)
     double* diag;   // npad
     int* rank;      // npad (also the Jacobi sweep tags)
     double* gdots;  // 3 b
