@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--xi", action="store_true",
                     help="time the effective correlation length (Lanczos on the row-to-row transfer matrix) "
                          "at the --m / --T workload instead; --steps evaluations after --prep steps")
+    ap.add_argument("--physics", action="store_true",
+                    help="finite-m scaling at T_c = 0.4398: run each m of --physics-ms to convergence, then "
+                         "xi_e and S_E; the fitted kappa and central charge beside the paper's")
+    ap.add_argument("--physics-ms", default="32,64,128,256")
     ap.add_argument("--scan-m", type=int, default=128)
     ap.add_argument("--scan-nbeta", type=int, default=32)
     ap.add_argument("--scan-prec", default="tf32")
@@ -675,6 +679,47 @@ def run_xi(args):
     print(json.dumps(out), flush=True)
 
 
+def run_physics(args):
+    """xi_e(T_c, m) ~ m^kappa and S_E = (c / 6) ln xi_e + const at the
+    paper's T_c, against its printed kappa and c."""
+    import numpy as np
+    import torch
+
+    from paper_2004_08669_gb300 import build
+    build.build()
+    from paper_2004_08669_gb300 import ctm, workloads as W
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tc_scaling.json")))
+    T = gold["T_c"]
+    prec = args.modes.split(",")[0]
+    rows = []
+    t0 = time.perf_counter()
+    for m in [int(x) for x in args.physics_ms.split(",")]:
+        g = ctm.CTMRG(W.dodecahedron(), m, 1.0 / T, prec=prec, device="cuda:0")
+        ts = time.perf_counter()
+        done, info = g.run(5000)
+        torch.cuda.synchronize()
+        run_s = time.perf_counter() - ts
+        obs = g.observables()
+        xi = g.xi(max_iters=120, tol=1e-10)
+        rows.append({"m": m, "steps": done, "converged": info["converged"], "delta": info["delta"],
+                     "f": obs["f"], "M": obs["M"], "u": obs["u"], "S_E": obs["S_E"], "xi_e": xi["xi"],
+                     "xi_converged": xi["converged"], "run_s": run_s})
+        g.close()
+    lm = np.log([r["m"] for r in rows])
+    lx = np.log([r["xi_e"] for r in rows])
+    se = np.array([r["S_E"] for r in rows])
+    kappa = float(np.polyfit(lm, lx, 1)[0])
+    c = float(6.0 * np.polyfit(lx, se, 1)[0])
+    pairs = [{"m": [rows[i]["m"], rows[i + 1]["m"]],
+              "kappa": float((lx[i + 1] - lx[i]) / (lm[i + 1] - lm[i])),
+              "c": float(6.0 * (se[i + 1] - se[i]) / (lx[i + 1] - lx[i]))} for i in range(len(rows) - 1)]
+    out = {"metric": "finite-m scaling at T_c (kappa, central charge) vs the paper", "T": T, "prec": prec,
+           "kappa_fit": kappa, "c_fit": c, "pairwise": pairs, "paper": {k: gold[k] for k in
+                                                                        ("kappa", "kappa_error", "c", "c_error")},
+           "runs": rows, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+
+
 def run_profile(args):
     """The timed workload's steps bracketed for a profiler, nothing measured."""
     import torch
@@ -710,6 +755,8 @@ def main():
         run_scan(args)
     elif args.xi:
         run_xi(args)
+    elif args.physics:
+        run_physics(args)
     else:
         run_ours(args)
 
