@@ -420,7 +420,7 @@ def run_ours(args):
                       "rayleigh_ritz_paths": res["rayleigh_ritz_paths"], "prep_steps": args.prep},
            "roofline": res["roofline"], "roofline_tensor": res["roofline_tensor"], "e2e": e2e,
            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
-           "kernels_ms_per_step": res["kernels_ms_per_step"]}
+           "kernels_ms_per_step": res["kernels_ms_per_step"], "tuned_shapes": res["tuned_shapes"]}
     if others:
         out["other_modes"] = others
     if cpu is not None:

@@ -271,15 +271,17 @@ ctm_status ctm_profile_read(ctm_handle* h, ctm_prof_entry* out, int max_entries,
 /* Kernels launched by this handle since ctm_init. */
 ctm_status ctm_launch_count(ctm_handle* h, long long* launches);
 
-/* Autotuner of the tensor-core GEMM (CTM_TF32 / CTM_BF16 handles; a no-op
- * with *n_out = 0 for the others).  For each of the three products of the
- * step -- X1 = P^t Omega P (N x N x m), C~ V (N x b x N) and U^t X
- * (m x N x N), N = m q -- it times every launch shape (tile width 64, 128
- * or 256 columns; 1 to 8 K slices, whose partial tiles fit the handle's
- * split-K buffer of 4 N b doubles) with CUDA events on the handle's stream,
- * reps launches each (<= 0: 5), on zeroed operands, and keeps the fastest
- * for every later GEMM of that shape and precision in this process (all
- * handles).  Uses only scratch buffers: call it between steps.  out (host,
+/* Autotuner of the tensor-core GEMMs (a no-op with *n_out = 0 for CTM_FP64).
+ * CTM_TF32 / CTM_BF16: for each of the three products of the step --
+ * X1 = P^t Omega P (N x N x m), C~ V (N x b x N) and U^t X (m x N x N),
+ * N = m q -- it times every launch shape (tile width 64, 128 or 256
+ * columns; 1 to 8 K slices, whose partial tiles fit the handle's split-K
+ * buffer of 4 N b doubles).  CTM_OZAKI64: the K slices (1 to 6 whole
+ * 512-wide exact chunks, or the kernel's own rule) of the two long-K
+ * products C~ V and U^t X (entries report bn = 64, the kernel's fixed tile
+ * width).  Timing uses CUDA events on the handle's stream, reps launches
+ * each (<= 0: 5), on zeroed operands; the fastest shape is kept for every
+ * later GEMM of that shape and precision in this process (all handles).  Uses only scratch buffers: call it between steps.  out (host,
  * may be NULL) receives up to max_out entries, *n_out their count.  Split
  * shapes sum their K slices in a fixed order, so results stay deterministic
  * but change in the last bits of the FP32 accumulation when the shape

@@ -60,6 +60,7 @@ struct Layout {
         off_oapart, off_oaclus, off_tcpart, total;
     size_t tcpart_cap;  // doubles of the split-K partial buffer of the tensor-core GEMM
     int slices;     // digit planes of the FP64-emulating form
+    size_t part_cap;  // doubles of the split-K partial buffer
     int prec;       // ctm_precision
     int esz;        // operand element bytes (2 bf16, 4 tf32; 0 in FP64 form)
     int ldm, ldN;   // operand leading dimensions for K = m and K = N
@@ -106,7 +107,11 @@ Layout make_layout(const ctm_config& c) {
     L.off_Linv = take(b * b * d);
     L.off_theta = take(np * d);
     L.off_res = take(np * d);
-    L.off_part = take((size_t)L.splits * b * b * d);
+    // split-K partials: the b x b Gram products (up to 16 slices) and, in the
+    // FP64-emulating forms, up to 6 slices of the N x b and m x N products
+    L.part_cap = (size_t)L.splits * b * b;
+    if (c.prec != CTM_FP64) L.part_cap = std::max(L.part_cap, (size_t)6 * N * b);
+    L.off_part = take(L.part_cap * d);
     L.off_red = take(4096 * d);
     L.off_A0 = take(np * np * d);
     L.off_A1 = take(np * np * d);
@@ -550,6 +555,16 @@ struct TcKey {
 std::mutex g_tc_mu;
 std::map<TcKey, ctm::TcPlan> g_tc_plans;
 
+// Ozaki GEMM K slices picked by ctm_tune, per (digit planes, M, N, K); 0 = the
+// kernel's own rule.
+std::map<TcKey, int> g_oz_plans;
+
+int oz_plan_for(int S, int M, int N, int K) {
+    std::lock_guard<std::mutex> g(g_tc_mu);
+    auto it = g_oz_plans.find(TcKey{S, M, N, K});
+    return it != g_oz_plans.end() ? it->second : 0;
+}
+
 ctm::TcPlan tc_plan_for(int esz, int M, int N, int K) {
     std::lock_guard<std::mutex> g(g_tc_mu);
     auto it = g_tc_plans.find(TcKey{esz, M, N, K});
@@ -612,8 +627,8 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
         prof_end(h, a, PC_OZSPLIT, nk, 0.0, 8.0 * ((splitA ? (double)M * K : 0.0) + (splitB ? (double)N * K : 0.0)));
     }
     cudaEvent_t a = prof_begin(h);
-    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr, h->part,
-                                 (size_t)h->lay.splits * h->lay.b * h->lay.b);
+    const int req = oz_plan_for(S, M, N, K);
+    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr, h->part, h->lay.part_cap, req);
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("oz_gemm: ") + cudaGetErrorString(e));
     const double pairs = S * (S + 1) / 2.0;
     prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * M * (double)N * K,
@@ -1692,12 +1707,98 @@ ctm_status ctm_eigen(ctm_handle* h, double* evals, double* vecs, int* b_out) {
 }
 
 // ------------------------------------------------------------- autotuner
+}  // extern "C"
+namespace {
+// The FP64-emulating form: K slices of the two long-K products of the step,
+// C~ V (N x b x N) and U^t X (m x N x N), whose output tiles (200 and 160 at
+// m = 256) fill the 152 SMs in one and a bit waves.
+ctm_status tune_oz(ctm_handle* h, int reps, ctm_tune_entry* out, int max_out, int* n_out) {
+    const Layout& L = h->lay;
+    const int S = L.slices, N = L.N, b = L.b, m = L.m;
+    auto opA = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, true); };
+    auto opB = [&](int R, int K) { return ctm::oz_operand_bytes(R, K, S, false); };
+    // digit-plane slots and exponents are scratch between steps: time on zeros
+    CTM_CUDA(cudaMemsetAsync(h->ozBig, 0, std::max(opA(N, N), opB(N, N)), h->st));
+    CTM_CUDA(cudaMemsetAsync(h->ozSA, 0, std::max({opA(N, b), opA(b, N), opA(m, N)}), h->st));
+    CTM_CUDA(cudaMemsetAsync(h->ozSB, 0, std::max({opB(N, m), opB(b, N), opB(b, b)}), h->st));
+    CTM_CUDA(cudaMemsetAsync(h->ozeBig, 0, N * sizeof(int), h->st));
+    CTM_CUDA(cudaMemsetAsync(h->ozeSA, 0, N * sizeof(int), h->st));
+    CTM_CUDA(cudaMemsetAsync(h->ozeSB, 0, N * sizeof(int), h->st));
+    struct Shape {
+        int M, Nn, K;
+        OzSlot sa, sb;
+        double* D;
+        int ldd;
+    };
+    const Shape sh[2] = {{N, b, N, OZ_BIG, OZ_SB, h->Y, N}, {m, N, N, OZ_SA, OZ_BIG, h->Pn, m}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CTM_CUDA(cudaEventCreate(&e0));
+    CTM_CUDA(cudaEventCreate(&e1));
+    auto done = [&](ctm_status st) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    };
+    int n = 0;
+    for (const Shape& X : sh) {
+        void *pa, *pb;
+        int *ea, *eb;
+        oz_slot(h, X.sa, &pa, &ea);
+        oz_slot(h, X.sb, &pb, &eb);
+        double best_ms = 1e30, def_ms = 0.0;
+        int best = 0, best_sl = 1, timed = 0;
+        std::vector<int> seen;
+        for (int req = 0; req <= 6; ++req) {
+            const int sl = req == 0 ? -1 : ctm::oz_plan_slices(X.K, req);
+            if (req > 0 && sl > 1 && (size_t)sl * X.M * X.Nn > L.part_cap) continue;
+            if (req > 0 && std::find(seen.begin(), seen.end(), sl) != seen.end()) continue;
+            if (req > 0) seen.push_back(sl);
+            auto launch = [&]() {
+                return ctm::oz_gemm(h->st, S, X.M, X.Nn, X.K, pa, ea, pb, eb, X.D, X.ldd, h->tcerr, h->part,
+                                    L.part_cap, req);
+            };
+            cudaError_t ce = launch();
+            if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("tune: ") + cudaGetErrorString(ce)));
+            cudaEventRecord(e0, h->st);
+            for (int r = 0; r < reps; ++r) launch();
+            cudaEventRecord(e1, h->st);
+            ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) return done(fail(CTM_ECUDA, std::string("tune: ") + cudaGetErrorString(ce)));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = (double)ms / reps;
+            if (req == 0) def_ms = per;
+            if (per < best_ms) {
+                best_ms = per;
+                best = req;
+                best_sl = req == 0 ? 1 : sl;
+            }
+            ++timed;
+        }
+        {
+            std::lock_guard<std::mutex> g(g_tc_mu);
+            g_oz_plans[TcKey{S, X.M, X.Nn, X.K}] = best;
+        }
+        if (out && n < max_out) out[n] = ctm_tune_entry{X.M, X.Nn, X.K, 64, best_sl, def_ms, best_ms, timed};
+        ++n;
+    }
+    int err = 0;
+    CTM_CUDA(cudaMemcpyAsync(&err, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    if (n_out) *n_out = std::min(n, max_out);
+    if (err) return done(fail(CTM_ETIMEOUT, "a bounded wait of the Ozaki GEMM gave up while tuning"));
+    return done(CTM_OK);
+}
+}  // namespace
+extern "C" {
+
 ctm_status ctm_tune(ctm_handle* h, int reps, ctm_tune_entry* out, int max_out, int* n_out) {
     if (!h) return fail(CTM_EINVAL, "handle is NULL");
     if (n_out) *n_out = 0;
     const Layout& L = h->lay;
-    if (!L.esz) return CTM_OK;  // only the tensor-core GEMM of the TF32 / BF16 forms has launch shapes
     if (reps <= 0) reps = 5;
+    if (is_oz(h)) return tune_oz(h, reps, out, max_out, n_out);
+    if (!L.esz) return CTM_OK;  // the FP64 form has no tensor-core launch shapes
     const bool bf16 = L.esz == 2;
     struct Shape {
         int M, N, K;

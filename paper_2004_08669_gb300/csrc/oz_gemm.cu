@@ -551,15 +551,33 @@ void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, l
     k_oz_split<true><<<dim3((ld + 31) / 32, (R + 31) / 32), blk, 0, st>>>(R, K, s, src, rs, ks, scale,
                                                                           (__nv_bfloat16*)planes, Rp, ld, rexp);
 }
+int oz_plan_slices(int K, int splits_req) {
+    const int chunks = (K + kOzChunk - 1) / kOzChunk;
+    const int want = std::max(1, std::min(splits_req, chunks));
+    const int kper = ((chunks + want - 1) / want) * kOzChunk;
+    return (K + kper - 1) / kper;
+}
+
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
                     const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part,
-                    size_t part_cap) {
+                    size_t part_cap, int splits_req) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (s < 3 || s > 7) return cudaErrorInvalidValue;
-    // split-K when the output tiles alone cannot fill the GPU
+    // split-K when the output tiles alone cannot fill the GPU, or as requested
     const long tiles = (long)((M + kOzBM - 1) / kOzBM) * ((N + kOzBN - 1) / kOzBN);
     int splits = 1, kper = K;
-    if (part && tiles < 152 && K >= 2 * kOzChunk) {
+    if (splits_req > 0) {
+        const int chunks = (K + kOzChunk - 1) / kOzChunk;
+        const int want = std::max(1, std::min(splits_req, chunks));
+        kper = ((chunks + want - 1) / want) * kOzChunk;
+        splits = (K + kper - 1) / kper;
+        if (splits < 2) {
+            splits = 1;
+            kper = K;
+        } else if (!part || (size_t)splits * M * N > part_cap) {
+            return cudaErrorInvalidValue;
+        }
+    } else if (part && tiles < 152 && K >= 2 * kOzChunk) {
         const long chunks = (K + kOzChunk - 1) / kOzChunk;
         long want = std::min<long>((2 * 152 + tiles - 1) / tiles, chunks);
         want = std::min<long>(want, (long)(part_cap / ((size_t)M * N)));

@@ -23,9 +23,14 @@ void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, l
 // D (M x N, column-major FP64, ldd) = A . B^t from split operands (A: M rows,
 // B: N rows, length K, s digits, 3 <= s <= 7).  *err (device) set on timeout.
 // part (part_cap doubles, may be null): split-K partials, used when the
-// output tiles alone cannot fill the GPU.
+// output tiles alone cannot fill the GPU (splits_req = 0), or for the K
+// slices requested (splits_req >= 1; slices are whole 512-wide exact chunks,
+// cudaErrorInvalidValue if their partials do not fit part_cap).
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
                     const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part = nullptr,
-                    size_t part_cap = 0);
+                    size_t part_cap = 0, int splits_req = 0);
+
+// K slices oz_gemm launches for a requested split count (whole exact chunks).
+int oz_plan_slices(int K, int splits_req);
 
 }  // namespace ctm

@@ -104,6 +104,32 @@ def test_tuned_tf32_step_stays_within_operand_precision(ctm):
     assert df <= 1e-4
 
 
+def test_tuned_ozaki_form_tracks_fp64_form(ctm):
+    """ctm_tune on the FP64-emulating form picks K slices for C~ V and U^t X
+    (q = 20, m = 64: K = 1280, three exact 512-wide chunks); the tuned form
+    then follows the FP64 form step by step from the same checkpoint to the
+    same accuracy as untuned (|df|/|f| <= 1e-11 over 15 steps)."""
+    spins, beta, m = W.dodecahedron(), 1 / 0.4398, 64
+    g = ctm.CTMRG(spins, m, beta, prec="ozaki64", max_subspace_iters=4)
+    g.step(10)
+    blob = g.save()
+    ents = ctm.ctm_tune(g.h, 3)
+    g.close()
+    N, b = m * 20, m + max(8, m // 8)
+    assert {(e["M"], e["N"], e["K"]) for e in ents} == {(N, b, N), (m, N, N)}
+    for e in ents:
+        assert 1 <= e["splits"] <= 3 and e["ms_best"] <= e["ms_default"] * (1 + 1e-9)
+    fs = {}
+    for prec in ("ozaki64", "fp64"):
+        h = ctm.CTMRG(spins, m, beta, prec=prec, max_subspace_iters=4)
+        h.load(blob)
+        fs[prec] = [h.step(1)[1]["kappa"] for _ in range(15)]
+        h.close()
+    d = max(abs(a - c) / abs(c) for a, c in zip(fs["ozaki64"], fs["fp64"]))
+    print(f"\ntuned ozaki64 vs fp64 (kappa): {d:.2e}, slices {[e['splits'] for e in ents]}")
+    assert d <= 1e-11
+
+
 def _single(ctm, spins, m, beta, prec, steps, **kw):
     g = ctm.CTMRG(spins, m, beta, prec=prec, **kw)
     done, info = g.run(steps)
