@@ -260,14 +260,19 @@ struct ArDF {
     __device__ static T fin(Acc c) { return quick(c.h, c.l); }
 };
 
-template <class Ar>
+// One thread per row i and W consecutive columns j of a q x q block (W = 4,
+// 2 or 1 as q allows): each shared-memory read of G or T1 feeds W
+// accumulations, and the E entries it pairs with are broadcast across the
+// warp.  nb blocks per CTA, each with its own G and T1 in shared memory.
+template <class Ar, int W>
 __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, const double* __restrict__ E,
                                const double* __restrict__ E1, const int* __restrict__ live_ptr, bool sym) {
     using T = typename Ar::T;
     extern __shared__ __align__(16) unsigned char sh_raw[];
     T* sh = (T*)sh_raw;
     const int q2 = q * q;
-    const int nb = max(1, (int)blockDim.x / q2);
+    const int tpb = q * (q / W);  // threads per q x q block
+    const int nb = max(1, (int)blockDim.x / tpb);
     T* sE = sh;
     T* sE1 = sE + q2;
     T* G = sE1 + q2;
@@ -278,35 +283,58 @@ __global__ void k_wcontract_ar(int m, int q, double* __restrict__ X, int ldx, co
     }
     const int live = min(*live_ptr, m);
     const long nblk = sym ? (long)live * (live + 1) / 2 : (long)live * live;
-    const int jb = threadIdx.x / q2;
-    const int el = threadIdx.x - jb * q2;
+    const int jb = threadIdx.x / tpb;
+    const int el = threadIdx.x - jb * tpb;
     const bool act = jb < nb;
-    const int i = el % q, j = el / q;
+    const int i = el % q, j0 = (el / q) * W;
+    T* Gb = G + jb * q2;
+    T* Tb = T1 + jb * q2;
     __syncthreads();
     for (long base = (long)blockIdx.x * nb; base < nblk; base += (long)gridDim.x * nb) {
-        long blk = base + jb;
-        bool ok = act && blk < nblk;
+        const long blk = base + jb;
+        const bool ok = act && blk < nblk;
         size_t off = 0, offT = 0;
         int g = 0, gp = 0;
         if (ok) {
             wc_block(blk, live, sym, g, gp);
             off = (size_t)q * g + (size_t)ldx * ((size_t)q * gp);
             offT = (size_t)q * gp + (size_t)ldx * ((size_t)q * g);
-            G[jb * q2 + el] = Ar::mul(Ar::load(X[off + i + (size_t)ldx * j]), sE1[el]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int j = j0 + w;
+                Gb[i + q * j] = Ar::mul(Ar::load(X[off + i + (size_t)ldx * j]), sE1[i + q * j]);
+            }
         }
         __syncthreads();
         if (ok) {
-            typename Ar::Acc c = Ar::acc0();
-            for (int k = 0; k < q; ++k) Ar::acc(c, G[jb * q2 + i + q * k], sE[k + q * j]);
-            T1[jb * q2 + el] = Ar::fin(c);
+            typename Ar::Acc c[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[w] = Ar::acc0();
+            for (int k = 0; k < q; ++k) {
+                const T gk = Gb[i + q * k];
+#pragma unroll
+                for (int w = 0; w < W; ++w) Ar::acc(c[w], gk, sE[k + q * (j0 + w)]);
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) Tb[i + q * (j0 + w)] = Ar::fin(c[w]);
         }
         __syncthreads();
         if (ok) {
-            typename Ar::Acc c = Ar::acc0();
-            for (int k = 0; k < q; ++k) Ar::acc(c, sE[i + q * k], T1[jb * q2 + k + q * j]);
-            const double v = Ar::store(Ar::mul(sE[el], Ar::fin(c)));
-            X[off + i + (size_t)ldx * j] = v;
-            if (sym && g != gp) X[offT + j + (size_t)ldx * i] = v;
+            typename Ar::Acc c[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[w] = Ar::acc0();
+            for (int k = 0; k < q; ++k) {
+                const T ek = sE[i + q * k];
+#pragma unroll
+                for (int w = 0; w < W; ++w) Ar::acc(c[w], ek, Tb[k + q * (j0 + w)]);
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int j = j0 + w;
+                const double v = Ar::store(Ar::mul(sE[i + q * j], Ar::fin(c[w])));
+                X[off + i + (size_t)ldx * j] = v;
+                if (sym && g != gp) X[offT + j + (size_t)ldx * i] = v;
+            }
         }
         __syncthreads();
     }
@@ -320,20 +348,32 @@ void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, 
         wcontract_f64(st, m, q, X, ldx, E, E1, live, sym);
         return;
     }
-    int q2 = q * q;
-    int threads = q2 <= 256 ? 256 : ((q2 + 31) / 32) * 32;
-    int nb = threads / q2;
-    if (nb < 1) nb = 1;
+    const int q2 = q * q;
+    const int W = (q % 4 == 0) ? 4 : ((q % 2 == 0) ? 2 : 1);
+    const int tpb = q * (q / W);
+    int nb = tpb <= 256 ? 256 / tpb : 1;
+    const int threads = ((nb * tpb + 31) / 32) * 32;
     long nblk = (long)m * m;
     long grid = (nblk + nb - 1) / nb;
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
+    auto go = [&](auto ar, auto wt) {
+        using A = decltype(ar);
+        constexpr int WW = decltype(wt)::value;
+        const size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(typename A::T);
+        k_wcontract_ar<A, WW><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
+    };
+    using W1 = std::integral_constant<int, 1>;
+    using W2 = std::integral_constant<int, 2>;
+    using W4 = std::integral_constant<int, 4>;
     if (arith == 1) {
-        size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float);
-        k_wcontract_ar<ArF32><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
+        if (W == 4) go(ArF32{}, W4{});
+        else if (W == 2) go(ArF32{}, W2{});
+        else go(ArF32{}, W1{});
     } else {
-        size_t smem = (size_t)(2 * q2 + 2 * nb * q2) * sizeof(float2);
-        k_wcontract_ar<ArDF><<<(unsigned)grid, threads, smem, st>>>(m, q, X, ldx, E, E1, live, sym);
+        if (W == 4) go(ArDF{}, W4{});
+        else if (W == 2) go(ArDF{}, W2{});
+        else go(ArDF{}, W1{});
     }
 }
 
