@@ -607,7 +607,7 @@ void oz_slot(ctm_handle* h, OzSlot sl, void** planes, int** e) {
 // FP64-emulating contraction on the tensor cores: split A and B (unless the
 // slot already holds that operand) and multiply the digit planes.
 ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool splitA, Opnd B, OzSlot sb, bool splitB,
-                double* D, int ldd) {
+                double* D, int ldd, int lowq = 0) {
     const int S = h->lay.slices;
     void *pa, *pb;
     int *ea, *eb;
@@ -628,11 +628,14 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
     }
     cudaEvent_t a = prof_begin(h);
     const int req = oz_plan_for(S, M, N, K);
-    cudaError_t e = ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr, h->part, h->lay.part_cap, req);
+    cudaError_t e =
+        ctm::oz_gemm(h->st, S, M, N, K, pa, ea, pb, eb, D, ldd, h->tcerr, h->part, h->lay.part_cap, req, lowq);
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("oz_gemm: ") + cudaGetErrorString(e));
     const double pairs = S * (S + 1) / 2.0;
-    prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * M * (double)N * K,
-             2.0 * S * ((double)M * K + (double)N * K) + 8.0 * (double)M * N);
+    // outputs computed: all of D, or its q x q blocks on and below the block diagonal
+    const double nb = lowq > 0 ? (double)(M / lowq) : 0.0;
+    const double outs = lowq > 0 ? nb * (nb + 1) / 2.0 * lowq * lowq : (double)M * N;
+    prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * outs * K, 2.0 * S * ((double)M * K + (double)N * K) + 8.0 * outs);
     return CTM_OK;
 }
 
@@ -678,8 +681,10 @@ int gemm_splits(const Layout& L, int M, int Nn, int K) {
 void stage_extend(ctm_handle* h, const double* E1) {
     const Layout& L = h->lay;
     if (is_oz(h)) {
+        // with the plain weight the contraction below reads only the blocks
+        // on and below the block diagonal of the symmetric X1
         ozmm(h, L.N, L.N, L.m, {h->P, L.m, 1, nullptr}, OZ_P, true, {h->P, L.m, 1, h->omega}, OZ_SB, true, h->C,
-             L.N);
+             L.N, E1 == h->E ? L.q : 0);
     } else if (L.esz) {
         // X1 = P^t diag(omega) P on the tensor cores: operand rows are the
         // columns of P (K = m), the second one scaled by omega along K.

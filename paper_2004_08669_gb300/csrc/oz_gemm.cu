@@ -293,7 +293,7 @@ template <int S>
 __global__ void __launch_bounds__(320, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
               int Mp, int Np, const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ D, int ldd,
-              int kper, double* __restrict__ part, int* err) {
+              int kper, double* __restrict__ part, int* err, int lowq) {
     constexpr int kOzStages = OzStages<S>::value;
     constexpr int NG = S;                           // groups t = 2 .. S + 1
     constexpr uint32_t A_PLANE = kOzBM * kOzKT * 2;  // 8 KB
@@ -309,6 +309,10 @@ __global__ void __launch_bounds__(320, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kOzBM, n0 = blockIdx.y * kOzBN;
+    // lower q x q block triangle only: a tile whose block rows all lie above
+    // its first block column has nothing to compute (uniform exit, before
+    // any barrier or tensor-memory allocation)
+    if (lowq > 0 && (min(m0 + kOzBM, M) - 1) / lowq < n0 / lowq) return;
     // split-K: this CTA's K range (kper is a multiple of the exact chunk)
     const int kbeg = blockIdx.z * kper;
     const int nk = (min(K, kbeg + kper) - kbeg + kOzKT - 1) / kOzKT;
@@ -494,7 +498,7 @@ __global__ void k_oz_reduce(int M, int N, int splits, const double* __restrict__
 template <int S>
 cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int Mp, int Np,
                       const int* eA, const int* eB, double* D, int ldd, int kper, int splits, double* part,
-                      int* err) {
+                      int* err, int lowq) {
     const size_t smem = 1024 + (size_t)OzStages<S>::value * S * (kOzBM * kOzKT * 2 + kOzBN * kOzKT * 2);
     static const bool attr = [&]() {
         cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -502,7 +506,7 @@ cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
     }();
     (void)attr;
     dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN, splits);
-    k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err);
+    k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err, lowq);
     if (splits > 1) {
         const size_t total = (size_t)M * N;
         const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
@@ -560,7 +564,7 @@ int oz_plan_slices(int K, int splits_req) {
 
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
                     const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part,
-                    size_t part_cap, int splits_req) {
+                    size_t part_cap, int splits_req, int lowq) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (s < 3 || s > 7) return cudaErrorInvalidValue;
     // split-K when the output tiles alone cannot fill the GPU, or as requested
@@ -594,12 +598,13 @@ cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Apl
     CUtensorMap ma, mb;
     if (!oz_map(&ma, Aplanes, K, s * Mp, ld, kOzBM) || !oz_map(&mb, Bplanes, K, s * Np, ld, kOzBN))
         return cudaErrorInvalidValue;
+    const int lq = splits > 1 ? 0 : lowq;  // partial tiles must all be written
     switch (s) {
-        case 3: return oz_launch<3>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
-        case 4: return oz_launch<4>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
-        case 5: return oz_launch<5>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
-        case 6: return oz_launch<6>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
-        default: return oz_launch<7>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err);
+        case 3: return oz_launch<3>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lq);
+        case 4: return oz_launch<4>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lq);
+        case 5: return oz_launch<5>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lq);
+        case 6: return oz_launch<6>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lq);
+        default: return oz_launch<7>(st, ma, mb, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lq);
     }
 }
 

@@ -25,10 +25,12 @@ void oz_split_strided(cudaStream_t st, int R, int K, int s, const double* src, l
 // part (part_cap doubles, may be null): split-K partials, used when the
 // output tiles alone cannot fill the GPU (splits_req = 0), or for the K
 // slices requested (splits_req >= 1; slices are whole 512-wide exact chunks,
-// cudaErrorInvalidValue if their partials do not fit part_cap).
+// cudaErrorInvalidValue if their partials do not fit part_cap).  lowq > 0
+// (no split-K): only the q x q blocks on or below the block diagonal of D
+// are needed; output tiles entirely above it are skipped (left unwritten).
 cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Aplanes, const int* eA,
                     const void* Bplanes, const int* eB, double* D, int ldd, int* err, double* part = nullptr,
-                    size_t part_cap = 0, int splits_req = 0);
+                    size_t part_cap = 0, int splits_req = 0, int lowq = 0);
 
 // K slices oz_gemm launches for a requested split count (whole exact chunks).
 int oz_plan_slices(int K, int splits_req);
