@@ -293,7 +293,7 @@ template <int S>
 __global__ void __launch_bounds__(320, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
               int Mp, int Np, const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ D, int ldd,
-              int kper, double* __restrict__ part, int* err, int lowq) {
+              int kper, int splits, double* __restrict__ part, int* err, int lowq) {
     constexpr int kOzStages = OzStages<S>::value;
     constexpr int NG = S;                           // groups t = 2 .. S + 1
     constexpr uint32_t A_PLANE = kOzBM * kOzKT * 2;  // 8 KB
@@ -308,16 +308,26 @@ __global__ void __launch_bounds__(320, 1)
     __shared__ uint32_t tmem_slot;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kOzBM, n0 = blockIdx.y * kOzBN;
-    // lower q x q block triangle only: a tile whose block rows all lie above
-    // its first block column has nothing to compute (uniform exit, before
-    // any barrier or tensor-memory allocation)
-    if (lowq > 0 && (min(m0 + kOzBM, M) - 1) / lowq < n0 / lowq) return;
-    // split-K: this CTA's K range (kper is a multiple of the exact chunk)
-    const int kbeg = blockIdx.z * kper;
-    const int nk = (min(K, kbeg + kper) - kbeg + kOzKT - 1) / kOzKT;
+    // Persistent: this CTA takes tiles blockIdx.x, + gridDim.x, ... of the
+    // (row tile, column tile, K slice) space; the stage ring and the
+    // accumulator hand-over keep their phases across tiles, so the producer
+    // loads the next tile's stages and the MMA warp starts the next tile while
+    // the epilogue warps convert and store the previous one.
+    const int tm = (M + kOzBM - 1) / kOzBM, tn = (N + kOzBN - 1) / kOzBN;
+    const long ntile = (long)tm * tn * splits;
     const int kt_per_chunk = kOzChunk / kOzKT;
-    const int nchunk = (nk + kt_per_chunk - 1) / kt_per_chunk;
+    // tile t: its origin, K range, and whether it has work (lower q x q block
+    // triangle only when lowq > 0: a tile whose block rows all lie above its
+    // first block column is skipped)
+    auto tile_of = [&](long t, int& m0, int& n0, int& kbeg, int& nk) -> bool {
+        const int z = (int)(t / ((long)tm * tn));
+        const long xy = t - (long)z * tm * tn;
+        m0 = (int)(xy % tm) * kOzBM;
+        n0 = (int)(xy / tm) * kOzBN;
+        kbeg = z * kper;
+        nk = (min(K, kbeg + kper) - kbeg + kOzKT - 1) / kOzKT;
+        return !(lowq > 0 && (min(m0 + kOzBM, M) - 1) / lowq < n0 / lowq);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOzStages; ++s) {
@@ -343,23 +353,31 @@ __global__ void __launch_bounds__(320, 1)
     if (warp == 8) {
         // ---- producer: all digit planes of one K-tile per stage
         if (lane == 0) {
-            int issued = 0;
-            for (int kt = 0; kt < nk; ++kt) {
-                int st = kt % kOzStages;
-                if (kt >= kOzStages && !mbar_wait(&empty_bar[st], ((kt / kOzStages) - 1) & 1, err)) break;
-                uint8_t* base = smem + st * STAGE;
-                mbar_expect_tx(&full_bar[st], STAGE);
+            long issued = 0;  // K-tiles issued by this CTA over all its tiles
+            bool ok = true;
+            for (long t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+                int m0, n0, kbeg, nk;
+                if (!tile_of(t, m0, n0, kbeg, nk)) continue;
+                for (int kt = 0; kt < nk; ++kt, ++issued) {
+                    const int st = (int)(issued % kOzStages);
+                    if (issued >= kOzStages &&
+                        !mbar_wait(&empty_bar[st], (uint32_t)(((issued / kOzStages) - 1) & 1), err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* base = smem + st * STAGE;
+                    mbar_expect_tx(&full_bar[st], STAGE);
 #pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    tma_load_2d(base + i * A_PLANE, &mapA, &full_bar[st], kbeg + kt * kOzKT, i * Mp + m0);
-                    tma_load_2d(base + S * A_PLANE + i * B_PLANE, &mapB, &full_bar[st], kbeg + kt * kOzKT,
-                                i * Np + n0);
+                    for (int i = 0; i < S; ++i) {
+                        tma_load_2d(base + i * A_PLANE, &mapA, &full_bar[st], kbeg + kt * kOzKT, i * Mp + m0);
+                        tma_load_2d(base + S * A_PLANE + i * B_PLANE, &mapB, &full_bar[st], kbeg + kt * kOzKT,
+                                    i * Np + n0);
+                    }
                 }
-                ++issued;
             }
             // own copies must land before the CTA may exit
-            for (int kt = (issued > kOzStages ? issued - kOzStages : 0); kt < issued; ++kt)
-                mbar_wait(&full_bar[kt % kOzStages], (kt / kOzStages) & 1, err);
+            for (long kt = (issued > kOzStages ? issued - kOzStages : 0); kt < issued; ++kt)
+                mbar_wait(&full_bar[kt % kOzStages], (uint32_t)((kt / kOzStages) & 1), err);
         }
     } else if (warp == 9) {
         // ---- MMA issuer
@@ -367,86 +385,102 @@ __global__ void __launch_bounds__(320, 1)
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
                                    ((uint32_t)(kOzBM >> 4) << 24);
             bool ok = true;
-            for (int c = 0; c < nchunk && ok; ++c) {
-                if (c > 0 && !mbar_wait(&acc_empty, (c - 1) & 1, err)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int kt0 = c * kt_per_chunk, kt1 = min(nk, kt0 + kt_per_chunk);
-                for (int kt = kt0; kt < kt1; ++kt) {
-                    int st = kt % kOzStages;
-                    if (!mbar_wait(&full_bar[st], (kt / kOzStages) & 1, err)) {
+            long used = 0;    // K-tiles consumed over all tiles
+            long chunks = 0;  // accumulator hand-overs over all tiles
+            for (long t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+                int m0, n0, kbeg, nk;
+                if (!tile_of(t, m0, n0, kbeg, nk)) continue;
+                const int nchunk = (nk + kt_per_chunk - 1) / kt_per_chunk;
+                for (int c = 0; c < nchunk && ok; ++c, ++chunks) {
+                    // the epilogue must have drained the previous hand-over
+                    if (chunks > 0 && !mbar_wait(&acc_empty, (uint32_t)((chunks - 1) & 1), err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t base = smem_u32(smem + st * STAGE);
+                    const int kt0 = c * kt_per_chunk, kt1 = min(nk, kt0 + kt_per_chunk);
+                    for (int kt = kt0; kt < kt1; ++kt, ++used) {
+                        const int st = (int)(used % kOzStages);
+                        if (!mbar_wait(&full_bar[st], (uint32_t)((used / kOzStages) & 1), err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t base = smem_u32(smem + st * STAGE);
 #pragma unroll
-                    for (int i = 0; i < S; ++i) {
+                        for (int i = 0; i < S; ++i) {
 #pragma unroll
-                        for (int j = 0; j < S; ++j) {
-                            if (i + j > S - 1) continue;  // keep i + j <= s + 1 (1-based)
-                            const int g = i + j;          // group index 0 .. S - 1
-                            const uint32_t a0 = base + i * A_PLANE;
-                            const uint32_t b0 = base + S * A_PLANE + j * B_PLANE;
+                            for (int j = 0; j < S; ++j) {
+                                if (i + j > S - 1) continue;  // keep i + j <= s + 1 (1-based)
+                                const int g = i + j;          // group index 0 .. S - 1
+                                const uint32_t a0 = base + i * A_PLANE;
+                                const uint32_t b0 = base + S * A_PLANE + j * B_PLANE;
 #pragma unroll
-                            for (int kk = 0; kk < kOzKT / 16; ++kk) {
-                                // the first MMA of a group in this chunk overwrites its accumulator
-                                const bool first = (kt == kt0) && (kk == 0) &&
-                                                   (i == (g < S ? 0 : g - (S - 1)));
-                                mma_bf16(tmem + (uint32_t)(g * kOzBN), sdesc64(a0 + 32 * kk), sdesc64(b0 + 32 * kk),
-                                         idesc, first ? 0u : 1u);
+                                for (int kk = 0; kk < kOzKT / 16; ++kk) {
+                                    // the first MMA of a group in this chunk overwrites its accumulator
+                                    const bool first = (kt == kt0) && (kk == 0) &&
+                                                       (i == (g < S ? 0 : g - (S - 1)));
+                                    mma_bf16(tmem + (uint32_t)(g * kOzBN), sdesc64(a0 + 32 * kk),
+                                             sdesc64(b0 + 32 * kk), idesc, first ? 0u : 1u);
+                                }
                             }
                         }
+                        mma_commit(&empty_bar[st]);
                     }
-                    mma_commit(&empty_bar[st]);
+                    mma_commit(&acc_full);
                 }
-                mma_commit(&acc_full);
             }
             if (!ok) mma_commit(&acc_full);
         }
     } else {
         // ---- epilogue warps 0..7: warp w reads TMEM lanes 32 (w % 4) .. + 31
         // (tile rows) and columns 32 (w / 4) .. + 31, so that each thread holds
-        // 32 double-float accumulators
+        // 32 double-float accumulators of its tile
         const int quad = warp & 3, half = warp >> 2;
         constexpr int EC = kOzBN / 2;
-        float hi[EC], lo[EC];
-#pragma unroll
-        for (int j = 0; j < EC; ++j) {
-            hi[j] = 0.f;
-            lo[j] = 0.f;
-        }
         bool ok = true;
-        for (int c = 0; c < nchunk; ++c) {
-            if (!mbar_wait(&acc_full, c & 1, err)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int g = 0; g < NG; ++g) {
-                const float sc = exp2f(-7.0f * (float)(g + 2));
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * kOzBN + half * EC), v);
-#pragma unroll
-                for (int j = 0; j < EC; ++j) df_add(hi[j], lo[j], v[j] * sc);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&acc_empty);
-        }
-        const int row = m0 + quad * 32 + lane;
-        if (ok && row < M) {
-            const int er = oz_e(eA[row]);
-            // split-K partials go to part + z M N (column-major, ld M)
-            double* out = (gridDim.z > 1) ? part + (size_t)blockIdx.z * M * N : D;
-            const size_t ldo = (gridDim.z > 1) ? (size_t)M : (size_t)ldd;
+        long chunks = 0;
+        for (long t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            int m0, n0, kbeg, nk;
+            if (!tile_of(t, m0, n0, kbeg, nk)) continue;
+            const int nchunk = (nk + kt_per_chunk - 1) / kt_per_chunk;
+            float hi[EC], lo[EC];
 #pragma unroll
             for (int j = 0; j < EC; ++j) {
-                const int col = n0 + half * EC + j;
-                if (col < N)
-                    out[row + ldo * col] = scale_pow2(f2d_bits(hi[j]) + f2d_bits(lo[j]), er + oz_e(eB[col]));
+                hi[j] = 0.f;
+                lo[j] = 0.f;
+            }
+            for (int c = 0; c < nchunk; ++c, ++chunks) {
+                if (!mbar_wait(&acc_full, (uint32_t)(chunks & 1), err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                for (int g = 0; g < NG; ++g) {
+                    const float sc = exp2f(-7.0f * (float)(g + 2));
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * kOzBN + half * EC), v);
+#pragma unroll
+                    for (int j = 0; j < EC; ++j) df_add(hi[j], lo[j], v[j] * sc);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&acc_empty);
+            }
+            // the accumulators are free: this store overlaps the next tile's MMA
+            const int row = m0 + quad * 32 + lane;
+            if (ok && row < M) {
+                const int er = oz_e(eA[row]);
+                // split-K partials go to part + z M N (column-major, ld M)
+                const int z = kbeg / kper;
+                double* out = (splits > 1) ? part + (size_t)z * M * N : D;
+                const size_t ldo = (splits > 1) ? (size_t)M : (size_t)ldd;
+#pragma unroll
+                for (int j = 0; j < EC; ++j) {
+                    const int col = n0 + half * EC + j;
+                    if (col < N)
+                        out[row + ldo * col] = scale_pow2(f2d_bits(hi[j]) + f2d_bits(lo[j]), er + oz_e(eB[col]));
+                }
             }
         }
     }
@@ -459,15 +493,16 @@ __global__ void __launch_bounds__(320, 1)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // resolved once (thread-safe initialisation of a local static)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -505,8 +540,13 @@ cudaError_t oz_launch(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
         return true;
     }();
     (void)attr;
-    dim3 grid((M + kOzBM - 1) / kOzBM, (N + kOzBN - 1) / kOzBN, splits);
-    k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, part, err, lowq);
+    // persistent: one CTA per SM (the kernel holds all 512 tensor-memory
+    // columns), each looping over tiles
+    const long tiles = (long)((M + kOzBM - 1) / kOzBM) * ((N + kOzBN - 1) / kOzBN) * splits;
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::max<long>(1, std::min<long>(tiles, sms));
+    k_oz_gemm<S><<<grid, 320, smem, st>>>(a, b, M, N, K, Mp, Np, eA, eB, D, ldd, kper, splits, part, err, lowq);
     if (splits > 1) {
         const size_t total = (size_t)M * N;
         const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
