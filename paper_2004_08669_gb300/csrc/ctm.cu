@@ -2,15 +2,21 @@
 //
 // One handle = one temperature of Algorithm 3 (Symmetric-CTMRG) of
 // arXiv:2004.08669 on one GPU.  A step is
-//   a2  extension   C~ = Sub-CTMRG(P, Omega P, W)      (gemm_f64 + wcontract_f64)
+//   a2  extension   C~ = Sub-CTMRG(P, Omega P, W)      (GEMM of the form + W contraction)
 //   a3  eigenpairs  leading b Ritz pairs of C~           (subspace iteration,
-//                   FP64 Jacobi Rayleigh-Ritz, CholQR2, multiplet-aware cut,
+//                   Jacobi Rayleigh-Ritz, CholQR2, multiplet-aware cut,
 //                   gauge alignment to the previous step)
-//   a4  renormalise P <- U^t Sub-CTMRG(P, U', W)          (gemm_f64 + wcontract_f64)
+//   a4  renormalise P <- U^t Sub-CTMRG(P, U', W)          (GEMMs + W contraction)
 //   a5  normalise   P <- P / ||P||_F, Omega <- Omega / (sum w^4)^{1/4}
 //   a6  S_E (Eq. 6) and the convergence measure delta on the device.
+// The GEMMs run on the FP64 cores (CTM_FP64), on tcgen05 in TF32 / BF16, or
+// as FP64 emulated by bf16 digit slices on tcgen05 (CTM_OZAKI64); the small
+// solves are FP64 (CTM_FP64) or double-float on the FP32 pipe (the others).
 // The host only sequences launches and reads back one small control block per
-// subspace iteration.
+// subspace iteration.  Also here: the autotuner of the tensor-core GEMMs, the
+// temperature scan (ctm_scan_*, one handle per beta, a native worker pool)
+// and the effective correlation length (ctm_xi, Lanczos on the row-to-row
+// transfer matrix).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>

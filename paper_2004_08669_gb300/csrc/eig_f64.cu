@@ -110,6 +110,7 @@ __device__ __forceinline__ Rot rot_fast(double app, double aqq, double apq, doub
 // carry errors of the same order.
 struct J64 {
     using T = double;
+    static constexpr int kMinBlocks = 3;  // blocks per SM of the one-round-per-barrier solver
     struct R {
         T c, s;
         bool on;
@@ -135,6 +136,7 @@ struct J64 {
 
 struct JDF {
     using T = float2;  // x = hi, y = lo
+    static constexpr int kMinBlocks = 4;  // blocks per SM of the one-round-per-barrier solver
     struct R {
         T c, s;
         bool on;
@@ -554,8 +556,8 @@ __device__ __forceinline__ void jac_fused(int r, int s2, int nh, int npad, int h
 // issued before the rotations so that both memory round trips overlap.  A is
 // double-buffered (read from one buffer, written in full to the other); S is
 // updated in place (the round's column pairs are disjoint).
-template <class JA>
-__global__ void __launch_bounds__(256, 2) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
+template <class JA, bool FUSE>
+__global__ void __launch_bounds__(256, FUSE ? 2 : JA::kMinBlocks) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
                                                 typename JA::T* S, typename JA::T* S1, double* __restrict__ diag,
                                                 int* act, int max_sweeps, double eps, double floor_rel,
                                                 DevCtl* ctl) {
@@ -655,7 +657,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi(int n, int npad, typename JA:
             // reads columns that other units write), else updated in place
             const T* Sc = (S1 && (rt & 1)) ? S1 : S;
             T* Sn = S1 ? ((rt & 1) ? S : S1) : S;
-            const bool fuse = S1 != nullptr && r + 2 <= s2 - 1;
+            const bool fuse = FUSE && S1 != nullptr && r + 2 <= s2 - 1;
             if (fuse) {
                 jac_fused<JA>(r, s2, nh, npad, half, nT, nA, nRC, nU, perm, inv, Ac, An, Sc, Sn, eps, floor_abs,
                               my_rot, f_al, f_be, f_c, f_s, f_on, f_ap);
@@ -1439,28 +1441,41 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
     int grid = (int)nU;
     const size_t smem = 3 * (size_t)npad * sizeof(int);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    // two instantiations: two rounds per barrier (more registers, two blocks
+    // per SM) and one round per barrier (fewer registers, more blocks)
+    const void* fF = (const void*)k_jacobi<JA, true>;
+    const void* fS = (const void*)k_jacobi<JA, false>;
     static std::mutex mu;  // host threads may drive handles concurrently
-    static int limit = 0;
+    static int limF = 0, limS = 0;
     static size_t limit_smem = 0;
-    int lim;
+    int lf, ls;
     {
         std::lock_guard<std::mutex> g(mu);
-        if (limit == 0 || smem > limit_smem) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_jacobi<JA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            limit = coop_grid_limit((const void*)k_jacobi<JA>, 256, smem);
+        if (limF == 0 || smem > limit_smem) {
+            if (smem > 48 * 1024) {
+                cudaFuncSetAttribute(fF, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaFuncSetAttribute(fS, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            }
+            limF = coop_grid_limit(fF, 256, smem);
+            limS = coop_grid_limit(fS, 256, smem);
             limit_smem = smem;
         }
-        lim = limit;
+        lf = limF;
+        ls = limS;
     }
-    if (grid > lim) grid = lim;
+    // two rounds per barrier only when every unit has its own block (and a
+    // second S buffer exists): with several units per block (large n) the
+    // recomputed rotations and the extra reads make a fused round cost more
+    // than two single ones
+    const bool fused = w.S1 != nullptr && nU <= lf;
+    if (grid > (fused ? lf : ls)) grid = fused ? lf : ls;
     if (grid < 1) grid = 1;
     double fl = floor_rel > 0.0 ? floor_rel : 0.0;
     double* diag = w.diag;
     int* act = w.rank;  // the sweep tags; rank is rewritten by the sort below
-    T* S1 = (T*)w.S1;  // NULL: one round per barrier, S in place
+    T* S1 = fused ? (T*)w.S1 : nullptr;  // NULL: one round per barrier, S in place
     void* args[] = {&n, &npad, &A0, &A1, &S, &S1, &diag, &act, &max_sweeps, &eps, &fl, &ctl};
-    cudaError_t e = launch_coop((const void*)k_jacobi<JA>, grid, 256, args, smem, st);
+    cudaError_t e = launch_coop(fused ? fF : fS, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);
     k_gather_ritz<JA><<<grid_for((size_t)n * n), 256, 0, st>>>(n, npad, w.rank, S, Sout, ldo);
