@@ -59,3 +59,46 @@ def test_binding_loads_and_validates_without_gpu(built_lib):
     with pytest.raises(ctm.CtmError):
         ctm.ctm_workspace_size(nan_b)
     del keep, keep2, keep3, keep4, keep5, keep6, np
+
+
+def test_host_side_validation_of_the_newer_entry_points(built_lib):
+    """The autotuner table, the scan and the correlation length validate
+    their arguments on the host, before any CUDA call."""
+    from paper_2004_08669_gb300 import ctm, workloads as W
+    with pytest.raises(ctm.CtmError) as e:
+        ctm.ctm_tc_plan_set("tf32", 64, 64, 64, 96, 1)
+    assert e.value.status == ctm.CTM_EINVAL
+    with pytest.raises(ctm.CtmError):
+        ctm.ctm_tc_plan_set("fp64", 64, 64, 64, 64, 1)
+    with pytest.raises(ctm.CtmError):
+        ctm.ctm_tc_plan_set("bf16", 64, 64, 64, 128, 17)
+    # a pinned shape is read back as the slices it launches (K = 384: six
+    # 64-wide K-tiles, three slices of two; K = 200: four tiles, so a request
+    # for three gives two slices of two, none empty); clearing restores the
+    # default (no split)
+    ctm.ctm_tc_plan_set("bf16", 96, 80, 384, 64, 3)
+    assert ctm.ctm_tc_plan_get("bf16", 96, 80, 384) == (64, 3)
+    ctm.ctm_tc_plan_set("bf16", 96, 80, 200, 64, 3)
+    assert ctm.ctm_tc_plan_get("bf16", 96, 80, 200) == (64, 2)
+    for K in (384, 200):
+        ctm.ctm_tc_plan_set("bf16", 96, 80, K, 0, 0)
+        assert ctm.ctm_tc_plan_get("bf16", 96, 80, K)[1] == 1
+    cfg, keep = ctm.make_config(W.dodecahedron(), 8, 0.0, prec="tf32")
+    one = ctm.ctm_workspace_size(cfg)
+    assert ctm.ctm_scan_workspace_size(cfg, 5) >= 5 * one
+    with pytest.raises(ctm.CtmError) as e:
+        ctm.ctm_scan_init(cfg, [], 2)
+    assert e.value.status == ctm.CTM_EINVAL
+    with pytest.raises(ctm.CtmError):
+        ctm.ctm_scan_init(cfg, [2.0, float("inf")], 2)
+    with pytest.raises(ctm.CtmError):
+        ctm.ctm_scan_init(cfg, [2.0], 65)
+    cfg.workspace = 1 << 40  # never touched: the size check fails first
+    cfg.workspace_bytes = 64
+    with pytest.raises(ctm.CtmError) as e:
+        ctm.ctm_scan_init(cfg, [2.0, 2.5], 2)
+    assert e.value.status == ctm.CTM_ENOMEM
+    assert ctm.lib.ctm_xi(None, 0, 0.0, None) == ctm.CTM_EINVAL
+    assert ctm.lib.ctm_tune(None, 0, None, 0, None) == ctm.CTM_EINVAL
+    assert ctm.lib.ctm_scan_run(None, 1, None, None) == ctm.CTM_EINVAL
+    del keep
