@@ -27,6 +27,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <string>
 #include <vector>
@@ -1956,7 +1957,8 @@ ctm_status ctm_scan_init(ctm_scan** out, const ctm_config* base, int nbeta, cons
     const size_t per = align256(one);
     if (base->workspace && base->workspace_bytes < per * (size_t)nbeta)
         return fail(CTM_ENOMEM, "workspace smaller than ctm_scan_workspace_size");
-    ctm_scan* sc = new ctm_scan();
+    ctm_scan* sc = new (std::nothrow) ctm_scan();
+    if (!sc) return fail(CTM_ENOMEM, "host allocation of the scan failed");
     sc->caller = (cudaStream_t)cuda_stream;
     sc->workers = std::min(workers, nbeta);
     sc->betas.assign(betas, betas + nbeta);
@@ -2032,8 +2034,15 @@ ctm_status ctm_scan_run(ctm_scan* sc, int max_steps, int* steps_done, int* conve
             if (stat[i] != CTM_OK) msg[i] = g_err;
         }
     };
+    // a thread that cannot be created leaves its share to the others
     std::vector<std::thread> pool;
-    for (int w = 1; w < sc->workers; ++w) pool.emplace_back(worker, w);
+    for (int w = 1; w < sc->workers; ++w) {
+        try {
+            pool.emplace_back(worker, w);
+        } catch (...) {
+            break;
+        }
+    }
     worker(0);
     for (auto& t : pool) t.join();
     cudaSetDevice(caller_dev);
@@ -2072,8 +2081,15 @@ ctm_status ctm_scan_observables(ctm_scan* sc, ctm_obs* out) {
             if (stat[i] != CTM_OK) msg[i] = g_err;
         }
     };
+    // a thread that cannot be created leaves its share to the others
     std::vector<std::thread> pool;
-    for (int w = 1; w < sc->workers; ++w) pool.emplace_back(worker, w);
+    for (int w = 1; w < sc->workers; ++w) {
+        try {
+            pool.emplace_back(worker, w);
+        } catch (...) {
+            break;
+        }
+    }
     worker(0);
     for (auto& t : pool) t.join();
     cudaSetDevice(caller_dev);
