@@ -530,12 +530,22 @@ void count_small(ctm_handle* h, int nk) {
 }
 
 // Profiled FP64 GEMM with its algorithmic FLOPs and minimum bytes.
+// Outputs of an M x N product: all of them, or (lowq > 0) the q x q blocks
+// on and below the block diagonal.
+double outputs_of(int M, int N, int lowq) {
+    if (lowq <= 0) return (double)M * N;
+    const double nb = (double)(M / lowq);
+    return nb * (nb + 1) / 2.0 * lowq * lowq;
+}
+
 void pgemm(ctm_handle* h, bool tA, bool tB, int M, int N, int K, const double* A, int lda, const double* B,
-           int ldb, double* C, int ldc, const double* scaleK = nullptr, int splits = 1) {
+           int ldb, double* C, int ldc, const double* scaleK = nullptr, int splits = 1, int lowq = 0) {
     cudaEvent_t a = prof_begin(h);
-    int nk = ctm::gemm_f64(h->st, tA, tB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, scaleK, splits, h->part);
-    double fl = 2.0 * M * (double)N * K;
-    double by = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
+    int nk = ctm::gemm_f64(h->st, tA, tB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, scaleK, splits, h->part,
+                           lowq);
+    const double outs = outputs_of(M, N, splits > 1 ? 0 : lowq);
+    double fl = 2.0 * outs * K;
+    double by = 8.0 * ((double)M * K + (double)K * N + outs);
     prof_end(h, a, PC_GEMM, nk, fl, by);
 }
 
@@ -581,14 +591,15 @@ ctm::TcPlan tc_plan_for(int esz, int M, int N, int K) {
 
 // Profiled tensor-core GEMM D = A B^t (operands already converted).
 ctm_status ptc(ctm_handle* h, int M, int N, int K, const void* A, int lda, const void* B, int ldb, double* D,
-               int ldd) {
+               int ldd, int lowq = 0) {
     cudaEvent_t a = prof_begin(h);
     const ctm::TcPlan plan = tc_plan_for(h->lay.esz, M, N, K);
     cudaError_t e = ctm::tc_gemm(h->st, h->lay.esz == 2, M, N, K, 1.0, A, lda, B, ldb, 0.0, D, ldd, h->tcerr, &plan,
-                                 h->tcpart, h->lay.tcpart_cap);
+                                 h->tcpart, h->lay.tcpart_cap, lowq);
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("tc_gemm: ") + cudaGetErrorString(e));
-    double fl = 2.0 * M * (double)N * K;
-    double by = (double)h->lay.esz * ((double)M * K + (double)K * N) + 8.0 * (double)M * N;
+    const double outs = outputs_of(M, N, ctm::tc_plan_slices(plan, K, h->lay.esz == 2, nullptr) > 1 ? 0 : lowq);
+    double fl = 2.0 * outs * K;
+    double by = (double)h->lay.esz * ((double)M * K + (double)K * N) + 8.0 * outs;
     prof_end(h, a, PC_TCGEMM, ctm::tc_plan_slices(plan, K, h->lay.esz == 2, nullptr) > 1 ? 2 : 1, fl, by);
     return CTM_OK;
 }
@@ -640,8 +651,7 @@ ctm_status ozmm(ctm_handle* h, int M, int N, int K, Opnd A, OzSlot sa, bool spli
     if (e != cudaSuccess) return fail(CTM_ECUDA, std::string("oz_gemm: ") + cudaGetErrorString(e));
     const double pairs = S * (S + 1) / 2.0;
     // outputs computed: all of D, or its q x q blocks on and below the block diagonal
-    const double nb = lowq > 0 ? (double)(M / lowq) : 0.0;
-    const double outs = lowq > 0 ? nb * (nb + 1) / 2.0 * lowq * lowq : (double)M * N;
+    const double outs = outputs_of(M, N, lowq);
     prof_end(h, a, PC_OZGEMM, 1, pairs * 2.0 * outs * K, 2.0 * S * ((double)M * K + (double)N * K) + 8.0 * outs);
     return CTM_OK;
 }
@@ -697,9 +707,9 @@ void stage_extend(ctm_handle* h, const double* E1) {
         // columns of P (K = m), the second one scaled by omega along K.
         pconvert(h, L.N, L.m, h->P, L.m, nullptr, h->opP, L.ldm);
         pconvert(h, L.N, L.m, h->P, L.m, h->omega, h->opPw, L.ldm);
-        ptc(h, L.N, L.N, L.m, h->opP, L.ldm, h->opPw, L.ldm, h->C, L.N);
+        ptc(h, L.N, L.N, L.m, h->opP, L.ldm, h->opPw, L.ldm, h->C, L.N, E1 == h->E ? L.q : 0);
     } else {
-        pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega);
+        pgemm(h, true, false, L.N, L.N, L.m, h->P, L.m, h->P, L.m, h->C, L.N, h->omega, 1, E1 == h->E ? L.q : 0);
     }
     pwcontract(h, h->C, E1, &h->ctl->live, h->live, true);  // X1 is symmetric
 }

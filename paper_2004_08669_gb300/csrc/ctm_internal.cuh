@@ -106,10 +106,12 @@ __device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int& epo
 // FP64 GEMM: C = alpha op(A) op(B) (+ beta C), column-major, optional per-k
 // scaling of B (scaleK[k] * B(k, j)), split-K over blockIdx.z writing
 // partial sums to C + z * splitStride (beta ignored when splits > 1).
-// Returns the number of kernels launched (1, or 2 with split-K).
+// Returns the number of kernels launched (1, or 2 with split-K).  lowq > 0
+// (no split-K): only the q x q blocks on or below the block diagonal of C are
+// needed; tiles entirely above it are skipped (left unwritten).
 int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, double alpha,
              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-             const double* scaleK, int splits, double* partial);
+             const double* scaleK, int splits, double* partial, int lowq = 0);
 
 // Blockwise vertex-weight contraction, in place on an N x N matrix (spin-fastest
 // index): every q x q block X_{gamma gamma'} becomes E o (E (X o E1) E), where

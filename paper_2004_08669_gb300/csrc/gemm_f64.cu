@@ -25,12 +25,14 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchun
                                                   const double* __restrict__ B, int ldb, double beta,
                                                   double* __restrict__ C, int ldc,
                                                   const double* __restrict__ scaleK,
-                                                  double* __restrict__ partial) {
+                                                  double* __restrict__ partial, int lowq) {
     __shared__ double As[BK][BM];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // lower q x q block triangle only: tiles entirely above it exit at once
+    if (lowq > 0 && (min(m0 + BM, M) - 1) / lowq < n0 / lowq) return;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
     double acc[4][4];
@@ -379,7 +381,7 @@ void wcontract_ar(cudaStream_t st, int arith, int m, int q, double* X, int ldx, 
 
 int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, double alpha,
              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-             const double* scaleK, int splits, double* partial) {
+             const double* scaleK, int splits, double* partial, int lowq) {
     if (M <= 0 || N <= 0) return 0;
     if (splits < 1 || K < 1) splits = 1;
     int kchunk = K < 1 ? BK : (K + splits - 1) / splits;
@@ -390,7 +392,7 @@ int gemm_f64(cudaStream_t st, bool transA, bool transB, int M, int N, int K, dou
     dim3 block(256);
 #define CTM_GEMM_LAUNCH(TA, TB)                                                                   \
     k_gemm_f64<TA, TB><<<grid, block, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, \
-                                               ldc, scaleK, partial)
+                                               ldc, scaleK, partial, splits > 1 ? 0 : lowq)
     if (!transA && !transB) CTM_GEMM_LAUNCH(false, false);
     else if (!transA && transB) CTM_GEMM_LAUNCH(false, true);
     else if (transA && !transB) CTM_GEMM_LAUNCH(true, false);

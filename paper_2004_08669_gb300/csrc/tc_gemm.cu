@@ -131,7 +131,7 @@ template <int KIND, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
               int K, double alpha, double beta, double* __restrict__ D, int ldd, int kchunk,
-              double* __restrict__ part, int* err) {
+              double* __restrict__ part, int* err, int lowq) {
     // K elements per 128-byte swizzle row: 64 (bf16) or 32 (fp32 / tf32)
     constexpr int KT = (KIND == 0) ? 64 : 32;
     constexpr int KMMA = (KIND == 0) ? 16 : 8;  // K per instruction (32 bytes)
@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(128, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    // lower q x q block triangle only: a tile entirely above it exits at once
+    // (uniformly, before any barrier or tensor-memory allocation)
+    if (lowq > 0 && (min(m0 + kBM, M) - 1) / lowq < n0 / lowq) return;
     // this CTA's K-tiles: [kt0, kt0 + nk); the host makes every slice non-empty
     const int nk_all = (K + KT - 1) / KT;
     const int kt0 = blockIdx.z * kchunk;
@@ -326,7 +329,8 @@ bool make_map(CUtensorMap* map, const void* base, bool bf16, int K, int rows, in
 
 template <int KIND, int BN>
 cudaError_t launch_tc(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, double alpha,
-                      double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err) {
+                      double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err,
+                      int lowq) {
     const size_t smem = 1024 + (size_t)kStages * (kBM * 128 + BN * 128);
     static const bool attr = [&]() {
         cudaFuncSetAttribute(k_tc_gemm<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -335,7 +339,7 @@ cudaError_t launch_tc(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
     (void)attr;
     dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
     k_tc_gemm<KIND, BN><<<grid, 128, smem, st>>>(a, b, M, N, K, alpha, beta, D, ldd, kchunk,
-                                                  splits > 1 ? part : nullptr, err);
+                                                  splits > 1 ? part : nullptr, err, splits > 1 ? 0 : lowq);
     if (splits > 1) {
         const size_t total = (size_t)M * N;
         const int blocks = (int)std::min<size_t>((total + 255) / 256, 4 * 152);
@@ -346,10 +350,13 @@ cudaError_t launch_tc(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& 
 
 template <int KIND>
 cudaError_t launch_bn(int bn, cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
-                      double alpha, double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err) {
-    if (bn == 64) return launch_tc<KIND, 64>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
-    if (bn == 128) return launch_tc<KIND, 128>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
-    return launch_tc<KIND, 256>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
+                      double alpha, double beta, double* D, int ldd, int splits, int kchunk, double* part, int* err,
+                      int lowq) {
+    if (bn == 64)
+        return launch_tc<KIND, 64>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err, lowq);
+    if (bn == 128)
+        return launch_tc<KIND, 128>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err, lowq);
+    return launch_tc<KIND, 256>(st, a, b, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err, lowq);
 }
 
 }  // namespace
@@ -385,7 +392,7 @@ int tc_plan_slices(const TcPlan& p, int K, bool bf16, int* kchunk) {
 
 cudaError_t tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, double alpha, const void* A, int lda,
                     const void* B, int ldb, double beta, double* D, int ldd, int* err, const TcPlan* plan,
-                    double* part, size_t part_cap) {
+                    double* part, size_t part_cap, int lowq) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if ((lda % 64) || (ldb % 64)) return cudaErrorInvalidValue;
     const TcPlan p = plan ? *plan : tc_default_plan(M, N, K, bf16);
@@ -396,8 +403,8 @@ cudaError_t tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, double alph
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, bf16, K, M, lda, kBM) || !make_map(&mb, B, bf16, K, N, ldb, p.bn))
         return cudaErrorInvalidValue;
-    if (bf16) return launch_bn<0>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
-    return launch_bn<1>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err);
+    if (bf16) return launch_bn<0>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err, lowq);
+    return launch_bn<1>(p.bn, st, ma, mb, M, N, K, alpha, beta, D, ldd, splits, kchunk, part, err, lowq);
 }
 
 }  // namespace ctm

@@ -35,9 +35,11 @@ int tc_plan_slices(const TcPlan& p, int K, bool bf16, int* kchunk);
 // *err (device int) is set to 1 if a bounded wait gave up.  plan NULL: the
 // default shape.  A split plan writes slices * M * N doubles of part
 // (capacity part_cap doubles) and sums them in order; cudaErrorInvalidValue
-// when they do not fit.
+// when they do not fit.  lowq > 0 (no split-K): only the q x q blocks on or
+// below the block diagonal of D are needed; tiles entirely above it are
+// skipped (left unwritten).
 cudaError_t tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, double alpha, const void* A, int lda,
                     const void* B, int ldb, double beta, double* D, int ldd, int* err, const TcPlan* plan = nullptr,
-                    double* part = nullptr, size_t part_cap = 0);
+                    double* part = nullptr, size_t part_cap = 0, int lowq = 0);
 
 }  // namespace ctm
