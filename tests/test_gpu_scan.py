@@ -197,6 +197,22 @@ def test_tf32_scan_m128_equals_independent_handles(ctm):
         assert np.isfinite(o["f"]) and o["f"] < 0
 
 
+def test_scan_energy_is_the_beta_derivative_of_beta_f(ctm):
+    """Through the scan: beta - d, beta, beta + d stepped to convergence
+    together (FP64, q = 20, m = 16, T = 0.6, d = 1e-4); the GPU's internal
+    energy at beta equals the central difference of its beta f to 1e-7, the
+    thermodynamic identity the oracle is pinned to for the same model."""
+    spins, m, beta, d = W.dodecahedron(), 16, 1 / 0.6, 1e-4
+    sc = ctm.Scan(spins, m, [beta - d, beta, beta + d], workers=3)
+    done, conv = sc.run(5000)
+    assert conv.tolist() == [1, 1, 1]
+    obs = sc.observables()
+    sc.close()
+    fd = ((beta + d) * obs[2]["f"] - (beta - d) * obs[0]["f"]) / (2 * d)
+    print(f"\nu = {obs[1]['u']:.12f}, d(beta f)/d beta = {fd:.12f}")
+    assert abs(fd - obs[1]["u"]) <= 1e-7 * abs(obs[1]["u"])
+
+
 def test_scan_invalid_arguments(ctm):
     cfg, keep = ctm.make_config(W.dodecahedron(), 8, 0.0)
     with pytest.raises(ctm.CtmError) as e:
