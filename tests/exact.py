@@ -6,6 +6,9 @@ Nothing here shares code with the oracle or with the CUDA path.
 - Onsager's internal energy (closed form with the complete elliptic integral
   of the first kind, scipy.special.ellipk).
 - Yang's spontaneous magnetisation (Yang 1952).
+- Their exact derivatives in K: d u/dK from the closed form of u with the
+  derivative of the complete elliptic integral,
+  dK(k)/dk = E(k) / (k (1 - k^2)) - K(k) / k, and d M/dK of Yang's formula.
 - Exact corner transfer matrices of a k x k quadrant of vertex tensors by
   direct contraction of the network drawn from its geometry.
 """
@@ -41,6 +44,29 @@ def onsager_u(K: float) -> float:
     k = 2.0 * math.sinh(2 * K) / math.cosh(2 * K) ** 2
     K1 = special.ellipk(k * k)
     return -1.0 / math.tanh(2 * K) * (1.0 + 2.0 / math.pi * (2.0 * math.tanh(2 * K) ** 2 - 1.0) * K1)
+
+
+def onsager_du_dK(K: float) -> float:
+    """d u / d K of onsager_u, differentiated by hand: u = -A B with
+    A = coth 2K and B = 1 + (2/pi)(2 t^2 - 1) K1(k), t = tanh 2K."""
+    s, c = math.sinh(2 * K), math.cosh(2 * K)
+    t = s / c
+    k = 2.0 * s / c ** 2
+    K1, E1 = special.ellipk(k * k), special.ellipe(k * k)
+    dK1_dk = E1 / (k * (1.0 - k * k)) - K1 / k
+    dk_dK = 4.0 / c - 8.0 * s * s / c ** 3
+    A, dA = c / s, -2.0 / s ** 2
+    B = 1.0 + 2.0 / math.pi * (2.0 * t * t - 1.0) * K1
+    dB = 2.0 / math.pi * (8.0 * t * (1.0 - t * t) * K1 + (2.0 * t * t - 1.0) * dK1_dk * dk_dK)
+    return -(dA * B + A * dB)
+
+
+def yang_dm_dK(K: float) -> float:
+    """d M / d K of Yang's M = (1 - sinh^-4 2K)^(1/8): cosh 2K sinh^-5 2K (1 - sinh^-4 2K)^(-7/8)."""
+    if K <= K_CRIT:
+        return 0.0
+    s = math.sinh(2 * K)
+    return math.cosh(2 * K) * s ** -5 * (1.0 - s ** -4) ** -0.875
 
 
 def yang_m(K: float) -> float:
