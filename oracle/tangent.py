@@ -100,6 +100,72 @@ def _entropy4_and_tangent(ev: np.ndarray, ev_dot: np.ndarray):
     return S, S_dot
 
 
+
+def _clusters(ev: np.ndarray, tol_c: float):
+    """Runs of consecutive eigenvalues (sorted by modulus) closer than
+    tol_c |lambda_1|: the multiplets whose basis is arbitrary."""
+    out, cur = [], [0]
+    for i in range(1, len(ev)):
+        if abs(ev[i] - ev[i - 1]) <= tol_c * abs(ev[0]):
+            cur.append(i)
+        else:
+            out.append(cur)
+            cur = [i]
+    if len(ev):
+        out.append(cur)
+    return out
+
+
+def _align(Z: np.ndarray, Z_ref: np.ndarray, ev: np.ndarray, tol_c: float):
+    """Rotate each cluster's columns of Z onto Z_ref's (the orthogonal
+    factor of the polar decomposition of Z_c^t Z_ref,c; a sign for a single
+    state).  Returns the rotated copy and the rotations."""
+    Z = Z.copy()
+    rot = []
+    for c in _clusters(ev, tol_c):
+        M = Z[:, c].T @ Z_ref[:, c]
+        a, _, bt = np.linalg.svd(M)
+        Rc = a @ bt
+        Z[:, c] = Z[:, c] @ Rc
+        rot.append((c, Rc))
+    return Z, rot
+
+
+def _rotate(Z_dot: np.ndarray, rot) -> np.ndarray:
+    Z_dot = Z_dot.copy()
+    for c, Rc in rot:
+        Z_dot[:, c] = Z_dot[:, c] @ Rc
+    return Z_dot
+
+
+def _gmres(apply, b: np.ndarray, tol: float, max_iter: int):
+    """Solve apply(x) = b by GMRES without restarts (Arnoldi with modified
+    Gram-Schmidt, applied twice; the small least-squares problem by lstsq).
+    Returns (x, iterations, relative residual)."""
+    b0 = float(np.linalg.norm(b))
+    if b0 == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    V = [b / b0]
+    H = np.zeros((max_iter + 1, max_iter))
+    res = 1.0
+    for k in range(max_iter):
+        w = apply(V[k])
+        for _ in range(2):
+            for j in range(k + 1):
+                h = float(V[j] @ w)
+                H[j, k] += h
+                w = w - h * V[j]
+        H[k + 1, k] = float(np.linalg.norm(w))
+        e1 = np.zeros(k + 2)
+        e1[0] = b0
+        y = np.linalg.lstsq(H[: k + 2, : k + 1], e1, rcond=None)[0]
+        res = float(np.linalg.norm(H[: k + 2, : k + 1] @ y - e1)) / b0
+        if res <= tol or H[k + 1, k] <= 1e-300:
+            return sum(yj * vj for yj, vj in zip(y, V)), k + 1, res
+        V.append(w / H[k + 1, k])
+    raise RuntimeError(f"GMRES did not reach {tol} in {max_iter} iterations (residual {res:.2e})")
+
+
 class TangentCTMRG:
     """Symmetric-CTMRG (Algorithm 3) with the forward-mode beta tangent
     carried beside every step."""
@@ -140,7 +206,7 @@ class TangentCTMRG:
         return O.sub_ctmrg(P, Pp, w, self.m, self.q)
 
     def _extension(self, w, w_dot):
-        """C~ = Sub(P, Omega P, w) and its tangent."""
+        """C~ = Sub(P, Omega P, w) and its tangent at the current state."""
         Pp = np.asfortranarray(self.omega[: self.m, None] * self.P)
         Pp_dot = np.asfortranarray(self.omega_dot[: self.m, None] * self.P + self.omega[: self.m, None] * self.P_dot)
         C = self._sub(self.P, Pp, w)
@@ -155,58 +221,170 @@ class TangentCTMRG:
         A_dot = C_dot[np.ix_(idx, idx)]
         return idx, ev, Z, A_dot
 
-    # -- one step -------------------------------------------------------------
-    def step(self) -> dict:
+    # -- one step, primal and tangent ----------------------------------------
+    def _primal(self, P, omega, live, U_ref=None) -> dict:
+        """The primal pieces of one step of Algorithm 3 from (P, omega).
+        With U_ref the kept eigenvectors are rotated, cluster by cluster,
+        onto U_ref's columns (orthogonal Procrustes; signs for single
+        states), which fixes the gauge of the step's output."""
         m, q, N = self.m, self.q, self.N
-        C, C_dot = self._extension(self.w, self.w_dot)
-        idx, ev, Z, A_dot = self._live_eig(C, C_dot)
+        Pp = np.asfortranarray(omega[:m, None] * P)
+        C = self._sub(P, Pp, self.w)
+        idx = np.array([g + m * s for s in range(q) for g in range(live)], dtype=np.int64)
+        A = C[np.ix_(idx, idx)]
+        ev, Z = O.eigh(0.5 * (A + A.T))
         meff = _kept_count(ev, m, self.tol_c, self.tol_z)
-        lam_dot, Z_dot = _eig_tangent(ev, Z, 0.5 * (A_dot + A_dot.T), meff, self.tol_c)
-
+        Zk = Z[:, :meff].copy()
+        rot = None
+        if U_ref is not None:
+            Zk, rot = _align(Zk, U_ref[idx, :meff], ev[:meff], self.tol_c)
         U = np.zeros((N, m), order="F")
-        U_dot = np.zeros((N, m), order="F")
-        U[idx, :meff] = Z[:, :meff]
-        U_dot[idx, :meff] = Z_dot
+        U[idx, :meff] = Zk
         Up = O.pindex2(U, m, q, m)
-        Up_dot = O.pindex2(U_dot, m, q, m)
-        X = self._sub(self.P, Up, self.w)
-        X_dot = self._sub(self.P_dot, Up, self.w) + self._sub(self.P, Up_dot, self.w) + self._sub(self.P, Up, self.w_dot)
+        X = self._sub(P, Up, self.w)
         R = U.T @ X
-        R_dot = U_dot.T @ X + U.T @ X_dot
         nrm = float(np.sqrt((R * R).sum()))
-        nrm_dot = float((R * R_dot).sum()) / nrm
-        self.P = np.asfortranarray(R / nrm)
-        self.P_dot = np.asfortranarray(R_dot / nrm - R * (nrm_dot / nrm ** 2))
-        self.kappa, self.kappa_dot = nrm, nrm_dot
+        z4 = float((ev[:meff] ** 4).sum())
+        omega_new = np.zeros(N)
+        omega_new[:meff] = ev[:meff] * z4 ** -0.25
+        return {"P": P, "omega": omega, "Pp": Pp, "idx": idx, "ev": ev, "Z": Z, "meff": meff, "rot": rot,
+                "U": U, "Up": Up, "X": X, "R": R, "nrm": nrm, "z4": z4,
+                "P_new": np.asfortranarray(R / nrm), "omega_new": omega_new}
 
-        evk, evk_dot = ev[:meff], lam_dot
-        z4 = float((evk ** 4).sum())
-        z4_dot = float((4.0 * evk ** 3 * evk_dot).sum())
+    def _tangent(self, pr: dict, P_dot, omega_dot, source: bool = True):
+        """Tangent of the step whose primal pieces are pr, along the input
+        tangent (P_dot, omega_dot), with (source) or without W's own beta
+        dependence.  Returns (P_new_dot, omega_new_dot, kappa_dot)."""
+        m, q, N = self.m, self.q, self.N
+        P, omega, Pp, idx, ev, Z, meff = pr["P"], pr["omega"], pr["Pp"], pr["idx"], pr["ev"], pr["Z"], pr["meff"]
+        Pp_dot = np.asfortranarray(omega_dot[:m, None] * P + omega[:m, None] * P_dot)
+        C_dot = self._sub(P_dot, Pp, self.w) + self._sub(P, Pp_dot, self.w)
+        if source:
+            C_dot += self._sub(P, Pp, self.w_dot)
+        A_dot = C_dot[np.ix_(idx, idx)]
+        lam_dot, Z_dot = _eig_tangent(ev, Z, 0.5 * (A_dot + A_dot.T), meff, self.tol_c)
+        if pr["rot"] is not None:
+            Z_dot = _rotate(Z_dot, pr["rot"])
+        U_dot = np.zeros((N, m), order="F")
+        U_dot[idx, :meff] = Z_dot
+        Up_dot = O.pindex2(U_dot, m, q, m)
+        X_dot = self._sub(P_dot, pr["Up"], self.w) + self._sub(P, Up_dot, self.w)
+        if source:
+            X_dot += self._sub(P, pr["Up"], self.w_dot)
+        R, nrm = pr["R"], pr["nrm"]
+        R_dot = U_dot.T @ pr["X"] + pr["U"].T @ X_dot
+        nrm_dot = float((R * R_dot).sum()) / nrm
+        P_new_dot = np.asfortranarray(R_dot / nrm - R * (nrm_dot / nrm ** 2))
+        evk = ev[:meff]
+        z4 = pr["z4"]
+        z4_dot = float((4.0 * evk ** 3 * lam_dot).sum())
         sc = z4 ** -0.25
         sc_dot = -0.25 * z4 ** -1.25 * z4_dot
-        self.omega = np.zeros(N)
-        self.omega_dot = np.zeros(N)
-        self.omega[:meff] = evk * sc
-        self.omega_dot[:meff] = evk_dot * sc + evk * sc_dot
-        self.live = meff
-        self.steps += 1
+        omega_new_dot = np.zeros(N)
+        omega_new_dot[:meff] = lam_dot * sc + evk * sc_dot
+        return P_new_dot, omega_new_dot, nrm_dot
 
-        # convergence of the primal (reading R6) and of the tangent: the
-        # normalised spectrum |omega_i| / |omega_1|, kappa, and their
-        # derivatives
+    def _measure(self, with_tangent: bool):
+        """Convergence of the primal (reading R6: the normalised spectrum
+        |omega_i| / |omega_1| and kappa) and of their derivatives."""
+        m = self.m
         a1 = abs(self.omega[0])
         ratio = np.abs(self.omega[:m]) / a1
         sgn = np.sign(self.omega[:m])
         ratio_dot = sgn * self.omega_dot[:m] / a1 - ratio * np.sign(self.omega[0]) * self.omega_dot[0] / a1
-        cur = (ratio, ratio_dot, nrm, nrm_dot)
+        cur = (ratio, ratio_dot, self.kappa, self.kappa_dot)
         if self._prev is None:
             delta = delta_t = np.inf
         else:
             pr, prd, pk, pkd = self._prev
-            delta = max(float(np.max(np.abs(ratio - pr))), abs(nrm / pk - 1.0))
-            delta_t = max(float(np.max(np.abs(ratio_dot - prd))), abs(nrm_dot - pkd) / nrm)
+            delta = max(float(np.max(np.abs(ratio - pr))), abs(self.kappa / pk - 1.0))
+            delta_t = (max(float(np.max(np.abs(ratio_dot - prd))), abs(self.kappa_dot - pkd) / self.kappa)
+                       if with_tangent else np.inf)
         self._prev = cur
-        return {"kappa": nrm, "kappa_dot": nrm_dot, "delta": delta, "delta_tangent": delta_t, "m_eff": meff}
+        return delta, delta_t
+
+    def step(self) -> dict:
+        """One primal step with its tangent (no gauge fixing: the tangent
+        follows whatever basis the eigensolver returns, reading R11)."""
+        pr = self._primal(self.P, self.omega, self.live)
+        P_dot, omega_dot, nrm_dot = self._tangent(pr, self.P_dot, self.omega_dot, True)
+        self.P, self.omega, self.live = pr["P_new"], pr["omega_new"], pr["meff"]
+        self.P_dot, self.omega_dot = P_dot, omega_dot
+        self.kappa, self.kappa_dot = pr["nrm"], nrm_dot
+        self.steps += 1
+        delta, delta_t = self._measure(True)
+        return {"kappa": self.kappa, "kappa_dot": nrm_dot, "delta": delta, "delta_tangent": delta_t,
+                "m_eff": pr["meff"]}
+
+    def run_primal(self, max_steps: int, tol: float = 1e-12) -> list:
+        """Primal steps only (the tangent is left untouched) until the
+        spectrum change falls below tol."""
+        hist = []
+        for _ in range(max_steps):
+            pr = self._primal(self.P, self.omega, self.live)
+            self.P, self.omega, self.live, self.kappa = pr["P_new"], pr["omega_new"], pr["meff"], pr["nrm"]
+            self.steps += 1
+            delta, _ = self._measure(False)
+            hist.append({"kappa": self.kappa, "delta": delta, "m_eff": pr["meff"]})
+            if delta < tol:
+                break
+        return hist
+
+    def fixed_point_derivative(self, tol: float = 1e-12, max_iter: int = 500, tol_fixed: float = 1e-10) -> dict:
+        """Derivative of a converged fixed point by the implicit function
+        theorem instead of the unrolled iteration.
+
+        A few primal steps with each step's kept eigenvectors rotated onto
+        the previous step's (Procrustes per cluster) make P repeat entry by
+        entry: a fixed point P* = F(P*) of the gauge-fixed step.  With the
+        reference basis held fixed, d P*/d beta solves
+          (I - J) x = dF/dbeta,   J = dF/d(P, omega) at the fixed point,
+        where J is one tangent step without W's own beta dependence and the
+        right side one tangent step from a zero input with it; the rotation
+        onto the reference does not move to first order there (the
+        parallel-transported tangent is orthogonal to its cluster).  The
+        linear system is solved by GMRES.  This works at unstable fixed
+        points too, where the unrolled tangent diverges (J has an eigenvalue
+        outside the unit circle but none equal to one)."""
+        m, q, N = self.m, self.q, self.N
+        U_ref = None
+        for _ in range(24):
+            pr = self._primal(self.P, self.omega, self.live, U_ref)
+            change = np.inf
+            if U_ref is not None:
+                # entries weighted by |omega| of both block legs: states far
+                # down the spectrum with nearly equal eigenvalues are fixed
+                # only to rounding / gap, and weigh nothing in any observable
+                a = np.abs(self.omega[:m]) / abs(self.omega[0])
+                wgt = a[:, None] * np.tile(a, q)[None, :]
+                change = float(np.max(wgt * np.abs(pr["P_new"] - self.P)))
+            self.P, self.omega, self.live, self.kappa = pr["P_new"], pr["omega_new"], pr["meff"], pr["nrm"]
+            U_ref = pr["U"]
+            if change < tol_fixed:
+                break
+        else:
+            raise RuntimeError("the gauge-fixed step does not repeat: not at a fixed point")
+        pr = self._primal(self.P, self.omega, self.live, U_ref)
+        meff = pr["meff"]
+        nP = m * N
+
+        def unpack(x):
+            om = np.zeros(N)
+            om[:meff] = x[nP:]
+            return np.asfortranarray(x[:nP].reshape((m, N), order="F")), om
+
+        def pack(P_dot, om_dot):
+            return np.concatenate([P_dot.ravel(order="F"), om_dot[:meff]])
+
+        def one_minus_J(x):
+            P_dot, om_dot, _ = self._tangent(pr, *unpack(x), source=False)
+            return x - pack(P_dot, om_dot)
+
+        rhs_P, rhs_om, _ = self._tangent(pr, np.zeros((m, N), order="F"), np.zeros(N), source=True)
+        x, iters, res = _gmres(one_minus_J, pack(rhs_P, rhs_om), tol, max_iter)
+        self.P_dot, self.omega_dot = unpack(x)
+        _, _, self.kappa_dot = self._tangent(pr, self.P_dot, self.omega_dot, source=True)
+        return {"iterations": iters, "residual": res, "fixed_point_change": change}
 
     def run(self, max_steps: int, tol: float = 1e-12, tol_tangent: float = 1e-10) -> list:
         hist = []

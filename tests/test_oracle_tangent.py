@@ -189,3 +189,73 @@ def test_planted_missing_weight_derivative_fails():
     ob = t.observables()
     assert abs(ob["C"] + K * K * E.onsager_du_dK(K)) > 1e-3
     assert not math.isclose(ob["d_beta_f_dbeta"], E.onsager_u(K), rel_tol=1e-6)
+
+
+# --- implicit fixed-point derivative ------------------------------------------------
+
+def test_gmres_solves_a_nonsymmetric_system():
+    rng = np.random.default_rng(11)
+    n = 40
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x, iters, res = TG._gmres(lambda v: A @ v, b, 1e-13, n)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-11, atol=1e-11)
+    assert res <= 1e-13 and iters <= n
+
+
+def test_procrustes_alignment_undoes_cluster_rotations_and_signs():
+    rng = np.random.default_rng(12)
+    Z_ref, _ = np.linalg.qr(rng.standard_normal((10, 5)))
+    ev = np.array([4.0, 2.0, 2.0, 2.0, -1.0])
+    G, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Z = Z_ref.copy()
+    Z[:, 1:4] = Z_ref[:, 1:4] @ G
+    Z[:, 0] *= -1.0
+    Z[:, 4] *= -1.0
+    Za, rot = TG._align(Z, Z_ref, ev, 1e-10)
+    np.testing.assert_allclose(Za, Z_ref, atol=1e-14)
+    assert [c for c, _ in rot] == [[0], [1, 2, 3], [4]]
+
+
+@pytest.mark.parametrize("model,m,beta", [("cube", 8, 1 / 0.5), ("ising", 16, 1 / 1.8)])
+def test_implicit_derivative_equals_the_unrolled_one(model, m, beta):
+    spins = MODELS[model]()
+    unrolled = converged(spins, m, beta)
+    t = TG.TangentCTMRG(spins, m, beta)
+    t.run_primal(3000, 1e-13)
+    info = t.fixed_point_derivative()
+    assert info["residual"] <= 1e-12
+    implicit = t.observables()
+    for k in ("df_dbeta", "du_dbeta", "dM_dbeta", "dS_dbeta"):
+        assert implicit[k] == pytest.approx(unrolled[k], rel=1e-8, abs=1e-12), k
+
+
+def test_implicit_derivative_at_an_unstable_fixed_point():
+    """q = 20, m = 8, T = 0.5: the converged state is unstable (continued
+    iteration amplifies the rounding noise), so the unrolled tangent cannot
+    converge; the implicit solve gives the derivative of that branch, which
+    Richardson differences of primal runs stopped on the branch (delta <
+    1e-12, reached before the drift) reproduce."""
+    spins, m, beta = W.dodecahedron(), 8, 1 / 0.5
+    t = TG.TangentCTMRG(spins, m, beta)
+    hist = t.run_primal(3000, 1e-12)
+    assert hist[-1]["delta"] < 1e-12
+    probe = TG.TangentCTMRG(spins, m, beta)
+    probe.run_primal(3000, 1e-12)
+    drift = probe.run_primal(150, 0.0)
+    assert max(r["delta"] for r in drift[-10:]) > 1e3 * hist[-1]["delta"]
+    t.fixed_point_derivative()
+    ob = t.observables()
+    assert ob["d_beta_f_dbeta"] == pytest.approx(ob["u"], rel=1e-10)
+
+    def on_branch(b):
+        c = TG.TangentCTMRG(spins, m, b)
+        assert c.run_primal(3000, 1e-12)[-1]["delta"] < 1e-12
+        return c.observables()
+
+    h = 2e-4 * beta
+    g = {s: on_branch(beta + s) for s in (-h, -h / 2, h / 2, h)}
+    for k, ok in (("df_dbeta", "f"), ("du_dbeta", "u"), ("dM_dbeta", "M"), ("dS_dbeta", "S_E")):
+        d1 = (g[h][ok] - g[-h][ok]) / (2 * h)
+        d2 = (g[h / 2][ok] - g[-h / 2][ok]) / h
+        assert ob[k] == pytest.approx((4.0 * d2 - d1) / 3.0, rel=1e-7), k
