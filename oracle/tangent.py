@@ -40,6 +40,11 @@ The iteration starts from the beta-independent initial state of Algorithm 3
 (P_dot = 0, omega_dot = 0) and runs primal and tangent together; once the
 primal has converged the tangents of the gauge-invariant quantities converge
 at the same rate, and their limits are the derivatives of the fixed point.
+At a gauge-fixed fixed point the same derivative comes from the implicit
+equation (I - J) x = dF/dbeta (fixed_point_derivative), and in reverse mode
+from the adjoint equation (I - J^t) x_bar = g with J^t applied as the
+transpose of one step (_vjp: transposed contractions, inverse permutations,
+the symmetric-eigen adjoint; adjoint_dlnkappa_dbeta).
 """
 from __future__ import annotations
 
@@ -136,6 +141,33 @@ def _rotate(Z_dot: np.ndarray, rot) -> np.ndarray:
     for c, Rc in rot:
         Z_dot[:, c] = Z_dot[:, c] @ Rc
     return Z_dot
+
+
+
+def _pindex2_adjoint(B_bar: np.ndarray, a: int, b: int, c: int) -> np.ndarray:
+    """Transpose (= inverse) of the permutation P-Index2 (Algorithm 2),
+    (a b) x c -> a x (c b): the oracle's own P-Index2 applied to the entry
+    numbers says where every entry goes."""
+    n = a * b * c
+    where = O.pindex2(np.arange(n, dtype=np.float64).reshape((a * b, c), order="F"), a, b, c)
+    src = where.ravel(order="F").astype(np.int64)
+    out = np.zeros(n)
+    out[src] = np.asarray(B_bar).ravel(order="F")
+    return np.asfortranarray(out.reshape((a * b, c), order="F"))
+
+
+def _eig_vjp(ev: np.ndarray, Z: np.ndarray, lam_bar: np.ndarray, Z_bar: np.ndarray, n: int, tol_c: float):
+    """Transpose of _eig_tangent: the cotangent of the (symmetrised) matrix
+    from those of the first n eigenvalues and eigenvectors."""
+    L = len(ev)
+    gap = ev[None, :n] - ev[:, None]
+    tiny = np.abs(gap) <= tol_c * abs(ev[0])
+    Fm = np.where(tiny, 0.0, 1.0 / np.where(tiny, 1.0, gap))
+    K = np.zeros((L, L))
+    K[:, :n] = (Z.T @ Z_bar) * Fm
+    K[np.arange(n), np.arange(n)] += lam_bar
+    A_bar = Z @ K @ Z.T
+    return 0.5 * (A_bar + A_bar.T)
 
 
 def _gmres(apply, b: np.ndarray, tol: float, max_iter: int):
@@ -330,23 +362,13 @@ class TangentCTMRG:
                 break
         return hist
 
-    def fixed_point_derivative(self, tol: float = 1e-12, max_iter: int = 500, tol_fixed: float = 1e-10) -> dict:
-        """Derivative of a converged fixed point by the implicit function
-        theorem instead of the unrolled iteration.
-
-        A few primal steps with each step's kept eigenvectors rotated onto
-        the previous step's (Procrustes per cluster) make P repeat entry by
-        entry: a fixed point P* = F(P*) of the gauge-fixed step.  With the
-        reference basis held fixed, d P*/d beta solves
-          (I - J) x = dF/dbeta,   J = dF/d(P, omega) at the fixed point,
-        where J is one tangent step without W's own beta dependence and the
-        right side one tangent step from a zero input with it; the rotation
-        onto the reference does not move to first order there (the
-        parallel-transported tangent is orthogonal to its cluster).  The
-        linear system is solved by GMRES.  This works at unstable fixed
-        points too, where the unrolled tangent diverges (J has an eigenvalue
-        outside the unit circle but none equal to one)."""
-        m, q, N = self.m, self.q, self.N
+    def gauge_fixed_point(self, tol_fixed: float = 1e-10) -> dict:
+        """From a converged state, a few primal steps with each step's kept
+        eigenvectors rotated onto the previous step's (Procrustes per
+        cluster) until P repeats entry by entry: a fixed point P* = F(P*) of
+        the gauge-fixed step.  Returns that step's primal pieces, whose
+        rotation reference is held fixed from then on."""
+        m, q = self.m, self.q
         U_ref = None
         for _ in range(24):
             pr = self._primal(self.P, self.omega, self.live, U_ref)
@@ -365,7 +387,13 @@ class TangentCTMRG:
         else:
             raise RuntimeError("the gauge-fixed step does not repeat: not at a fixed point")
         pr = self._primal(self.P, self.omega, self.live, U_ref)
-        meff = pr["meff"]
+        pr["fixed_point_change"] = change
+        return pr
+
+    def _packing(self, meff: int):
+        """The state vector of the fixed-point equations: P (m x N) and the
+        kept entries of omega."""
+        m, N = self.m, self.N
         nP = m * N
 
         def unpack(x):
@@ -373,8 +401,28 @@ class TangentCTMRG:
             om[:meff] = x[nP:]
             return np.asfortranarray(x[:nP].reshape((m, N), order="F")), om
 
-        def pack(P_dot, om_dot):
-            return np.concatenate([P_dot.ravel(order="F"), om_dot[:meff]])
+        def pack(P_part, om_part):
+            return np.concatenate([np.asarray(P_part).ravel(order="F"), om_part[:meff]])
+
+        return pack, unpack
+
+    def fixed_point_derivative(self, tol: float = 1e-12, max_iter: int = 500, tol_fixed: float = 1e-10) -> dict:
+        """Derivative of a converged fixed point by the implicit function
+        theorem instead of the unrolled iteration.
+
+        At the gauge-fixed fixed point (gauge_fixed_point), with the
+        reference basis held fixed, d P*/d beta solves
+          (I - J) x = dF/dbeta,   J = dF/d(P, omega) at the fixed point,
+        where J is one tangent step without W's own beta dependence and the
+        right side one tangent step from a zero input with it; the rotation
+        onto the reference does not move to first order there (the
+        parallel-transported tangent is orthogonal to its cluster).  The
+        linear system is solved by GMRES.  This works at unstable fixed
+        points too, where the unrolled tangent diverges (J has an eigenvalue
+        outside the unit circle but none equal to one)."""
+        m, N = self.m, self.N
+        pr = self.gauge_fixed_point(tol_fixed)
+        pack, unpack = self._packing(pr["meff"])
 
         def one_minus_J(x):
             P_dot, om_dot, _ = self._tangent(pr, *unpack(x), source=False)
@@ -384,7 +432,86 @@ class TangentCTMRG:
         x, iters, res = _gmres(one_minus_J, pack(rhs_P, rhs_om), tol, max_iter)
         self.P_dot, self.omega_dot = unpack(x)
         _, _, self.kappa_dot = self._tangent(pr, self.P_dot, self.omega_dot, source=True)
-        return {"iterations": iters, "residual": res, "fixed_point_change": change}
+        return {"iterations": iters, "residual": res, "fixed_point_change": pr["fixed_point_change"]}
+
+    # -- reverse mode ----------------------------------------------------------
+    def _sub_vjp(self, P, Pp, w, X_bar):
+        """Adjoint of out = Sub-CTMRG(P, P', w) (Algorithm 3: X1 = P^t P',
+        P-Index, the product with w, P-Index), linear in each argument: the
+        cotangents (P_bar, P'_bar, w_bar) of an output cotangent X_bar.  The
+        transposes of the two P-Index permutations are P-Index with the
+        middle legs exchanged (Algorithm 1 swaps the second and third legs)."""
+        m, q = self.m, self.q
+        X2 = O.pindex(P.T @ Pp, m, q, m, q)
+        X3_bar = O.pindex(X_bar, m, q, m, q)
+        X2_bar = X3_bar @ w.T
+        w_bar = X2.T @ X3_bar
+        X1_bar = O.pindex(X2_bar, m, m, q, q)
+        return Pp @ X1_bar.T, P @ X1_bar, w_bar
+
+    def _vjp(self, pr: dict, P_bar, omega_bar, kappa_bar: float, source: bool = True):
+        """Reverse mode of one step: the transpose of _tangent.  Given the
+        cotangents of the step's outputs (P_new, omega_new, kappa), returns
+        those of its inputs (P, omega) and, with source, of beta through W.
+        Each stage is the transpose of its forward counterpart: the
+        normalisations, U^t X, the Sub-CTMRG contractions (transposed
+        products and inverse permutations), P-Index2 (an inverse
+        permutation), the gauge rotation, and the symmetric-eigen adjoint
+        A_bar = Z (diag(lambda_bar) + F o (Z^t Z_bar)) Z^t (symmetrised) with
+        F_ji = 1 / (lambda_i - lambda_j), set to zero inside a cluster
+        (reading R11) and coupling the kept columns to the whole live
+        spectrum."""
+        m, q, N = self.m, self.q, self.N
+        P, omega, Pp, idx, ev, Z, meff = pr["P"], pr["omega"], pr["Pp"], pr["idx"], pr["ev"], pr["Z"], pr["meff"]
+        R, nrm, U, X = pr["R"], pr["nrm"], pr["U"], pr["X"]
+        # P_new = R / kappa, kappa = ||R||
+        R_bar = P_bar / nrm + (kappa_bar - float((P_bar * R).sum()) / nrm ** 2) * R / nrm
+        # R = U^t X
+        U_bar = X @ R_bar.T
+        X_bar = U @ R_bar
+        # X = Sub(P, U', w)
+        P_in_bar, Up_bar, wX_bar = self._sub_vjp(P, pr["Up"], self.w, X_bar)
+        U_bar = U_bar + _pindex2_adjoint(Up_bar, m, q, m)
+        Z_bar = U_bar[idx, :meff]
+        if pr["rot"] is not None:
+            Z_bar = _rotate(Z_bar, [(c, Rc.T) for c, Rc in pr["rot"]])
+        # omega_new = lambda (sum lambda^4)^(-1/4) on the kept states
+        evk = ev[:meff]
+        z4 = pr["z4"]
+        ob = omega_bar[:meff]
+        lam_bar = ob * z4 ** -0.25 - float((ob * evk).sum()) * z4 ** -1.25 * evk ** 3
+        A_bar = _eig_vjp(ev, Z, lam_bar, Z_bar, meff, self.tol_c)
+        C_bar = np.zeros((N, N), order="F")
+        C_bar[np.ix_(idx, idx)] = A_bar
+        # C~ = Sub(P, Omega P, w)
+        P_a, Pp_bar, wC_bar = self._sub_vjp(P, Pp, self.w, C_bar)
+        P_in_bar = P_in_bar + P_a + omega[:m, None] * Pp_bar
+        omega_in_bar = np.zeros(N)
+        omega_in_bar[:m] = (P * Pp_bar).sum(axis=1)
+        beta_bar = float(((wX_bar + wC_bar) * self.w_dot).sum()) if source else 0.0
+        return np.asfortranarray(P_in_bar), omega_in_bar, beta_bar
+
+    def adjoint_dlnkappa_dbeta(self, tol: float = 1e-12, max_iter: int = 500, tol_fixed: float = 1e-10) -> dict:
+        """d ln kappa / d beta of the fixed point in reverse mode: the
+        cotangent of ln kappa through one gauge-fixed step gives its partial
+        derivatives (g_x, g_beta); the adjoint fixed-point equation
+          (I - J^t) x_bar = g_x
+        is solved by GMRES with J^t applied as one reverse step, and the
+        total derivative is g_beta + x_bar . dF/dbeta, the last term again
+        one reverse step (its beta cotangent).  f = -ln kappa / (2 beta)."""
+        pr = self.gauge_fixed_point(tol_fixed)
+        meff = pr["meff"]
+        pack, unpack = self._packing(meff)
+        zP, zo = np.zeros((self.m, self.N), order="F"), np.zeros(self.N)
+        gP, go, g_beta = self._vjp(pr, zP, zo, 1.0 / pr["nrm"], source=True)
+
+        def one_minus_Jt(y):
+            P_b, om_b, _ = self._vjp(pr, *unpack(y), 0.0, source=False)
+            return y - pack(P_b, om_b)
+
+        x_bar, iters, res = _gmres(one_minus_Jt, pack(gP, go), tol, max_iter)
+        _, _, b_beta = self._vjp(pr, *unpack(x_bar), 0.0, source=True)
+        return {"dlnkappa_dbeta": g_beta + b_beta, "iterations": iters, "residual": res}
 
     def run(self, max_steps: int, tol: float = 1e-12, tol_tangent: float = 1e-10) -> list:
         hist = []

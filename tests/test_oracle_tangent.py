@@ -259,3 +259,134 @@ def test_implicit_derivative_at_an_unstable_fixed_point():
         d1 = (g[h][ok] - g[-h][ok]) / (2 * h)
         d2 = (g[h / 2][ok] - g[-h / 2][ok]) / h
         assert ob[k] == pytest.approx((4.0 * d2 - d1) / 3.0, rel=1e-7), k
+
+
+# --- reverse mode -------------------------------------------------------------------
+
+def test_pindex2_adjoint_is_the_transpose():
+    rng = np.random.default_rng(13)
+    a, b, c = 3, 4, 5
+    A = np.asfortranarray(rng.standard_normal((a * b, c)))
+    B_bar = np.asfortranarray(rng.standard_normal((a, c * b)))
+    assert (B_bar * O.pindex2(A, a, b, c)).sum() == pytest.approx((TG._pindex2_adjoint(B_bar, a, b, c) * A).sum(),
+                                                                 rel=1e-14)
+
+
+def test_eig_vjp_is_the_transpose_of_eig_tangent():
+    rng = np.random.default_rng(14)
+    n = 10
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev_in = np.array([4.0, -3.0, 2.0, 2.0, 1.5, 1.0, 0.7, 0.7, 0.3, 0.1])
+    ev, Z = O.eigh(Q @ np.diag(ev_in) @ Q.T)
+    B = rng.standard_normal((n, n))
+    A_dot = B + B.T
+    k = 6
+    lam_dot, Z_dot = TG._eig_tangent(ev, Z, A_dot, k, 1e-10)
+    lam_bar, Z_bar = rng.standard_normal(k), rng.standard_normal((n, k))
+    lhs = lam_bar @ lam_dot + (Z_bar * Z_dot).sum()
+    rhs = (TG._eig_vjp(ev, Z, lam_bar, Z_bar, k, 1e-10) * A_dot).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def twisted_reference(t, pr0, angle=0.7):
+    """pr0's kept basis with every multiplet's columns turned by a fixed
+    angle (pairs) or orthogonal matrix, so that aligning onto it takes a
+    rotation that is not symmetric."""
+    U = pr0["U"].copy()
+    idx, meff = pr0["idx"], pr0["meff"]
+    rng = np.random.default_rng(17)
+    for c in TG._clusters(pr0["ev"][:meff], t.tol_c):
+        if len(c) > 1:
+            G, _ = np.linalg.qr(rng.standard_normal((len(c), len(c))))
+            if len(c) == 2:
+                G = np.array([[np.cos(angle), -np.sin(angle)], [np.sin(angle), np.cos(angle)]])
+            sub = U[np.ix_(idx, c)] @ G
+            U[np.ix_(idx, c)] = sub
+    return U
+
+
+REVERSE_CASES = [("clock3", 6, 0.5, 5), ("dodecahedron", 4, 1 / 0.5, 8), ("cube", 8, 1 / 0.5, 12),
+                 ("ising", 16, 1 / 1.8, 30)]
+
+
+@pytest.mark.parametrize("model,m,beta,steps", REVERSE_CASES)
+@pytest.mark.parametrize("rotated", [False, True])
+def test_reverse_step_is_the_transpose_of_the_tangent_step(model, m, beta, steps, rotated):
+    """<y_bar, J x_dot> = <J^t y_bar, x_dot> for one step, J with W's beta
+    dependence as a third input, with and without the gauge rotation onto a
+    reference basis."""
+    spins = MODELS[model]()
+    t = TG.TangentCTMRG(spins, m, beta)
+    t.run_primal(steps, 0.0)
+    pr0 = t._primal(t.P, t.omega, t.live)
+    pr = t._primal(pr0["P_new"], pr0["omega_new"], pr0["meff"], twisted_reference(t, pr0) if rotated else None)
+    assert (pr["rot"] is not None) == rotated
+    rng = np.random.default_rng(15)
+    N = t.N
+    P_dot = np.asfortranarray(rng.standard_normal((m, N)))
+    om_dot = np.zeros(N)
+    om_dot[:m] = rng.standard_normal(m)
+    Pn_dot, on_dot, k_dot = t._tangent(pr, P_dot, om_dot, True)
+    P_bar = np.asfortranarray(rng.standard_normal((m, N)))
+    om_bar = np.zeros(N)
+    om_bar[: pr["meff"]] = rng.standard_normal(pr["meff"])
+    k_bar = float(rng.standard_normal())
+    Pb, ob, bb = t._vjp(pr, P_bar, om_bar, k_bar, True)
+    lhs = (P_bar * Pn_dot).sum() + om_bar @ on_dot + k_bar * k_dot
+    rhs = (Pb * P_dot).sum() + ob @ om_dot + bb
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+@pytest.mark.parametrize("model,m,beta", [("cube", 8, 1 / 0.5), ("ising", 16, 1 / 1.8)])
+def test_adjoint_fixed_point_equals_forward(model, m, beta):
+    """d ln kappa / d beta through the adjoint equation (I - J^t) x_bar = g
+    equals the forward implicit derivative; for Ising it is -2 u (ln kappa =
+    -2 beta f) with Onsager's u."""
+    spins = MODELS[model]()
+    t = TG.TangentCTMRG(spins, m, beta)
+    t.run_primal(3000, 1e-13)
+    rev = t.adjoint_dlnkappa_dbeta()
+    assert rev["residual"] <= 1e-12
+    t.fixed_point_derivative()
+    assert rev["dlnkappa_dbeta"] == pytest.approx(t.kappa_dot / t.kappa, rel=1e-9)
+    if model == "ising":
+        assert rev["dlnkappa_dbeta"] == pytest.approx(-2.0 * E.onsager_u(beta), rel=1e-10)
+
+
+def test_planted_untransposed_gauge_rotation_fails_the_transpose_test(monkeypatch):
+    """Rotating the eigenvector cotangent by R instead of R^t breaks the
+    transpose identity wherever a cluster's rotation is not symmetric (a
+    C3v doublet of the q = 20 corner, turned against a twisted reference)."""
+    spins, m, beta = W.dodecahedron(), 4, 1 / 0.5
+    t = TG.TangentCTMRG(spins, m, beta)
+    t.run_primal(8, 0.0)
+    pr0 = t._primal(t.P, t.omega, t.live)
+    # a 2 x 2 reflection is symmetric: pick the twist that makes the
+    # doublet's alignment a proper rotation
+    for flip in (False, True):
+        U_ref = twisted_reference(t, pr0)
+        if flip:
+            c = next(c for c in TG._clusters(pr0["ev"][: pr0["meff"]], t.tol_c) if len(c) == 2)
+            U_ref[pr0["idx"], c[1]] *= -1.0
+        pr = t._primal(pr0["P_new"], pr0["omega_new"], pr0["meff"], U_ref)
+        if any(len(c) == 2 and abs(Rc[0, 1] - Rc[1, 0]) > 0.1 for c, Rc in pr["rot"]):
+            break
+    else:
+        raise AssertionError("no doublet rotation that is not symmetric")
+    real_rotate = TG._rotate
+
+    def wrong_rotate(Z_dot, rot):
+        return real_rotate(Z_dot, [(c, Rc.T) for c, Rc in rot])
+
+    rng = np.random.default_rng(16)
+    N = t.N
+    P_dot = np.asfortranarray(rng.standard_normal((m, N)))
+    om_dot = np.zeros(N)
+    Pn_dot, on_dot, k_dot = t._tangent(pr, P_dot, om_dot, False)
+    P_bar = np.asfortranarray(rng.standard_normal((m, N)))
+    om_bar = np.zeros(N)
+    monkeypatch.setattr(TG, "_rotate", wrong_rotate)
+    Pb, ob, _ = t._vjp(pr, P_bar, om_bar, 0.0, False)
+    lhs = (P_bar * Pn_dot).sum()
+    rhs = (Pb * P_dot).sum()
+    assert abs(lhs - rhs) > 1e-6 * abs(lhs)
