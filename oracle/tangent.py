@@ -92,6 +92,67 @@ def _eig_tangent(ev: np.ndarray, Z: np.ndarray, A_dot: np.ndarray, n: int, tol_c
     return lam_dot, Z @ Fm
 
 
+def _deflated_solve(A: np.ndarray, Zb: np.ndarray, lam: np.ndarray, Rhs: np.ndarray, tol: float = 1e-14,
+                    max_iter: int = 2000):
+    """Y with lambda_i y_i - A y_i = r_i on the complement of span(Zb) (Zb
+    eigenvectors of the symmetric A, so A leaves the complement invariant),
+    column by column, for right sides in that complement: the fixed-point
+    iteration Y <- (R + (I - Zb Zb^t) A Y) diag(lambda)^-1, which converges at
+    the rate max_i |lambda_b| / |lambda_i| (lambda_b the largest eigenvalue
+    left outside the block).  Returns (Y, iterations)."""
+    def deflate(Y):
+        return Y - Zb @ (Zb.T @ Y)
+
+    inv = 1.0 / lam
+    Y = Rhs * inv
+    scale = max(float(np.abs(Y).max()), 1e-300)
+    for it in range(1, max_iter + 1):
+        Y_new = (Rhs + deflate(A @ Y)) * inv
+        change = float(np.abs(Y_new - Y).max())
+        Y = Y_new
+        if change <= tol * scale:
+            return Y, it
+    raise RuntimeError("deflated iteration did not converge")
+
+
+def _block_coupling(ev: np.ndarray, b: int, n: int, tol_c: float) -> np.ndarray:
+    gap = ev[None, :n] - ev[:b, None]
+    tiny = np.abs(gap) <= tol_c * abs(ev[0])
+    return np.where(tiny, 0.0, 1.0 / np.where(tiny, 1.0, gap))
+
+
+def _eig_tangent_block(A: np.ndarray, ev: np.ndarray, Z: np.ndarray, A_dot: np.ndarray, n: int, b: int,
+                       tol_c: float):
+    """_eig_tangent from the leading b eigenpairs only (what a block
+    subspace iteration provides), for the first n <= b pairs.  Inside the
+    block the coupling is the same sum over j < b; the part outside it,
+    y_i = (lambda_i - A)^-1 (I - Z_b Z_b^t) A_dot z_i, comes from the deflated
+    iteration (_deflated_solve).  Returns (lambda_dot, Z_dot, iterations)."""
+    Zb = Z[:, :b]
+    H = Zb.T @ A_dot @ Zb
+    H = 0.5 * (H + H.T)
+    lam_dot = np.diag(H)[:n].copy()
+    Z_in = Zb @ (H[:, :n] * _block_coupling(ev, b, n, tol_c))
+    Rhs = A_dot @ Z[:, :n]
+    Y, it = _deflated_solve(A, Zb, ev[:n], Rhs - Zb @ (Zb.T @ Rhs))
+    return lam_dot, Z_in + Y, it
+
+
+def _eig_vjp_block(A: np.ndarray, ev: np.ndarray, Z: np.ndarray, lam_bar: np.ndarray, Z_bar: np.ndarray, n: int,
+                   b: int, tol_c: float):
+    """Transpose of _eig_tangent_block.  The deflated solve is symmetric
+    column by column, so the outside part's cotangent is the same solve
+    applied to the deflated Z_bar, paired with the kept vectors."""
+    Zb = Z[:, :b]
+    K = (Zb.T @ Z_bar) * _block_coupling(ev, b, n, tol_c)
+    K[np.arange(n), np.arange(n)] += lam_bar
+    A_bar = Zb[:, :] @ np.hstack([K, np.zeros((b, b - n))]) @ Zb.T
+    Xb, _ = _deflated_solve(A, Zb, ev[:n], Z_bar - Zb @ (Zb.T @ Z_bar))
+    Xb = Xb - Zb @ (Zb.T @ Xb)
+    A_bar = A_bar + Xb @ Z[:, :n].T
+    return 0.5 * (A_bar + A_bar.T)
+
+
 def _entropy4_and_tangent(ev: np.ndarray, ev_dot: np.ndarray):
     """S = -sum p ln p with p = ev^4 / sum ev^4, and dS."""
     w4 = ev ** 4
@@ -203,7 +264,12 @@ class TangentCTMRG:
     carried beside every step."""
 
     def __init__(self, spins, m: int, beta: float, boundary_spin: int = 0,
-                 tol_cluster: float = 1e-10, tol_zero: float = 1e-10):
+                 tol_cluster: float = 1e-10, tol_zero: float = 1e-10, ritz_block: int | None = None):
+        """ritz_block: take the eigen tangent (and its transpose) from the
+        leading ritz_block eigenpairs and a deflated iteration, as a block
+        subspace iteration would, instead of from the whole live spectrum."""
+        self.ritz_block = ritz_block
+        self.block_iterations = 0
         self.spins = np.ascontiguousarray(spins, dtype=np.float64)
         self.q, self.dim = self.spins.shape
         if m < 1 or not 0 <= boundary_spin < self.q:
@@ -253,6 +319,24 @@ class TangentCTMRG:
         A_dot = C_dot[np.ix_(idx, idx)]
         return idx, ev, Z, A_dot
 
+    def _eig_t(self, A, ev, Z, A_dot, n):
+        if self.ritz_block is None:
+            return _eig_tangent(ev, Z, A_dot, n, self.tol_c)
+        b = min(len(ev), max(self.ritz_block, n))
+        if b == len(ev):
+            return _eig_tangent(ev, Z, A_dot, n, self.tol_c)
+        lam_dot, Z_dot, it = _eig_tangent_block(A, ev, Z, A_dot, n, b, self.tol_c)
+        self.block_iterations = max(self.block_iterations, it)
+        return lam_dot, Z_dot
+
+    def _eig_v(self, A, ev, Z, lam_bar, Z_bar, n):
+        if self.ritz_block is None:
+            return _eig_vjp(ev, Z, lam_bar, Z_bar, n, self.tol_c)
+        b = min(len(ev), max(self.ritz_block, n))
+        if b == len(ev):
+            return _eig_vjp(ev, Z, lam_bar, Z_bar, n, self.tol_c)
+        return _eig_vjp_block(A, ev, Z, lam_bar, Z_bar, n, b, self.tol_c)
+
     # -- one step, primal and tangent ----------------------------------------
     def _primal(self, P, omega, live, U_ref=None) -> dict:
         """The primal pieces of one step of Algorithm 3 from (P, omega).
@@ -264,7 +348,8 @@ class TangentCTMRG:
         C = self._sub(P, Pp, self.w)
         idx = np.array([g + m * s for s in range(q) for g in range(live)], dtype=np.int64)
         A = C[np.ix_(idx, idx)]
-        ev, Z = O.eigh(0.5 * (A + A.T))
+        A = 0.5 * (A + A.T)
+        ev, Z = O.eigh(A)
         meff = _kept_count(ev, m, self.tol_c, self.tol_z)
         Zk = Z[:, :meff].copy()
         rot = None
@@ -279,7 +364,7 @@ class TangentCTMRG:
         z4 = float((ev[:meff] ** 4).sum())
         omega_new = np.zeros(N)
         omega_new[:meff] = ev[:meff] * z4 ** -0.25
-        return {"P": P, "omega": omega, "Pp": Pp, "idx": idx, "ev": ev, "Z": Z, "meff": meff, "rot": rot,
+        return {"P": P, "omega": omega, "Pp": Pp, "idx": idx, "A": A, "ev": ev, "Z": Z, "meff": meff, "rot": rot,
                 "U": U, "Up": Up, "X": X, "R": R, "nrm": nrm, "z4": z4,
                 "P_new": np.asfortranarray(R / nrm), "omega_new": omega_new}
 
@@ -294,7 +379,7 @@ class TangentCTMRG:
         if source:
             C_dot += self._sub(P, Pp, self.w_dot)
         A_dot = C_dot[np.ix_(idx, idx)]
-        lam_dot, Z_dot = _eig_tangent(ev, Z, 0.5 * (A_dot + A_dot.T), meff, self.tol_c)
+        lam_dot, Z_dot = self._eig_t(pr["A"], ev, Z, 0.5 * (A_dot + A_dot.T), meff)
         if pr["rot"] is not None:
             Z_dot = _rotate(Z_dot, pr["rot"])
         U_dot = np.zeros((N, m), order="F")
@@ -480,7 +565,7 @@ class TangentCTMRG:
         z4 = pr["z4"]
         ob = omega_bar[:meff]
         lam_bar = ob * z4 ** -0.25 - float((ob * evk).sum()) * z4 ** -1.25 * evk ** 3
-        A_bar = _eig_vjp(ev, Z, lam_bar, Z_bar, meff, self.tol_c)
+        A_bar = self._eig_v(pr["A"], ev, Z, lam_bar, Z_bar, meff)
         C_bar = np.zeros((N, N), order="F")
         C_bar[np.ix_(idx, idx)] = A_bar
         # C~ = Sub(P, Omega P, w)
@@ -530,8 +615,9 @@ class TangentCTMRG:
         C, C_dot = self._extension(self.w, self.w_dot)
         Ch, Ch_dot = self._extension(self.wh, self.wh_dot)
         idx, ev, Z, A_dot = self._live_eig(C, C_dot)
+        A = C[np.ix_(idx, idx)]
         meff = _kept_count(ev, m, self.tol_c, self.tol_z)
-        lam_dot, Z_dot = _eig_tangent(ev, Z, 0.5 * (A_dot + A_dot.T), meff, self.tol_c)
+        lam_dot, Z_dot = self._eig_t(0.5 * (A + A.T), ev, Z, 0.5 * (A_dot + A_dot.T), meff)
         evk, Zk = ev[:meff], Z[:, :meff]
         Hh = Ch[np.ix_(idx, idx)]
         Hh_dot = Ch_dot[np.ix_(idx, idx)]

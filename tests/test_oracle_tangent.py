@@ -390,3 +390,67 @@ def test_planted_untransposed_gauge_rotation_fails_the_transpose_test(monkeypatc
     lhs = (P_bar * Pn_dot).sum()
     rhs = (Pb * P_dot).sum()
     assert abs(lhs - rhs) > 1e-6 * abs(lhs)
+
+
+# --- the eigen tangent from a Ritz block (what the GPU's subspace iteration has) --
+
+def q20_corner(m=8, T=0.44, steps=40):
+    t = TG.TangentCTMRG(W.dodecahedron(), m, 1.0 / T, ritz_block=m + max(8, m // 8))
+    t.run_primal(steps, 0.0)
+    pr0 = t._primal(t.P, t.omega, t.live)
+    return t, t._primal(pr0["P_new"], pr0["omega_new"], pr0["meff"], pr0["U"])
+
+
+def test_block_eigen_tangent_equals_the_full_spectrum_one():
+    """From the leading b = m + 8 eigenpairs and the deflated iteration
+    (rate |lambda_b / lambda_m|, 0.40 here) the kept pairs' tangent equals
+    the one coupled to the whole live spectrum, on a q = 20 corner."""
+    t, pr = q20_corner()
+    rng = np.random.default_rng(18)
+    L = len(pr["ev"])
+    B = rng.standard_normal((L, L))
+    A_dot = B + B.T
+    n, b = pr["meff"], t.ritz_block
+    ld, Zd = TG._eig_tangent(pr["ev"], pr["Z"], A_dot, n, t.tol_c)
+    ld_b, Zd_b, it = TG._eig_tangent_block(pr["A"], pr["ev"], pr["Z"], A_dot, n, b, t.tol_c)
+    rate = abs(pr["ev"][b] / pr["ev"][n - 1])
+    assert rate < 0.5 and it <= int(np.log(1e-14) / np.log(rate)) + 8
+    np.testing.assert_allclose(ld_b, ld, rtol=1e-12, atol=1e-12 * np.abs(ld).max())
+    np.testing.assert_allclose(Zd_b, Zd, atol=1e-12 * np.abs(Zd).max())
+    lam_bar, Z_bar = rng.standard_normal(n), rng.standard_normal((L, n))
+    lhs = lam_bar @ ld_b + (Z_bar * Zd_b).sum()
+    rhs = (TG._eig_vjp_block(pr["A"], pr["ev"], pr["Z"], lam_bar, Z_bar, n, b, t.tol_c) * A_dot).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_block_step_is_transposed_and_equals_the_full_step():
+    t, pr = q20_corner(m=6, T=0.5)
+    full = TG.TangentCTMRG(W.dodecahedron(), 6, 1 / 0.5)
+    rng = np.random.default_rng(19)
+    N = t.N
+    P_dot = np.asfortranarray(rng.standard_normal((6, N)))
+    om_dot = np.zeros(N)
+    om_dot[:6] = rng.standard_normal(6)
+    Pn, on, kd = t._tangent(pr, P_dot, om_dot, True)
+    Pn_f, on_f, kd_f = full._tangent(pr, P_dot, om_dot, True)
+    np.testing.assert_allclose(Pn, Pn_f, atol=1e-12 * np.abs(Pn_f).max())
+    assert kd == pytest.approx(kd_f, rel=1e-12)
+    P_bar = np.asfortranarray(rng.standard_normal((6, N)))
+    om_bar = np.zeros(N)
+    om_bar[: pr["meff"]] = rng.standard_normal(pr["meff"])
+    Pb, ob, bb = t._vjp(pr, P_bar, om_bar, 0.3, True)
+    lhs = (P_bar * Pn).sum() + om_bar @ on + 0.3 * kd
+    rhs = (Pb * P_dot).sum() + ob @ om_dot + bb
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+@pytest.mark.parametrize("model,m,beta", [("cube", 8, 1 / 0.5), ("ising", 16, 1 / 1.8)])
+def test_ritz_block_run_gives_the_same_derivatives(model, m, beta):
+    spins = MODELS[model]()
+    full = converged(spins, m, beta)
+    t = TG.TangentCTMRG(spins, m, beta, ritz_block=m + max(8, m // 8))
+    t.run(3000, 1e-13, 1e-11)
+    blk = t.observables()
+    assert t.block_iterations > 0
+    for k in ("df_dbeta", "du_dbeta", "dM_dbeta", "dS_dbeta"):
+        assert blk[k] == pytest.approx(full[k], rel=1e-11, abs=1e-13), k
