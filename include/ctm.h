@@ -137,8 +137,17 @@ ctm_status ctm_step(ctm_handle* h, int nsteps, int* steps_done, ctm_step_info* i
  * eigenpairs, then Eq. (5)-(6) and the free energy. out: host. */
 ctm_status ctm_observables(ctm_handle* h, ctm_obs* out);
 
-/* Adjoint of the step for the fixed-point derivatives of f and M with
- * respect to beta.  Not built yet: returns CTM_EUNSUPPORTED. */
+/* Derivative of the converged fixed point with respect to beta, contracted
+ * with the gradient of the observables:
+ *   *grad_beta = grad_obs->f dF/dbeta + grad_obs->M dM/dbeta
+ *              + grad_obs->u du/dbeta + grad_obs->S_E dS_E/dbeta
+ * (the other fields of grad_obs are ignored), by implicit differentiation
+ * of the gauge-fixed step at the current, converged state: the tangent of
+ * one step (the contractions by the product rule, the leading Ritz pairs'
+ * first-order perturbation with the coupling outside the Ritz block from a
+ * deflated iteration, the normalisations) and the linear fixed-point
+ * equation (I - J) x = dF/dbeta.  Not built yet: returns CTM_EUNSUPPORTED
+ * and leaves *grad_beta untouched. */
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
 
 /* Effective correlation length (Sec. II): the leading eigenvalues of the
