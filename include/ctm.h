@@ -139,14 +139,14 @@ ctm_status ctm_observables(ctm_handle* h, ctm_obs* out);
 
 /* Derivative of the converged fixed point with respect to beta, contracted
  * with the gradient of the observables:
- *   *grad_beta = grad_obs->f dF/dbeta + grad_obs->M dM/dbeta
+ *   *grad_beta = grad_obs->f df/dbeta + grad_obs->M dM/dbeta
  *              + grad_obs->u du/dbeta + grad_obs->S_E dS_E/dbeta
  * (the other fields of grad_obs are ignored), by implicit differentiation
  * of the gauge-fixed step at the current, converged state: the tangent of
  * one step (the contractions by the product rule, the leading Ritz pairs'
  * first-order perturbation with the coupling outside the Ritz block from a
  * deflated iteration, the normalisations) and the linear fixed-point
- * equation (I - J) x = dF/dbeta.  Not built yet: returns CTM_EUNSUPPORTED
+ * equation (I - J) x = d(step)/dbeta, J = d(step)/d(state).  Not built yet: returns CTM_EUNSUPPORTED
  * and leaves *grad_beta untouched. */
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
 
