@@ -137,6 +137,43 @@ ctm_status ctm_step(ctm_handle* h, int nsteps, int* steps_done, ctm_step_info* i
  * eigenpairs, then Eq. (5)-(6) and the free energy. out: host. */
 ctm_status ctm_observables(ctm_handle* h, ctm_obs* out);
 
+/* One step of the forward-mode beta tangent (FP64 form; the derivative of
+ * the step of Algorithm 3).  At the handle's current state (P, omega), set
+ * for instance by ctm_set_state, it takes one step and its tangent along the
+ * input tangent (P_dot, omega_dot) and, with source != 0, along W's own beta
+ * dependence (dW/dbeta = W times the plaquette's sum of dot products):
+ *   C~ = Sub-CTMRG(P, Omega P, W) and dC~ by the product rule;
+ *   the kept eigenpairs' first-order perturbation: the coupling among the
+ *   leading Ritz pairs that are eigenpairs to 1e-11 |theta_0| (zero inside a
+ *   cluster, |theta_i - theta_j| <= tol_cluster |theta_0|), and the part
+ *   outside them by the deflated iteration
+ *   Y <- (R + (I - Z Z^t) C~ Y) diag(theta)^-1 to a change of 1e-14;
+ *   U, U' = P-Index2(U), X = Sub-CTMRG(P, U', W), P_raw = U^t X and their
+ *   tangents; kappa = ||P_raw||, P_new = P_raw / kappa; omega_new = theta
+ *   (sum theta^4)^(-1/4) on the kept states; and the tangents of all three.
+ * P_dot, P_new, P_dot_new: m x (m q) in the paper's layout (as
+ * ctm_get_state); omega_dot, omega_new, omega_dot_new: m entries (zero past
+ * m_eff); all host memory owned by the caller.  The handle's P and omega are
+ * not changed; its C~ buffer, Ritz block and warm start are (the next
+ * ctm_step starts its subspace iteration cold).  Allocates about 6 (m q)^2
+ * doubles of device scratch for the call.  CTM_EUNSUPPORTED for the other
+ * precision forms; CTM_ENOTCONVERGED if the subspace or the deflated
+ * iteration does not converge. */
+typedef struct {
+    double* P_new;          /* out, m x m q                                  */
+    double* omega_new;      /* out, m                                        */
+    double* P_dot_new;      /* out, m x m q                                  */
+    double* omega_dot_new;  /* out, m                                        */
+    double kappa;           /* growth factor ||P_raw||                       */
+    double kappa_dot;       /* its tangent                                   */
+    int m_eff;              /* kept states                                   */
+    int ritz_pairs;         /* Ritz pairs coupled inside the block           */
+    int deflate_iterations; /* iterations of the deflated solve              */
+    int subspace_iterations;
+} ctm_tangent_out;
+ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* omega_dot, int source,
+                            ctm_tangent_out* out);
+
 /* Derivative of the converged fixed point with respect to beta, contracted
  * with the gradient of the observables:
  *   *grad_beta = grad_obs->f df/dbeta + grad_obs->M dM/dbeta

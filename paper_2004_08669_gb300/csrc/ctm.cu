@@ -36,6 +36,7 @@
 #include "ctm_internal.cuh"
 #include "eig_f64.cuh"
 #include "oz_gemm.cuh"
+#include "tangent.cuh"
 #include "tc_gemm.cuh"
 #include "xi.cuh"
 
@@ -1545,6 +1546,222 @@ ctm_status ctm_observables(ctm_handle* h, ctm_obs* out) {
     out->steps = h->steps;
     out->converged = h->last.converged;
     return conv ? CTM_OK : fail(CTM_ENOTCONVERGED, "observables: subspace iteration reached its cap");
+}
+
+ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* omega_dot, int source,
+                            ctm_tangent_out* out) {
+    if (!h || !P_dot || !omega_dot || !out) return fail(CTM_EINVAL, "NULL argument");
+    const Layout& L = h->lay;
+    if (L.prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "the tangent step is built for the FP64 form");
+    if (!out->P_new || !out->omega_new || !out->P_dot_new || !out->omega_dot_new)
+        return fail(CTM_EINVAL, "NULL output array");
+    const int m = L.m, q = L.q, N = L.N, b = L.b;
+    if (q * q > 1024) return fail(CTM_EINVAL, "the tangent step needs q <= 32");
+    const int live = h->live;
+    const size_t d = sizeof(double), mN = (size_t)m * N, NN = (size_t)N * N;
+    // scratch: X1 (extension, before the contraction), C~, dC~, X1' (renormalisation), dX,
+    // dP (in and out), dZ / dU / dU', the eigen tangent's blocks, partial sums
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = off;
+        off = align256(off + bytes);
+        return r;
+    };
+    const size_t o_X1 = take(NN * d), o_Cs = take(NN * d), o_Cd = take(NN * d), o_X1p = take(NN * d),
+                 o_Xd = take(NN * d), o_Pd = take(mN * d), o_Pnd = take(mN * d), o_Zd = take((size_t)N * m * d),
+                 o_Ud = take((size_t)N * m * d), o_Upd = take(mN * d), o_W1 = take((size_t)N * b * d),
+                 o_HH = take((size_t)b * b * d), o_K = take((size_t)b * m * d), o_ld = take((size_t)m * d),
+                 o_od = take((size_t)m * d), o_Rhs = take((size_t)N * m * d), o_Y = take((size_t)N * m * d),
+                 o_T = take((size_t)N * m * d), o_Tz = take((size_t)b * m * d), o_res = take((size_t)b * d),
+                 o_part = take((size_t)2 * ctm::kTanParts * d);
+    char* scratch = nullptr;
+    if (cudaMalloc(&scratch, off) != cudaSuccess) return fail(CTM_ENOMEM, "cudaMalloc of the tangent scratch failed");
+    auto Dp = [&](size_t o) { return (double*)(scratch + o); };
+    double *X1s = Dp(o_X1), *Cs = Dp(o_Cs), *Cd = Dp(o_Cd), *X1p = Dp(o_X1p), *Xd = Dp(o_Xd), *Pd = Dp(o_Pd),
+           *Pnd = Dp(o_Pnd), *Zd = Dp(o_Zd), *Ud = Dp(o_Ud), *Upd = Dp(o_Upd), *W1 = Dp(o_W1), *HH = Dp(o_HH),
+           *Kc = Dp(o_K), *lamd = Dp(o_ld), *omd = Dp(o_od), *Rhs = Dp(o_Rhs), *Y = Dp(o_Y), *T = Dp(o_T),
+           *Tz = Dp(o_Tz), *res = Dp(o_res), *part = Dp(o_part);
+    cudaStream_t st = h->st;
+    auto done = [&](ctm_status s) {
+        cudaStreamSynchronize(st);
+        cudaFree(scratch);
+        h->warm = false;  // the Ritz block left behind is not aligned to anything
+        h->warm_live = -1;
+        return s;
+    };
+#define TAN_CUDA(call)                                                                                \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return done(fail(CTM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+    } while (0)
+    auto gemm = [&](bool tA, bool tB, int M, int Nn, int K, double alpha, const double* A, int lda, const double* B,
+                    int ldb, double beta, double* C, int ldc, const double* scaleK) {
+        int nk = ctm::gemm_f64(st, tA, tB, M, Nn, K, alpha, A, lda, B, ldb, beta, C, ldc, scaleK, 1, h->part, 0);
+        count_small(h, nk);
+    };
+    auto host_sum = [&](size_t n, const double* x, const double* y, double* outv) -> ctm_status {
+        ctm::dot_partial(st, n, x, y, part);
+        count_small(h, 1);
+        std::vector<double> hp(ctm::kTanParts);
+        CTM_CUDA(cudaMemcpyAsync(hp.data(), part, d * ctm::kTanParts, cudaMemcpyDeviceToHost, st));
+        CTM_CUDA(cudaStreamSynchronize(st));
+        double acc = 0.0;
+        for (double v : hp) acc += v;
+        *outv = acc;
+        return CTM_OK;
+    };
+    // input tangent in the device layout (spin-fastest columns)
+    {
+        std::vector<double> tmp(mN);
+        for (int g = 0; g < m; ++g)
+            for (int s = 0; s < q; ++s)
+                for (int a = 0; a < m; ++a)
+                    tmp[a + (size_t)m * (s + (size_t)q * g)] = P_dot[a + (size_t)m * (g + (size_t)m * s)];
+        TAN_CUDA(cudaMemcpyAsync(Pd, tmp.data(), d * mN, cudaMemcpyHostToDevice, st));
+        TAN_CUDA(cudaMemcpyAsync(omd, omega_dot, d * m, cudaMemcpyHostToDevice, st));
+        TAN_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- primal: the step of Algorithm 3 with its pieces kept -------------
+    // X1 = P^t diag(omega) P (all blocks), kept before the contraction
+    gemm(true, false, N, N, m, 1.0, h->P, m, h->P, m, 0.0, h->C, N, h->omega);
+    TAN_CUDA(cudaMemcpyAsync(X1s, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, h->C, h->E, &h->ctl->live, live, false);
+    ctm::mask_live(st, N, q, live, h->C, N);
+    TAN_CUDA(cudaMemcpyAsync(Cs, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    count_small(h, 1);
+    bool conv = false;
+    int iters = 0;
+    ctm_status s = stage_eigen(h, 400, &conv, &iters);
+    if (s != CTM_OK) return done(s);
+    if (!conv) return done(fail(CTM_ENOTCONVERGED, "tangent step: the subspace iteration did not converge"));
+    const int meff = h->hctl->meff_new;
+    if (meff < 1 || meff > m) return done(fail(CTM_ENUMERIC, "tangent step: no state kept"));
+    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, h->Z, N, h->ctl, h->U, h->Up);
+    count_small(h, 1);
+    // X1' = P^t U', X = its contraction (left in h->C), P_raw = U^t X
+    gemm(true, false, N, N, m, 1.0, h->P, m, h->Up, m, 0.0, h->C, N, nullptr);
+    TAN_CUDA(cudaMemcpyAsync(X1p, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, h->C, h->E, h->mfull, m);
+    gemm(true, false, m, N, N, 1.0, h->U, N, h->C, N, 0.0, h->Pn, m, nullptr);
+    double nrm2 = 0.0;
+    s = host_sum(mN, h->Pn, h->Pn, &nrm2);
+    if (s != CTM_OK) return done(s);
+    const double kap = sqrt(nrm2);
+    if (!(kap > 0.0) || !std::isfinite(kap)) return done(fail(CTM_ENUMERIC, "tangent step: zero or non-finite P"));
+    // Ritz values and residuals of the whole block: the eigen tangent uses
+    // the leading pairs that are eigenpairs to 1e-11 |theta_0|
+    gemm(false, false, N, b, N, 1.0, Cs, N, h->Z, N, 0.0, W1, N, nullptr);
+    ctm::resid_f64(st, N, b, W1, h->Z, N, h->theta, res);
+    count_small(h, 1);
+    std::vector<double> th(b), rs(b);
+    TAN_CUDA(cudaMemcpyAsync(th.data(), h->theta, d * b, cudaMemcpyDeviceToHost, st));
+    TAN_CUDA(cudaMemcpyAsync(rs.data(), res, d * b, cudaMemcpyDeviceToHost, st));
+    TAN_CUDA(cudaStreamSynchronize(st));
+    const double a0 = fabs(th[0]), tolc = h->cfg.tol_cluster;
+    int bt = 0;
+    while (bt < b && bt < q * live && rs[bt] <= 1e-11 * a0) ++bt;
+    while (bt > meff && bt < b && fabs(th[bt - 1] - th[bt]) <= tolc * a0) --bt;
+    if (bt < meff) return done(fail(CTM_ENOTCONVERGED, "tangent step: kept Ritz pairs not converged"));
+    // ---- tangent -----------------------------------------------------------
+    // dX1 = dP^t W P + P^t W dP + P^t dW P (W = diag(omega)), contracted,
+    // plus the contraction's own beta-derivative on X1
+    gemm(true, false, N, N, m, 1.0, Pd, m, h->P, m, 0.0, Cd, N, h->omega);
+    gemm(true, false, N, N, m, 1.0, h->P, m, Pd, m, 1.0, Cd, N, h->omega);
+    gemm(true, false, N, N, m, 1.0, h->P, m, h->P, m, 1.0, Cd, N, omd);
+    pwcontract(h, Cd, h->E, &h->ctl->live, live, false);
+    if (source) TAN_CUDA(ctm::wcontract_dbeta(st, q, live, X1s, N, h->E, h->Eh, Cd, N));
+    ctm::mask_live(st, N, q, live, Cd, N);
+    count_small(h, source ? 2 : 1);
+    // eigen tangent: in-block coupling over the bt pairs, the rest by the
+    // deflated iteration Y <- (Rhs + (I - Z Z^t) C~ Y) diag(theta)^-1
+    gemm(false, false, N, bt, N, 1.0, Cd, N, h->Z, N, 0.0, W1, N, nullptr);
+    gemm(true, false, bt, bt, N, 1.0, h->Z, N, W1, N, 0.0, HH, b, nullptr);
+    ctm::tangent_coupling(st, bt, meff, HH, b, h->theta, tolc, Kc, lamd);
+    gemm(false, false, N, meff, bt, 1.0, h->Z, N, Kc, bt, 0.0, Zd, N, nullptr);
+    TAN_CUDA(cudaMemcpyAsync(Rhs, W1, d * (size_t)N * meff, cudaMemcpyDeviceToDevice, st));
+    gemm(false, false, N, meff, bt, -1.0, h->Z, N, HH, b, 1.0, Rhs, N, nullptr);
+    TAN_CUDA(cudaMemsetAsync(Y, 0, d * (size_t)N * meff, st));
+    ctm::deflate_update(st, N, meff, Rhs, nullptr, h->theta, Y, part);
+    count_small(h, 2);
+    int dit = 0;
+    bool dconv = false;
+    std::vector<double> hp(2 * ctm::kTanParts);
+    for (dit = 1; dit <= 4000; ++dit) {
+        gemm(false, false, N, meff, N, 1.0, Cs, N, Y, N, 0.0, T, N, nullptr);
+        gemm(true, false, bt, meff, N, 1.0, h->Z, N, T, N, 0.0, Tz, bt, nullptr);
+        gemm(false, false, N, meff, bt, -1.0, h->Z, N, Tz, bt, 1.0, T, N, nullptr);
+        ctm::deflate_update(st, N, meff, Rhs, T, h->theta, Y, part);
+        count_small(h, 1);
+        if (dit % 4 == 0) {
+            TAN_CUDA(cudaMemcpyAsync(hp.data(), part, d * hp.size(), cudaMemcpyDeviceToHost, st));
+            TAN_CUDA(cudaStreamSynchronize(st));
+            double ch = 0.0, my = 0.0;
+            for (int k = 0; k < ctm::kTanParts; ++k) {
+                ch = std::max(ch, hp[2 * k]);
+                my = std::max(my, hp[2 * k + 1]);
+            }
+            if (!std::isfinite(ch) || !std::isfinite(my))
+                return done(fail(CTM_ENUMERIC, "tangent step: non-finite deflated iterate"));
+            if (ch <= 1e-14 * std::max(my, 1e-300)) {
+                dconv = true;
+                break;
+            }
+        }
+    }
+    if (!dconv) return done(fail(CTM_ENOTCONVERGED, "tangent step: the deflated iteration did not converge"));
+    ctm::add_inplace(st, (size_t)N * meff, Y, Zd);
+    TAN_CUDA(cudaMemsetAsync(Zd + (size_t)N * meff, 0, d * (size_t)N * (m - meff), st));
+    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, Zd, N, h->ctl, Ud, Upd);
+    count_small(h, 2);
+    // dX1' = dP^t U' + P^t dU', contracted, plus the contraction's beta-derivative on X1'
+    gemm(true, false, N, N, m, 1.0, Pd, m, h->Up, m, 0.0, Xd, N, nullptr);
+    gemm(true, false, N, N, m, 1.0, h->P, m, Upd, m, 1.0, Xd, N, nullptr);
+    pwcontract(h, Xd, h->E, h->mfull, m);
+    if (source) {
+        TAN_CUDA(ctm::wcontract_dbeta(st, q, m, X1p, N, h->E, h->Eh, Xd, N));
+        count_small(h, 1);
+    }
+    // dP_raw = dU^t X + U^t dX; dkappa = <P_raw, dP_raw> / kappa
+    gemm(true, false, m, N, N, 1.0, Ud, N, h->C, N, 0.0, Pnd, m, nullptr);
+    gemm(true, false, m, N, N, 1.0, h->U, N, Xd, N, 1.0, Pnd, m, nullptr);
+    double pdot = 0.0;
+    s = host_sum(mN, h->Pn, Pnd, &pdot);
+    if (s != CTM_OK) return done(s);
+    const double kdot = pdot / kap;
+    ctm::tangent_normalise(st, mN, h->Pn, Pnd, 1.0 / kap, kdot / (kap * kap), Pd);
+    count_small(h, 1);
+    // outputs in the paper's layout
+    std::vector<double> pn(mN), pdn(mN), ld(meff);
+    TAN_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, d * mN, cudaMemcpyDeviceToHost, st));
+    TAN_CUDA(cudaMemcpyAsync(pdn.data(), Pd, d * mN, cudaMemcpyDeviceToHost, st));
+    TAN_CUDA(cudaMemcpyAsync(ld.data(), lamd, d * meff, cudaMemcpyDeviceToHost, st));
+    TAN_CUDA(cudaStreamSynchronize(st));
+    for (int g = 0; g < m; ++g)
+        for (int sp = 0; sp < q; ++sp)
+            for (int a = 0; a < m; ++a) {
+                const size_t src = a + (size_t)m * (sp + (size_t)q * g), dst = a + (size_t)m * (g + (size_t)m * sp);
+                out->P_new[dst] = pn[src] / kap;
+                out->P_dot_new[dst] = pdn[src];
+            }
+    // omega_new = theta (sum theta^4)^(-1/4) over the kept states, and its tangent
+    double z4 = 0.0, z4d = 0.0;
+    for (int i = 0; i < meff; ++i) {
+        z4 += th[i] * th[i] * th[i] * th[i];
+        z4d += 4.0 * th[i] * th[i] * th[i] * ld[i];
+    }
+    const double sc = pow(z4, -0.25), scd = -0.25 * pow(z4, -1.25) * z4d;
+    for (int i = 0; i < m; ++i) {
+        out->omega_new[i] = i < meff ? th[i] * sc : 0.0;
+        out->omega_dot_new[i] = i < meff ? ld[i] * sc + th[i] * scd : 0.0;
+    }
+    out->kappa = kap;
+    out->kappa_dot = kdot;
+    out->m_eff = meff;
+    out->ritz_pairs = bt;
+    out->deflate_iterations = dit;
+    out->subspace_iterations = iters;
+#undef TAN_CUDA
+    return done(CTM_OK);
 }
 
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta) {

@@ -71,6 +71,14 @@ class ctm_xi_result(ctypes.Structure):
                 "iterations": self.iterations, "converged": self.converged}
 
 
+class ctm_tangent_out(ctypes.Structure):
+    _fields_ = [("P_new", ctypes.POINTER(ctypes.c_double)), ("omega_new", ctypes.POINTER(ctypes.c_double)),
+                ("P_dot_new", ctypes.POINTER(ctypes.c_double)), ("omega_dot_new", ctypes.POINTER(ctypes.c_double)),
+                ("kappa", ctypes.c_double), ("kappa_dot", ctypes.c_double), ("m_eff", ctypes.c_int),
+                ("ritz_pairs", ctypes.c_int), ("deflate_iterations", ctypes.c_int),
+                ("subspace_iterations", ctypes.c_int)]
+
+
 class ctm_tune_entry(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("bn", ctypes.c_int),
                 ("splits", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
@@ -99,6 +107,7 @@ def _load():
         "ctm_step_backward": [H, ctypes.POINTER(ctm_obs), _dp],
         "ctm_get_spectrum": [H, _dp],
         "ctm_xi": [H, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctm_xi_result)],
+        "ctm_tangent_step": [H, _dp, _dp, ctypes.c_int, ctypes.POINTER(ctm_tangent_out)],
         "ctm_get_state": [H, _dp, _dp, _ip],
         "ctm_set_state": [H, _dp, _dp, ctypes.c_int],
         "ctm_save": [H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
@@ -211,6 +220,24 @@ def ctm_xi(h, max_iters: int = 0, tol: float = 0.0) -> tuple:
     r = ctm_xi_result()
     st = _check(lib.ctm_xi(h, int(max_iters), float(tol), ctypes.byref(r)), (CTM_OK, CTM_ENOTCONVERGED))
     return r.to_dict(), st
+
+
+def ctm_tangent_step(h, m: int, q: int, P_dot: np.ndarray, omega_dot: np.ndarray, source: bool = True) -> dict:
+    """One step and its beta tangent from the handle's current state; arrays
+    in the paper's layout (P: m x m q, omega: m)."""
+    N = m * q
+    P_dot = np.asfortranarray(P_dot, dtype=np.float64)
+    om_dot = np.ascontiguousarray(omega_dot, dtype=np.float64)
+    if P_dot.shape != (m, N) or om_dot.shape != (m,):
+        raise ValueError("P_dot must be m x m q and omega_dot m long")
+    P_new, P_dot_new = np.zeros((m, N), order="F"), np.zeros((m, N), order="F")
+    om_new, om_dot_new = np.zeros(m), np.zeros(m)
+    r = ctm_tangent_out()
+    r.P_new, r.omega_new, r.P_dot_new, r.omega_dot_new = _dptr(P_new), _dptr(om_new), _dptr(P_dot_new), _dptr(om_dot_new)
+    _check(lib.ctm_tangent_step(h, _dptr(P_dot), _dptr(om_dot), int(bool(source)), ctypes.byref(r)))
+    return {"P_new": P_new, "omega_new": om_new, "P_dot_new": P_dot_new, "omega_dot_new": om_dot_new,
+            "kappa": r.kappa, "kappa_dot": r.kappa_dot, "m_eff": r.m_eff, "ritz_pairs": r.ritz_pairs,
+            "deflate_iterations": r.deflate_iterations, "subspace_iterations": r.subspace_iterations}
 
 
 def ctm_get_spectrum(h, m: int) -> np.ndarray:
@@ -471,6 +498,9 @@ class CTMRG:
 
     def set_state(self, P, omega, live: int):
         ctm_set_state(self.h, P, omega, live)
+
+    def tangent_step(self, P_dot, omega_dot, source: bool = True) -> dict:
+        return ctm_tangent_step(self.h, self.m, self.q, P_dot, omega_dot, source)
 
     def extend(self):
         ctm_extend(self.h)

@@ -101,4 +101,5 @@ def test_host_side_validation_of_the_newer_entry_points(built_lib):
     assert ctm.lib.ctm_xi(None, 0, 0.0, None) == ctm.CTM_EINVAL
     assert ctm.lib.ctm_tune(None, 0, None, 0, None) == ctm.CTM_EINVAL
     assert ctm.lib.ctm_scan_run(None, 1, None, None) == ctm.CTM_EINVAL
+    assert ctm.lib.ctm_tangent_step(None, None, None, 1, None) == ctm.CTM_EINVAL
     del keep
