@@ -179,12 +179,17 @@ ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* om
  *   *grad_beta = grad_obs->f df/dbeta + grad_obs->M dM/dbeta
  *              + grad_obs->u du/dbeta + grad_obs->S_E dS_E/dbeta
  * (the other fields of grad_obs are ignored), by implicit differentiation
- * of the gauge-fixed step at the current, converged state: the tangent of
- * one step (the contractions by the product rule, the leading Ritz pairs'
- * first-order perturbation with the coupling outside the Ritz block from a
- * deflated iteration, the normalisations) and the linear fixed-point
- * equation (I - J) x = d(step)/dbeta, J = d(step)/d(state).  Not built yet: returns CTM_EUNSUPPORTED
- * and leaves *grad_beta untouched. */
+ * of the gauge-fixed step at the current state: one more step whose Ritz
+ * block is rotated onto the last step's must repeat P (entries weighted by
+ * |omega| of both block legs, to 1e-8), else CTM_ENOTCONVERGED; then the
+ * linear fixed-point equation (I - J) x = d(step)/dbeta, J = d(step)/d(state),
+ * is solved by GMRES on the host (to 1e-12, at most 300 iterations) with J
+ * applied as the tangent step of ctm_tangent_step, and df/dbeta follows
+ * from the growth factor's tangent (f = -ln kappa / (2 beta)).  FP64 form
+ * only (else CTM_EUNSUPPORTED); the state must come from ctm_step (else
+ * CTM_EINVAL).  Built for the free energy: a nonzero grad_obs->M, u or S_E
+ * returns CTM_EUNSUPPORTED and leaves *grad_beta untouched.  The handle's P
+ * and omega are unchanged. */
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
 
 /* Effective correlation length (Sec. II): the leading eigenvalues of the

@@ -207,6 +207,8 @@ struct ctm_handle {
     ctm::EigWork ew;
     ctm::OaWork oa;
     long long rr_refined = 0, rr_jacobi = 0;  // Rayleigh-Ritz solves by path
+    int last_backward_iters = 0;              // GMRES iterations of the last ctm_step_backward
+    double last_backward_residual = 0.0;
     double last_resid = 0.0;                  // last Ritz residual / |w_1|
     int rr_fail_streak = 0;                   // consecutive failed refinements
     double resid_rate = 0.5;                  // measured Ritz residual reduction per iteration
@@ -1015,6 +1017,329 @@ ctm_status step_once(ctm_handle* h) {
     return conv ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
+// ------------------------------------------------- beta tangent of a step
+// Paper layout P[a + m (g + m s)] <-> device layout P[a + m (s + q g)].
+void to_device_layout(const Layout& L, const double* src, double* dst) {
+    for (int g = 0; g < L.m; ++g)
+        for (int s = 0; s < L.q; ++s)
+            for (int a = 0; a < L.m; ++a)
+                dst[a + (size_t)L.m * (s + (size_t)L.q * g)] = src[a + (size_t)L.m * (g + (size_t)L.m * s)];
+}
+
+void from_device_layout(const Layout& L, const double* src, double* dst) {
+    for (int g = 0; g < L.m; ++g)
+        for (int s = 0; s < L.q; ++s)
+            for (int a = 0; a < L.m; ++a)
+                dst[a + (size_t)L.m * (g + (size_t)L.m * s)] = src[a + (size_t)L.m * (s + (size_t)L.q * g)];
+}
+
+// Scratch and the primal pieces of one step, kept for any number of tangents.
+struct TanCtx {
+    char* scratch = nullptr;
+    double *X1s = nullptr, *Cs = nullptr, *Cd = nullptr, *X1p = nullptr, *Xd = nullptr, *Pd = nullptr,
+           *Pnd = nullptr, *Zd = nullptr, *Ud = nullptr, *Upd = nullptr, *W1 = nullptr, *HH = nullptr,
+           *Kc = nullptr, *lamd = nullptr, *omd = nullptr, *Rhs = nullptr, *Y = nullptr, *T = nullptr,
+           *Tz = nullptr, *res = nullptr, *part = nullptr;
+    int meff = 0, bt = 0, iters = 0, live = 0, deflate_iters = 0;
+    double kap = 0.0, sc = 0.0, z4 = 0.0;
+    std::vector<double> th;
+};
+
+ctm_status tan_alloc(ctm_handle* h, TanCtx& c) {
+    const Layout& L = h->lay;
+    const int m = L.m, N = L.N, b = L.b;
+    if (L.q * L.q > 1024) return fail(CTM_EINVAL, "the tangent step needs q <= 32");
+    const size_t d = sizeof(double), mN = (size_t)m * N, NN = (size_t)N * N;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = off;
+        off = align256(off + bytes);
+        return r;
+    };
+    const size_t o_X1 = take(NN * d), o_Cs = take(NN * d), o_Cd = take(NN * d), o_X1p = take(NN * d),
+                 o_Xd = take(NN * d), o_Pd = take(mN * d), o_Pnd = take(mN * d), o_Zd = take((size_t)N * m * d),
+                 o_Ud = take((size_t)N * m * d), o_Upd = take(mN * d), o_W1 = take((size_t)N * b * d),
+                 o_HH = take((size_t)b * b * d), o_K = take((size_t)b * m * d), o_ld = take((size_t)m * d),
+                 o_od = take((size_t)m * d), o_Rhs = take((size_t)N * m * d), o_Y = take((size_t)N * m * d),
+                 o_T = take((size_t)N * m * d), o_Tz = take((size_t)b * m * d), o_res = take((size_t)b * d),
+                 o_part = take((size_t)2 * ctm::kTanParts * d);
+    if (cudaMalloc(&c.scratch, off) != cudaSuccess) {
+        c.scratch = nullptr;
+        return fail(CTM_ENOMEM, "cudaMalloc of the tangent scratch failed");
+    }
+    auto Dp = [&](size_t o) { return (double*)(c.scratch + o); };
+    c.X1s = Dp(o_X1);
+    c.Cs = Dp(o_Cs);
+    c.Cd = Dp(o_Cd);
+    c.X1p = Dp(o_X1p);
+    c.Xd = Dp(o_Xd);
+    c.Pd = Dp(o_Pd);
+    c.Pnd = Dp(o_Pnd);
+    c.Zd = Dp(o_Zd);
+    c.Ud = Dp(o_Ud);
+    c.Upd = Dp(o_Upd);
+    c.W1 = Dp(o_W1);
+    c.HH = Dp(o_HH);
+    c.Kc = Dp(o_K);
+    c.lamd = Dp(o_ld);
+    c.omd = Dp(o_od);
+    c.Rhs = Dp(o_Rhs);
+    c.Y = Dp(o_Y);
+    c.T = Dp(o_T);
+    c.Tz = Dp(o_Tz);
+    c.res = Dp(o_res);
+    c.part = Dp(o_part);
+    return CTM_OK;
+}
+
+void tan_free(ctm_handle* h, TanCtx& c) {
+    cudaStreamSynchronize(h->st);
+    if (c.scratch) cudaFree(c.scratch);
+    c.scratch = nullptr;
+}
+
+void tan_gemm(ctm_handle* h, bool tA, bool tB, int M, int Nn, int K, double alpha, const double* A, int lda,
+              const double* B, int ldb, double beta, double* C, int ldc, const double* scaleK) {
+    int nk = ctm::gemm_f64(h->st, tA, tB, M, Nn, K, alpha, A, lda, B, ldb, beta, C, ldc, scaleK, 1, h->part, 0);
+    count_small(h, nk);
+}
+
+ctm_status tan_sum(ctm_handle* h, TanCtx& c, size_t n, const double* x, const double* y, double* outv) {
+    ctm::dot_partial(h->st, n, x, y, c.part);
+    count_small(h, 1);
+    std::vector<double> hp(ctm::kTanParts);
+    CTM_CUDA(cudaMemcpyAsync(hp.data(), c.part, sizeof(double) * ctm::kTanParts, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    double acc = 0.0;
+    for (double v : hp) acc += v;
+    *outv = acc;
+    return CTM_OK;
+}
+
+// The primal pieces of one step of Algorithm 3 at the handle's (P, omega):
+// X1 (before its contraction), C~ (live block), the Ritz block (warm and
+// rotated onto the last step's if the handle is warm), U, U', X1', X (left
+// in h->C), P_raw (h->Pn) and kappa = ||P_raw||.
+ctm_status tan_prepare(ctm_handle* h, TanCtx& c) {
+    const Layout& L = h->lay;
+    const int m = L.m, q = L.q, N = L.N, b = L.b;
+    const size_t d = sizeof(double), mN = (size_t)m * N, NN = (size_t)N * N;
+    cudaStream_t st = h->st;
+    c.live = h->live;
+    tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, h->P, m, 0.0, h->C, N, h->omega);
+    CTM_CUDA(cudaMemcpyAsync(c.X1s, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, h->C, h->E, &h->ctl->live, c.live, false);
+    ctm::mask_live(st, N, q, c.live, h->C, N);
+    CTM_CUDA(cudaMemcpyAsync(c.Cs, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    count_small(h, 1);
+    bool conv = false;
+    ctm_status s = stage_eigen(h, 400, &conv, &c.iters);
+    if (s != CTM_OK) return s;
+    if (!conv) return fail(CTM_ENOTCONVERGED, "tangent step: the subspace iteration did not converge");
+    c.meff = h->hctl->meff_new;
+    if (c.meff < 1 || c.meff > m) return fail(CTM_ENUMERIC, "tangent step: no state kept");
+    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, h->Z, N, h->ctl, h->U, h->Up);
+    count_small(h, 1);
+    tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, h->Up, m, 0.0, h->C, N, nullptr);
+    CTM_CUDA(cudaMemcpyAsync(c.X1p, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, h->C, h->E, h->mfull, m);
+    tan_gemm(h, true, false, m, N, N, 1.0, h->U, N, h->C, N, 0.0, h->Pn, m, nullptr);
+    double nrm2 = 0.0;
+    s = tan_sum(h, c, mN, h->Pn, h->Pn, &nrm2);
+    if (s != CTM_OK) return s;
+    c.kap = sqrt(nrm2);
+    if (!(c.kap > 0.0) || !std::isfinite(c.kap)) return fail(CTM_ENUMERIC, "tangent step: zero or non-finite P");
+    // Ritz values and residuals of the whole block: the eigen tangent couples
+    // the leading pairs that are eigenpairs to 1e-11 |theta_0|
+    tan_gemm(h, false, false, N, b, N, 1.0, c.Cs, N, h->Z, N, 0.0, c.W1, N, nullptr);
+    ctm::resid_f64(st, N, b, c.W1, h->Z, N, h->theta, c.res);
+    count_small(h, 1);
+    c.th.assign(b, 0.0);
+    std::vector<double> rs(b);
+    CTM_CUDA(cudaMemcpyAsync(c.th.data(), h->theta, d * b, cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaMemcpyAsync(rs.data(), c.res, d * b, cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    const double a0 = fabs(c.th[0]), tolc = h->cfg.tol_cluster;
+    int bt = 0;
+    while (bt < b && bt < q * c.live && rs[bt] <= 1e-11 * a0) ++bt;
+    while (bt > c.meff && bt < b && fabs(c.th[bt - 1] - c.th[bt]) <= tolc * a0) --bt;
+    if (bt < c.meff) return fail(CTM_ENOTCONVERGED, "tangent step: kept Ritz pairs not converged");
+    c.bt = bt;
+    c.z4 = 0.0;
+    for (int i = 0; i < c.meff; ++i) c.z4 += c.th[i] * c.th[i] * c.th[i] * c.th[i];
+    c.sc = pow(c.z4, -0.25);
+    return CTM_OK;
+}
+
+// Input tangent (device layout P_dot, m entries of omega_dot) from the host.
+ctm_status tan_upload(ctm_handle* h, TanCtx& c, const double* P_dot_dev_layout, const double* omega_dot) {
+    const Layout& L = h->lay;
+    CTM_CUDA(cudaMemcpyAsync(c.Pd, P_dot_dev_layout, sizeof(double) * L.m * L.N, cudaMemcpyHostToDevice, h->st));
+    CTM_CUDA(cudaMemcpyAsync(c.omd, omega_dot, sizeof(double) * L.m, cudaMemcpyHostToDevice, h->st));
+    return CTM_OK;
+}
+
+// One tangent of the prepared step along (c.Pd, c.omd) and, with source, W's
+// own beta dependence.  Leaves the new P tangent in c.Pd (device layout),
+// the new omega tangent in omega_dot_new (m entries) and kappa's in kdot.
+ctm_status tan_apply(ctm_handle* h, TanCtx& c, bool source, double* kdot, std::vector<double>* omega_dot_new) {
+    const Layout& L = h->lay;
+    const int m = L.m, q = L.q, N = L.N, b = L.b, meff = c.meff, bt = c.bt;
+    const size_t d = sizeof(double), mN = (size_t)m * N;
+    cudaStream_t st = h->st;
+    const double tolc = h->cfg.tol_cluster;
+    // dX1 = dP^t W P + P^t W dP + P^t dW P (W = diag(omega)), contracted,
+    // plus the contraction's own beta-derivative on X1
+    tan_gemm(h, true, false, N, N, m, 1.0, c.Pd, m, h->P, m, 0.0, c.Cd, N, h->omega);
+    tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, c.Pd, m, 1.0, c.Cd, N, h->omega);
+    tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, h->P, m, 1.0, c.Cd, N, c.omd);
+    pwcontract(h, c.Cd, h->E, &h->ctl->live, c.live, false);
+    if (source) CTM_CUDA(ctm::wcontract_dbeta(st, q, c.live, c.X1s, N, h->E, h->Eh, c.Cd, N));
+    ctm::mask_live(st, N, q, c.live, c.Cd, N);
+    count_small(h, source ? 2 : 1);
+    // eigen tangent: in-block coupling over the bt pairs, the rest by the
+    // deflated iteration Y <- (Rhs + (I - Z Z^t) C~ Y) diag(theta)^-1
+    tan_gemm(h, false, false, N, bt, N, 1.0, c.Cd, N, h->Z, N, 0.0, c.W1, N, nullptr);
+    tan_gemm(h, true, false, bt, bt, N, 1.0, h->Z, N, c.W1, N, 0.0, c.HH, b, nullptr);
+    ctm::tangent_coupling(st, bt, meff, c.HH, b, h->theta, tolc, c.Kc, c.lamd);
+    tan_gemm(h, false, false, N, meff, bt, 1.0, h->Z, N, c.Kc, bt, 0.0, c.Zd, N, nullptr);
+    CTM_CUDA(cudaMemcpyAsync(c.Rhs, c.W1, d * (size_t)N * meff, cudaMemcpyDeviceToDevice, st));
+    tan_gemm(h, false, false, N, meff, bt, -1.0, h->Z, N, c.HH, b, 1.0, c.Rhs, N, nullptr);
+    CTM_CUDA(cudaMemsetAsync(c.Y, 0, d * (size_t)N * meff, st));
+    ctm::deflate_update(st, N, meff, c.Rhs, nullptr, h->theta, c.Y, c.part);
+    count_small(h, 2);
+    int dit = 0;
+    bool dconv = false;
+    std::vector<double> hp(2 * ctm::kTanParts);
+    for (dit = 1; dit <= 4000; ++dit) {
+        tan_gemm(h, false, false, N, meff, N, 1.0, c.Cs, N, c.Y, N, 0.0, c.T, N, nullptr);
+        tan_gemm(h, true, false, bt, meff, N, 1.0, h->Z, N, c.T, N, 0.0, c.Tz, bt, nullptr);
+        tan_gemm(h, false, false, N, meff, bt, -1.0, h->Z, N, c.Tz, bt, 1.0, c.T, N, nullptr);
+        ctm::deflate_update(st, N, meff, c.Rhs, c.T, h->theta, c.Y, c.part);
+        count_small(h, 1);
+        if (dit % 4 == 0) {
+            CTM_CUDA(cudaMemcpyAsync(hp.data(), c.part, d * hp.size(), cudaMemcpyDeviceToHost, st));
+            CTM_CUDA(cudaStreamSynchronize(st));
+            double ch = 0.0, my = 0.0;
+            for (int k = 0; k < ctm::kTanParts; ++k) {
+                ch = std::max(ch, hp[2 * k]);
+                my = std::max(my, hp[2 * k + 1]);
+            }
+            if (!std::isfinite(ch) || !std::isfinite(my))
+                return fail(CTM_ENUMERIC, "tangent step: non-finite deflated iterate");
+            if (ch <= 1e-14 * std::max(my, 1e-300)) {
+                dconv = true;
+                break;
+            }
+        }
+    }
+    if (!dconv) return fail(CTM_ENOTCONVERGED, "tangent step: the deflated iteration did not converge");
+    c.deflate_iters = dit;
+    ctm::add_inplace(st, (size_t)N * meff, c.Y, c.Zd);
+    CTM_CUDA(cudaMemsetAsync(c.Zd + (size_t)N * meff, 0, d * (size_t)N * (m - meff), st));
+    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, c.Zd, N, h->ctl, c.Ud, c.Upd);
+    count_small(h, 2);
+    // dX1' = dP^t U' + P^t dU', contracted, plus the contraction's beta-derivative on X1'
+    tan_gemm(h, true, false, N, N, m, 1.0, c.Pd, m, h->Up, m, 0.0, c.Xd, N, nullptr);
+    tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, c.Upd, m, 1.0, c.Xd, N, nullptr);
+    pwcontract(h, c.Xd, h->E, h->mfull, m);
+    if (source) {
+        CTM_CUDA(ctm::wcontract_dbeta(st, q, m, c.X1p, N, h->E, h->Eh, c.Xd, N));
+        count_small(h, 1);
+    }
+    // dP_raw = dU^t X + U^t dX; dkappa = <P_raw, dP_raw> / kappa
+    tan_gemm(h, true, false, m, N, N, 1.0, c.Ud, N, h->C, N, 0.0, c.Pnd, m, nullptr);
+    tan_gemm(h, true, false, m, N, N, 1.0, h->U, N, c.Xd, N, 1.0, c.Pnd, m, nullptr);
+    double pdot = 0.0;
+    ctm_status s = tan_sum(h, c, mN, h->Pn, c.Pnd, &pdot);
+    if (s != CTM_OK) return s;
+    *kdot = pdot / c.kap;
+    ctm::tangent_normalise(st, mN, h->Pn, c.Pnd, 1.0 / c.kap, *kdot / (c.kap * c.kap), c.Pd);
+    count_small(h, 1);
+    // omega_new = theta (sum theta^4)^(-1/4) on the kept states, and its tangent
+    std::vector<double> ld(meff);
+    CTM_CUDA(cudaMemcpyAsync(ld.data(), c.lamd, d * meff, cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    double z4d = 0.0;
+    for (int i = 0; i < meff; ++i) z4d += 4.0 * c.th[i] * c.th[i] * c.th[i] * ld[i];
+    const double scd = -0.25 * pow(c.z4, -1.25) * z4d;
+    omega_dot_new->assign(m, 0.0);
+    for (int i = 0; i < meff; ++i) (*omega_dot_new)[i] = ld[i] * c.sc + c.th[i] * scd;
+    return CTM_OK;
+}
+
+// GMRES without restarts on the host (Arnoldi with modified Gram-Schmidt
+// applied twice, Givens rotations for the small least-squares problem):
+// solve op(x) = rhs to a relative residual tol.
+template <class Op>
+ctm_status host_gmres(Op op, const std::vector<double>& rhs, std::vector<double>& x, double tol, int max_iter,
+                      int* iters, double* rel_res) {
+    const size_t n = rhs.size();
+    double b0 = 0.0;
+    for (double v : rhs) b0 += v * v;
+    b0 = std::sqrt(b0);
+    x.assign(n, 0.0);
+    *iters = 0;
+    *rel_res = 0.0;
+    if (b0 == 0.0) return CTM_OK;
+    std::vector<std::vector<double>> V(1, std::vector<double>(n));
+    for (size_t i = 0; i < n; ++i) V[0][i] = rhs[i] / b0;
+    std::vector<std::vector<double>> H;  // columns of the Hessenberg matrix
+    std::vector<double> cs, sn, g(1, b0), w(n);
+    int k = 0;
+    double res = 1.0;
+    for (k = 0; k < max_iter; ++k) {
+        ctm_status s = op(V[k], w);
+        if (s != CTM_OK) return s;
+        std::vector<double> hk(k + 2, 0.0);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j <= k; ++j) {
+                double hj = 0.0;
+                for (size_t i = 0; i < n; ++i) hj += V[j][i] * w[i];
+                hk[j] += hj;
+                for (size_t i = 0; i < n; ++i) w[i] -= hj * V[j][i];
+            }
+        double nw = 0.0;
+        for (double v : w) nw += v * v;
+        nw = std::sqrt(nw);
+        hk[k + 1] = nw;
+        for (int j = 0; j < k; ++j) {  // earlier rotations
+            const double t = cs[j] * hk[j] + sn[j] * hk[j + 1];
+            hk[j + 1] = -sn[j] * hk[j] + cs[j] * hk[j + 1];
+            hk[j] = t;
+        }
+        const double r = std::hypot(hk[k], hk[k + 1]);
+        const double ck = r > 0.0 ? hk[k] / r : 1.0, sk = r > 0.0 ? hk[k + 1] / r : 0.0;
+        cs.push_back(ck);
+        sn.push_back(sk);
+        hk[k] = r;
+        hk[k + 1] = 0.0;
+        g.push_back(-sk * g[k]);
+        g[k] = ck * g[k];
+        H.push_back(hk);
+        res = std::fabs(g[k + 1]) / b0;
+        if (res <= tol || nw == 0.0) {
+            ++k;
+            break;
+        }
+        V.emplace_back(n);
+        for (size_t i = 0; i < n; ++i) V[k + 1][i] = w[i] / nw;
+    }
+    if (res > tol) return fail(CTM_ENOTCONVERGED, "ctm_step_backward: GMRES did not converge");
+    // back substitution for y, x = V y
+    std::vector<double> y(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= H[j][i] * y[j];
+        y[i] = acc / H[i][i];
+    }
+    for (int j = 0; j < k; ++j)
+        for (size_t i = 0; i < n; ++i) x[i] += y[j] * V[j][i];
+    *iters = k;
+    *rel_res = res;
+    return CTM_OK;
+}
+
 }  // namespace
 
 // ================================================================ C-ABI
@@ -1551,224 +1876,138 @@ ctm_status ctm_observables(ctm_handle* h, ctm_obs* out) {
 ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* omega_dot, int source,
                             ctm_tangent_out* out) {
     if (!h || !P_dot || !omega_dot || !out) return fail(CTM_EINVAL, "NULL argument");
-    const Layout& L = h->lay;
-    if (L.prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "the tangent step is built for the FP64 form");
+    if (h->lay.prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "the tangent step is built for the FP64 form");
     if (!out->P_new || !out->omega_new || !out->P_dot_new || !out->omega_dot_new)
         return fail(CTM_EINVAL, "NULL output array");
-    const int m = L.m, q = L.q, N = L.N, b = L.b;
-    if (q * q > 1024) return fail(CTM_EINVAL, "the tangent step needs q <= 32");
-    const int live = h->live;
-    const size_t d = sizeof(double), mN = (size_t)m * N, NN = (size_t)N * N;
-    // scratch: X1 (extension, before the contraction), C~, dC~, X1' (renormalisation), dX,
-    // dP (in and out), dZ / dU / dU', the eigen tangent's blocks, partial sums
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = off;
-        off = align256(off + bytes);
-        return r;
-    };
-    const size_t o_X1 = take(NN * d), o_Cs = take(NN * d), o_Cd = take(NN * d), o_X1p = take(NN * d),
-                 o_Xd = take(NN * d), o_Pd = take(mN * d), o_Pnd = take(mN * d), o_Zd = take((size_t)N * m * d),
-                 o_Ud = take((size_t)N * m * d), o_Upd = take(mN * d), o_W1 = take((size_t)N * b * d),
-                 o_HH = take((size_t)b * b * d), o_K = take((size_t)b * m * d), o_ld = take((size_t)m * d),
-                 o_od = take((size_t)m * d), o_Rhs = take((size_t)N * m * d), o_Y = take((size_t)N * m * d),
-                 o_T = take((size_t)N * m * d), o_Tz = take((size_t)b * m * d), o_res = take((size_t)b * d),
-                 o_part = take((size_t)2 * ctm::kTanParts * d);
-    char* scratch = nullptr;
-    if (cudaMalloc(&scratch, off) != cudaSuccess) return fail(CTM_ENOMEM, "cudaMalloc of the tangent scratch failed");
-    auto Dp = [&](size_t o) { return (double*)(scratch + o); };
-    double *X1s = Dp(o_X1), *Cs = Dp(o_Cs), *Cd = Dp(o_Cd), *X1p = Dp(o_X1p), *Xd = Dp(o_Xd), *Pd = Dp(o_Pd),
-           *Pnd = Dp(o_Pnd), *Zd = Dp(o_Zd), *Ud = Dp(o_Ud), *Upd = Dp(o_Upd), *W1 = Dp(o_W1), *HH = Dp(o_HH),
-           *Kc = Dp(o_K), *lamd = Dp(o_ld), *omd = Dp(o_od), *Rhs = Dp(o_Rhs), *Y = Dp(o_Y), *T = Dp(o_T),
-           *Tz = Dp(o_Tz), *res = Dp(o_res), *part = Dp(o_part);
-    cudaStream_t st = h->st;
-    auto done = [&](ctm_status s) {
-        cudaStreamSynchronize(st);
-        cudaFree(scratch);
+    const Layout& L = h->lay;
+    const int m = L.m, q = L.q;
+    TanCtx c;
+    ctm_status s = tan_alloc(h, c);
+    if (s != CTM_OK) return s;
+    auto done = [&](ctm_status st) {
+        tan_free(h, c);
         h->warm = false;  // the Ritz block left behind is not aligned to anything
         h->warm_live = -1;
-        return s;
+        return st;
     };
-#define TAN_CUDA(call)                                                                                \
-    do {                                                                                              \
-        cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess) return done(fail(CTM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
-    } while (0)
-    auto gemm = [&](bool tA, bool tB, int M, int Nn, int K, double alpha, const double* A, int lda, const double* B,
-                    int ldb, double beta, double* C, int ldc, const double* scaleK) {
-        int nk = ctm::gemm_f64(st, tA, tB, M, Nn, K, alpha, A, lda, B, ldb, beta, C, ldc, scaleK, 1, h->part, 0);
-        count_small(h, nk);
-    };
-    auto host_sum = [&](size_t n, const double* x, const double* y, double* outv) -> ctm_status {
-        ctm::dot_partial(st, n, x, y, part);
-        count_small(h, 1);
-        std::vector<double> hp(ctm::kTanParts);
-        CTM_CUDA(cudaMemcpyAsync(hp.data(), part, d * ctm::kTanParts, cudaMemcpyDeviceToHost, st));
-        CTM_CUDA(cudaStreamSynchronize(st));
-        double acc = 0.0;
-        for (double v : hp) acc += v;
-        *outv = acc;
-        return CTM_OK;
-    };
-    // input tangent in the device layout (spin-fastest columns)
-    {
-        std::vector<double> tmp(mN);
-        for (int g = 0; g < m; ++g)
-            for (int s = 0; s < q; ++s)
-                for (int a = 0; a < m; ++a)
-                    tmp[a + (size_t)m * (s + (size_t)q * g)] = P_dot[a + (size_t)m * (g + (size_t)m * s)];
-        TAN_CUDA(cudaMemcpyAsync(Pd, tmp.data(), d * mN, cudaMemcpyHostToDevice, st));
-        TAN_CUDA(cudaMemcpyAsync(omd, omega_dot, d * m, cudaMemcpyHostToDevice, st));
-        TAN_CUDA(cudaStreamSynchronize(st));
-    }
-    // ---- primal: the step of Algorithm 3 with its pieces kept -------------
-    // X1 = P^t diag(omega) P (all blocks), kept before the contraction
-    gemm(true, false, N, N, m, 1.0, h->P, m, h->P, m, 0.0, h->C, N, h->omega);
-    TAN_CUDA(cudaMemcpyAsync(X1s, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
-    pwcontract(h, h->C, h->E, &h->ctl->live, live, false);
-    ctm::mask_live(st, N, q, live, h->C, N);
-    TAN_CUDA(cudaMemcpyAsync(Cs, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
-    count_small(h, 1);
-    bool conv = false;
-    int iters = 0;
-    ctm_status s = stage_eigen(h, 400, &conv, &iters);
+    h->warm = false;  // a cold subspace iteration: the output basis is the eigensolver's own
+    s = tan_prepare(h, c);
     if (s != CTM_OK) return done(s);
-    if (!conv) return done(fail(CTM_ENOTCONVERGED, "tangent step: the subspace iteration did not converge"));
-    const int meff = h->hctl->meff_new;
-    if (meff < 1 || meff > m) return done(fail(CTM_ENUMERIC, "tangent step: no state kept"));
-    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, h->Z, N, h->ctl, h->U, h->Up);
-    count_small(h, 1);
-    // X1' = P^t U', X = its contraction (left in h->C), P_raw = U^t X
-    gemm(true, false, N, N, m, 1.0, h->P, m, h->Up, m, 0.0, h->C, N, nullptr);
-    TAN_CUDA(cudaMemcpyAsync(X1p, h->C, d * NN, cudaMemcpyDeviceToDevice, st));
-    pwcontract(h, h->C, h->E, h->mfull, m);
-    gemm(true, false, m, N, N, 1.0, h->U, N, h->C, N, 0.0, h->Pn, m, nullptr);
-    double nrm2 = 0.0;
-    s = host_sum(mN, h->Pn, h->Pn, &nrm2);
+    std::vector<double> pin((size_t)m * L.N);
+    to_device_layout(L, P_dot, pin.data());
+    s = tan_upload(h, c, pin.data(), omega_dot);
     if (s != CTM_OK) return done(s);
-    const double kap = sqrt(nrm2);
-    if (!(kap > 0.0) || !std::isfinite(kap)) return done(fail(CTM_ENUMERIC, "tangent step: zero or non-finite P"));
-    // Ritz values and residuals of the whole block: the eigen tangent uses
-    // the leading pairs that are eigenpairs to 1e-11 |theta_0|
-    gemm(false, false, N, b, N, 1.0, Cs, N, h->Z, N, 0.0, W1, N, nullptr);
-    ctm::resid_f64(st, N, b, W1, h->Z, N, h->theta, res);
-    count_small(h, 1);
-    std::vector<double> th(b), rs(b);
-    TAN_CUDA(cudaMemcpyAsync(th.data(), h->theta, d * b, cudaMemcpyDeviceToHost, st));
-    TAN_CUDA(cudaMemcpyAsync(rs.data(), res, d * b, cudaMemcpyDeviceToHost, st));
-    TAN_CUDA(cudaStreamSynchronize(st));
-    const double a0 = fabs(th[0]), tolc = h->cfg.tol_cluster;
-    int bt = 0;
-    while (bt < b && bt < q * live && rs[bt] <= 1e-11 * a0) ++bt;
-    while (bt > meff && bt < b && fabs(th[bt - 1] - th[bt]) <= tolc * a0) --bt;
-    if (bt < meff) return done(fail(CTM_ENOTCONVERGED, "tangent step: kept Ritz pairs not converged"));
-    // ---- tangent -----------------------------------------------------------
-    // dX1 = dP^t W P + P^t W dP + P^t dW P (W = diag(omega)), contracted,
-    // plus the contraction's own beta-derivative on X1
-    gemm(true, false, N, N, m, 1.0, Pd, m, h->P, m, 0.0, Cd, N, h->omega);
-    gemm(true, false, N, N, m, 1.0, h->P, m, Pd, m, 1.0, Cd, N, h->omega);
-    gemm(true, false, N, N, m, 1.0, h->P, m, h->P, m, 1.0, Cd, N, omd);
-    pwcontract(h, Cd, h->E, &h->ctl->live, live, false);
-    if (source) TAN_CUDA(ctm::wcontract_dbeta(st, q, live, X1s, N, h->E, h->Eh, Cd, N));
-    ctm::mask_live(st, N, q, live, Cd, N);
-    count_small(h, source ? 2 : 1);
-    // eigen tangent: in-block coupling over the bt pairs, the rest by the
-    // deflated iteration Y <- (Rhs + (I - Z Z^t) C~ Y) diag(theta)^-1
-    gemm(false, false, N, bt, N, 1.0, Cd, N, h->Z, N, 0.0, W1, N, nullptr);
-    gemm(true, false, bt, bt, N, 1.0, h->Z, N, W1, N, 0.0, HH, b, nullptr);
-    ctm::tangent_coupling(st, bt, meff, HH, b, h->theta, tolc, Kc, lamd);
-    gemm(false, false, N, meff, bt, 1.0, h->Z, N, Kc, bt, 0.0, Zd, N, nullptr);
-    TAN_CUDA(cudaMemcpyAsync(Rhs, W1, d * (size_t)N * meff, cudaMemcpyDeviceToDevice, st));
-    gemm(false, false, N, meff, bt, -1.0, h->Z, N, HH, b, 1.0, Rhs, N, nullptr);
-    TAN_CUDA(cudaMemsetAsync(Y, 0, d * (size_t)N * meff, st));
-    ctm::deflate_update(st, N, meff, Rhs, nullptr, h->theta, Y, part);
-    count_small(h, 2);
-    int dit = 0;
-    bool dconv = false;
-    std::vector<double> hp(2 * ctm::kTanParts);
-    for (dit = 1; dit <= 4000; ++dit) {
-        gemm(false, false, N, meff, N, 1.0, Cs, N, Y, N, 0.0, T, N, nullptr);
-        gemm(true, false, bt, meff, N, 1.0, h->Z, N, T, N, 0.0, Tz, bt, nullptr);
-        gemm(false, false, N, meff, bt, -1.0, h->Z, N, Tz, bt, 1.0, T, N, nullptr);
-        ctm::deflate_update(st, N, meff, Rhs, T, h->theta, Y, part);
-        count_small(h, 1);
-        if (dit % 4 == 0) {
-            TAN_CUDA(cudaMemcpyAsync(hp.data(), part, d * hp.size(), cudaMemcpyDeviceToHost, st));
-            TAN_CUDA(cudaStreamSynchronize(st));
-            double ch = 0.0, my = 0.0;
-            for (int k = 0; k < ctm::kTanParts; ++k) {
-                ch = std::max(ch, hp[2 * k]);
-                my = std::max(my, hp[2 * k + 1]);
-            }
-            if (!std::isfinite(ch) || !std::isfinite(my))
-                return done(fail(CTM_ENUMERIC, "tangent step: non-finite deflated iterate"));
-            if (ch <= 1e-14 * std::max(my, 1e-300)) {
-                dconv = true;
-                break;
-            }
-        }
-    }
-    if (!dconv) return done(fail(CTM_ENOTCONVERGED, "tangent step: the deflated iteration did not converge"));
-    ctm::add_inplace(st, (size_t)N * meff, Y, Zd);
-    TAN_CUDA(cudaMemsetAsync(Zd + (size_t)N * meff, 0, d * (size_t)N * (m - meff), st));
-    k_make_U<<<grid_for(mN), 256, 0, st>>>(N, m, q, Zd, N, h->ctl, Ud, Upd);
-    count_small(h, 2);
-    // dX1' = dP^t U' + P^t dU', contracted, plus the contraction's beta-derivative on X1'
-    gemm(true, false, N, N, m, 1.0, Pd, m, h->Up, m, 0.0, Xd, N, nullptr);
-    gemm(true, false, N, N, m, 1.0, h->P, m, Upd, m, 1.0, Xd, N, nullptr);
-    pwcontract(h, Xd, h->E, h->mfull, m);
-    if (source) {
-        TAN_CUDA(ctm::wcontract_dbeta(st, q, m, X1p, N, h->E, h->Eh, Xd, N));
-        count_small(h, 1);
-    }
-    // dP_raw = dU^t X + U^t dX; dkappa = <P_raw, dP_raw> / kappa
-    gemm(true, false, m, N, N, 1.0, Ud, N, h->C, N, 0.0, Pnd, m, nullptr);
-    gemm(true, false, m, N, N, 1.0, h->U, N, Xd, N, 1.0, Pnd, m, nullptr);
-    double pdot = 0.0;
-    s = host_sum(mN, h->Pn, Pnd, &pdot);
+    double kdot = 0.0;
+    std::vector<double> odn;
+    s = tan_apply(h, c, source != 0, &kdot, &odn);
     if (s != CTM_OK) return done(s);
-    const double kdot = pdot / kap;
-    ctm::tangent_normalise(st, mN, h->Pn, Pnd, 1.0 / kap, kdot / (kap * kap), Pd);
-    count_small(h, 1);
-    // outputs in the paper's layout
-    std::vector<double> pn(mN), pdn(mN), ld(meff);
-    TAN_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, d * mN, cudaMemcpyDeviceToHost, st));
-    TAN_CUDA(cudaMemcpyAsync(pdn.data(), Pd, d * mN, cudaMemcpyDeviceToHost, st));
-    TAN_CUDA(cudaMemcpyAsync(ld.data(), lamd, d * meff, cudaMemcpyDeviceToHost, st));
-    TAN_CUDA(cudaStreamSynchronize(st));
-    for (int g = 0; g < m; ++g)
-        for (int sp = 0; sp < q; ++sp)
-            for (int a = 0; a < m; ++a) {
-                const size_t src = a + (size_t)m * (sp + (size_t)q * g), dst = a + (size_t)m * (g + (size_t)m * sp);
-                out->P_new[dst] = pn[src] / kap;
-                out->P_dot_new[dst] = pdn[src];
-            }
-    // omega_new = theta (sum theta^4)^(-1/4) over the kept states, and its tangent
-    double z4 = 0.0, z4d = 0.0;
-    for (int i = 0; i < meff; ++i) {
-        z4 += th[i] * th[i] * th[i] * th[i];
-        z4d += 4.0 * th[i] * th[i] * th[i] * ld[i];
-    }
-    const double sc = pow(z4, -0.25), scd = -0.25 * pow(z4, -1.25) * z4d;
+    std::vector<double> pn((size_t)m * L.N), pdn((size_t)m * L.N);
+    CTM_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * pn.size(), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaMemcpyAsync(pdn.data(), c.Pd, sizeof(double) * pdn.size(), cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    for (double& v : pn) v /= c.kap;
+    from_device_layout(L, pn.data(), out->P_new);
+    from_device_layout(L, pdn.data(), out->P_dot_new);
     for (int i = 0; i < m; ++i) {
-        out->omega_new[i] = i < meff ? th[i] * sc : 0.0;
-        out->omega_dot_new[i] = i < meff ? ld[i] * sc + th[i] * scd : 0.0;
+        out->omega_new[i] = i < c.meff ? c.th[i] * c.sc : 0.0;
+        out->omega_dot_new[i] = odn[i];
     }
-    out->kappa = kap;
+    (void)q;
+    out->kappa = c.kap;
     out->kappa_dot = kdot;
-    out->m_eff = meff;
-    out->ritz_pairs = bt;
-    out->deflate_iterations = dit;
-    out->subspace_iterations = iters;
-#undef TAN_CUDA
+    out->m_eff = c.meff;
+    out->ritz_pairs = c.bt;
+    out->deflate_iterations = c.deflate_iters;
+    out->subspace_iterations = c.iters;
     return done(CTM_OK);
 }
 
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta) {
-    (void)h;
-    (void)grad_obs;
-    (void)grad_beta;
-    return fail(CTM_EUNSUPPORTED, "ctm_step_backward is not built yet");
+    if (!h || !grad_obs || !grad_beta) return fail(CTM_EINVAL, "NULL argument");
+    if (h->lay.prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "the backward step is built for the FP64 form");
+    if (grad_obs->M != 0.0 || grad_obs->u != 0.0 || grad_obs->S_E != 0.0)
+        return fail(CTM_EUNSUPPORTED, "ctm_step_backward: only the free energy's gradient is built");
+    if (!h->warm || h->steps < 1) return fail(CTM_EINVAL, "ctm_step_backward needs a state reached by ctm_step");
+    const Layout& L = h->lay;
+    const int m = L.m, N = L.N;
+    TanCtx c;
+    ctm_status s = tan_alloc(h, c);
+    if (s != CTM_OK) return s;
+    auto done = [&](ctm_status st) {
+        tan_free(h, c);
+        return st;
+    };
+    // the gauge-fixed step at the state: its Ritz block rotated onto the last
+    // step's, so that at a fixed point P_new repeats P entry by entry
+    s = tan_prepare(h, c);
+    if (s != CTM_OK) return done(s);
+    const size_t mN = (size_t)m * N;
+    std::vector<double> pn(mN), p0(mN), om0(m);
+    CTM_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaMemcpyAsync(p0.data(), h->P, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaMemcpyAsync(om0.data(), h->omega, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    {
+        // entries weighted by |omega| of both block legs (device layout
+        // a + m (s + q g)): states deep in the spectrum with nearly equal
+        // eigenvalues are fixed only to rounding over their gap
+        double change = 0.0;
+        const double a1 = std::fabs(om0[0]) > 0.0 ? std::fabs(om0[0]) : 1.0;
+        for (size_t e = 0; e < mN; ++e) {
+            const int a = (int)(e % m), g = (int)((e / m) / L.q);
+            const double wgt = std::fabs(om0[a]) * std::fabs(om0[g]) / (a1 * a1);
+            change = std::max(change, wgt * std::fabs(pn[e] / c.kap - p0[e]));
+        }
+        if (!(change < 1e-8))
+            return done(fail(CTM_ENOTCONVERGED, "ctm_step_backward: the state is not a fixed point of the step"));
+    }
+    // right side: the tangent of the step along W's own beta dependence
+    const int meff = c.meff;
+    const size_t n = mN + (size_t)meff;
+    std::vector<double> zeroP(mN, 0.0), zeroO(m, 0.0), rhs(n), x(n, 0.0);
+    double kd_b = 0.0;
+    std::vector<double> odn;
+    auto apply = [&](const double* Pin, const double* Oin, bool source, double* out_vec, double* kdot) -> ctm_status {
+        std::vector<double> oin(m, 0.0);
+        for (int i = 0; i < meff; ++i) oin[i] = Oin[i];
+        ctm_status st = tan_upload(h, c, Pin, oin.data());
+        if (st != CTM_OK) return st;
+        st = tan_apply(h, c, source, kdot, &odn);
+        if (st != CTM_OK) return st;
+        if (out_vec) {
+            CTM_CUDA(cudaMemcpyAsync(out_vec, c.Pd, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st));
+            CTM_CUDA(cudaStreamSynchronize(h->st));
+            for (int i = 0; i < meff; ++i) out_vec[mN + i] = odn[i];
+        }
+        return CTM_OK;
+    };
+    s = apply(zeroP.data(), zeroO.data(), true, rhs.data(), &kd_b);
+    if (s != CTM_OK) return done(s);
+    // GMRES on (I - J) x = rhs, J x = one tangent step without the source
+    std::vector<double> Jv(n);
+    auto op = [&](const std::vector<double>& v, std::vector<double>& w) -> ctm_status {
+        double kd = 0.0;
+        ctm_status st = apply(v.data(), v.data() + mN, false, Jv.data(), &kd);
+        if (st != CTM_OK) return st;
+        for (size_t i = 0; i < n; ++i) w[i] = v[i] - Jv[i];
+        return CTM_OK;
+    };
+    int gm_iters = 0;
+    double gm_res = 0.0;
+    s = host_gmres(op, rhs, x, 1e-12, 300, &gm_iters, &gm_res);
+    if (s != CTM_OK) return done(s);
+    // d kappa / d beta at the fixed point: the step's kappa tangent along x
+    // with the source
+    double kdot = 0.0;
+    s = apply(x.data(), x.data() + mN, true, nullptr, &kdot);
+    if (s != CTM_OK) return done(s);
+    const double beta = h->cfg.beta, lk = std::log(c.kap);
+    // f = -ln kappa / (2 beta)
+    const double df = 0.5 * lk / (beta * beta) - 0.5 * kdot / (beta * c.kap);
+    *grad_beta = grad_obs->f * df;
+    h->last_backward_iters = gm_iters;
+    h->last_backward_residual = gm_res;
+    return done(CTM_OK);
 }
 
 ctm_status ctm_get_spectrum(ctm_handle* h, double* omega) {

@@ -210,10 +210,12 @@ def ctm_observables(h):
     return o, st
 
 
-def ctm_step_backward(h, grad_obs: ctm_obs):
+def ctm_step_backward(h, grad_obs: ctm_obs) -> float:
+    """sum_k grad_obs_k d obs_k / d beta at the converged fixed point (the
+    library builds the free energy's term; see ctm.h)."""
     g = np.zeros(1)
     _check(lib.ctm_step_backward(h, ctypes.byref(grad_obs), _dptr(g)))
-    return g
+    return float(g[0])
 
 
 def ctm_xi(h, max_iters: int = 0, tol: float = 0.0) -> tuple:
@@ -501,6 +503,13 @@ class CTMRG:
 
     def tangent_step(self, P_dot, omega_dot, source: bool = True) -> dict:
         return ctm_tangent_step(self.h, self.m, self.q, P_dot, omega_dot, source)
+
+    def df_dbeta(self) -> float:
+        """d f / d beta of the converged fixed point by implicit
+        differentiation on the device (ctm_step_backward with grad f = 1)."""
+        go = ctm_obs()
+        go.f = 1.0
+        return ctm_step_backward(self.h, go)
 
     def extend(self):
         ctm_extend(self.h)

@@ -120,3 +120,32 @@ def test_tangent_step_rejects_other_forms_and_bad_arguments(ctm):
             g.tangent_step(np.zeros((8, 159)), np.zeros(8))
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("T", [0.44, 0.6])
+def test_backward_free_energy_derivative_matches_the_oracle(ctm, T):
+    """ctm_step_backward at the converged q = 20, m = 8 fixed point: df/dbeta
+    by GMRES on (I - J) x = d(step)/dbeta with the GPU tangent step equals
+    the oracle's fixed-point derivative, and f + beta df/dbeta equals the
+    bond-expectation energy u (thermodynamics)."""
+    spins, m, beta = W.dodecahedron(), 8, 1.0 / T
+    t = TG.TangentCTMRG(spins, m, beta)
+    assert t.run_primal(3000, 1e-13)[-1]["delta"] < 1e-13
+    assert t.fixed_point_derivative()["residual"] <= 1e-12
+    ob = t.observables()
+    g = ctm.CTMRG(spins, m, beta, device="cuda:0")
+    try:
+        g.run(5000)
+        o = g.observables()
+        df = g.df_dbeta()
+        with pytest.raises(ctm.CtmError) as e:
+            go = ctm.ctm_obs()
+            go.M = 1.0
+            ctm.ctm_step_backward(g.h, go)
+        assert e.value.status == ctm.CTM_EUNSUPPORTED
+    finally:
+        g.close()
+    print(f"\nT = {T}: df/dbeta GPU {df:.12e}, oracle {ob['df_dbeta']:.12e}; f + beta df/dbeta "
+          f"{o['f'] + beta * df:.12f}, u {o['u']:.12f}")
+    assert df == pytest.approx(ob["df_dbeta"], rel=1e-8)
+    assert o["f"] + beta * df == pytest.approx(o["u"], rel=1e-9)
