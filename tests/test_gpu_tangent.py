@@ -149,3 +149,22 @@ def test_backward_free_energy_derivative_matches_the_oracle(ctm, T):
           f"{o['f'] + beta * df:.12f}, u {o['u']:.12f}")
     assert df == pytest.approx(ob["df_dbeta"], rel=1e-8)
     assert o["f"] + beta * df == pytest.approx(o["u"], rel=1e-9)
+
+
+def test_free_energy_autograd_function(ctm):
+    """torch.autograd through the library: f(beta) at the converged q = 20,
+    m = 8 fixed point and its gradient from ctm_step_backward, against the
+    oracle's fixed point and implicit derivative."""
+    import torch
+
+    from paper_2004_08669_gb300 import autograd as AG
+    spins, m, T = W.dodecahedron(), 8, 0.44
+    t = TG.TangentCTMRG(spins, m, 1.0 / T)
+    assert t.run_primal(3000, 1e-13)[-1]["delta"] < 1e-13
+    t.fixed_point_derivative()
+    ob = t.observables()
+    beta = torch.tensor(1.0 / T, dtype=torch.float64, requires_grad=True)
+    f = AG.free_energy(beta, spins, m)
+    f.backward()
+    assert f.item() == pytest.approx(ob["f"], rel=1e-12)
+    assert beta.grad.item() == pytest.approx(ob["df_dbeta"], rel=1e-8)
