@@ -36,6 +36,7 @@
 #include "ctm_internal.cuh"
 #include "eig_f64.cuh"
 #include "oz_gemm.cuh"
+#include "host_gmres.h"
 #include "tangent.cuh"
 #include "tc_gemm.cuh"
 #include "xi.cuh"
@@ -1268,78 +1269,6 @@ ctm_status tan_apply(ctm_handle* h, TanCtx& c, bool source, double* kdot, std::v
     return CTM_OK;
 }
 
-// GMRES without restarts on the host (Arnoldi with modified Gram-Schmidt
-// applied twice, Givens rotations for the small least-squares problem):
-// solve op(x) = rhs to a relative residual tol.
-template <class Op>
-ctm_status host_gmres(Op op, const std::vector<double>& rhs, std::vector<double>& x, double tol, int max_iter,
-                      int* iters, double* rel_res) {
-    const size_t n = rhs.size();
-    double b0 = 0.0;
-    for (double v : rhs) b0 += v * v;
-    b0 = std::sqrt(b0);
-    x.assign(n, 0.0);
-    *iters = 0;
-    *rel_res = 0.0;
-    if (b0 == 0.0) return CTM_OK;
-    std::vector<std::vector<double>> V(1, std::vector<double>(n));
-    for (size_t i = 0; i < n; ++i) V[0][i] = rhs[i] / b0;
-    std::vector<std::vector<double>> H;  // columns of the Hessenberg matrix
-    std::vector<double> cs, sn, g(1, b0), w(n);
-    int k = 0;
-    double res = 1.0;
-    for (k = 0; k < max_iter; ++k) {
-        ctm_status s = op(V[k], w);
-        if (s != CTM_OK) return s;
-        std::vector<double> hk(k + 2, 0.0);
-        for (int pass = 0; pass < 2; ++pass)
-            for (int j = 0; j <= k; ++j) {
-                double hj = 0.0;
-                for (size_t i = 0; i < n; ++i) hj += V[j][i] * w[i];
-                hk[j] += hj;
-                for (size_t i = 0; i < n; ++i) w[i] -= hj * V[j][i];
-            }
-        double nw = 0.0;
-        for (double v : w) nw += v * v;
-        nw = std::sqrt(nw);
-        hk[k + 1] = nw;
-        for (int j = 0; j < k; ++j) {  // earlier rotations
-            const double t = cs[j] * hk[j] + sn[j] * hk[j + 1];
-            hk[j + 1] = -sn[j] * hk[j] + cs[j] * hk[j + 1];
-            hk[j] = t;
-        }
-        const double r = std::hypot(hk[k], hk[k + 1]);
-        const double ck = r > 0.0 ? hk[k] / r : 1.0, sk = r > 0.0 ? hk[k + 1] / r : 0.0;
-        cs.push_back(ck);
-        sn.push_back(sk);
-        hk[k] = r;
-        hk[k + 1] = 0.0;
-        g.push_back(-sk * g[k]);
-        g[k] = ck * g[k];
-        H.push_back(hk);
-        res = std::fabs(g[k + 1]) / b0;
-        if (res <= tol || nw == 0.0) {
-            ++k;
-            break;
-        }
-        V.emplace_back(n);
-        for (size_t i = 0; i < n; ++i) V[k + 1][i] = w[i] / nw;
-    }
-    if (res > tol) return fail(CTM_ENOTCONVERGED, "ctm_step_backward: GMRES did not converge");
-    // back substitution for y, x = V y
-    std::vector<double> y(k, 0.0);
-    for (int i = k - 1; i >= 0; --i) {
-        double acc = g[i];
-        for (int j = i + 1; j < k; ++j) acc -= H[j][i] * y[j];
-        y[i] = acc / H[i][i];
-    }
-    for (int j = 0; j < k; ++j)
-        for (size_t i = 0; i < n; ++i) x[i] += y[j] * V[j][i];
-    *iters = k;
-    *rel_res = res;
-    return CTM_OK;
-}
-
 }  // namespace
 
 // ================================================================ C-ABI
@@ -1994,8 +1923,14 @@ ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* gra
     };
     int gm_iters = 0;
     double gm_res = 0.0;
-    s = host_gmres(op, rhs, x, 1e-12, 300, &gm_iters, &gm_res);
-    if (s != CTM_OK) return done(s);
+    ctm_status op_status = CTM_OK;
+    auto op_host = [&](const std::vector<double>& v, std::vector<double>& w) -> bool {
+        op_status = op(v, w);
+        return op_status == CTM_OK;
+    };
+    const int gst = ctm::host_gmres(op_host, rhs, x, 1e-12, 300, &gm_iters, &gm_res);
+    if (gst == ctm::kGmresOpFailed) return done(op_status);
+    if (gst != ctm::kGmresOk) return done(fail(CTM_ENOTCONVERGED, "ctm_step_backward: GMRES did not converge"));
     // d kappa / d beta at the fixed point: the step's kappa tangent along x
     // with the source
     double kdot = 0.0;
