@@ -1831,9 +1831,13 @@ ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* om
     s = tan_apply(h, c, source != 0, &kdot, &odn);
     if (s != CTM_OK) return done(s);
     std::vector<double> pn((size_t)m * L.N), pdn((size_t)m * L.N);
-    CTM_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * pn.size(), cudaMemcpyDeviceToHost, h->st));
-    CTM_CUDA(cudaMemcpyAsync(pdn.data(), c.Pd, sizeof(double) * pdn.size(), cudaMemcpyDeviceToHost, h->st));
-    CTM_CUDA(cudaStreamSynchronize(h->st));
+    {
+        cudaError_t e = cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * pn.size(), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pdn.data(), c.Pd, sizeof(double) * pdn.size(), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return done(fail(CTM_ECUDA, std::string("ctm_tangent_step: ") + cudaGetErrorString(e)));
+    }
     for (double& v : pn) v /= c.kap;
     from_device_layout(L, pn.data(), out->P_new);
     from_device_layout(L, pdn.data(), out->P_dot_new);
@@ -1872,10 +1876,14 @@ ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* gra
     if (s != CTM_OK) return done(s);
     const size_t mN = (size_t)m * N;
     std::vector<double> pn(mN), p0(mN), om0(m);
-    CTM_CUDA(cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st));
-    CTM_CUDA(cudaMemcpyAsync(p0.data(), h->P, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st));
-    CTM_CUDA(cudaMemcpyAsync(om0.data(), h->omega, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
-    CTM_CUDA(cudaStreamSynchronize(h->st));
+    {
+        cudaError_t e = cudaMemcpyAsync(pn.data(), h->Pn, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p0.data(), h->P, sizeof(double) * mN, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(om0.data(), h->omega, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return done(fail(CTM_ECUDA, std::string("ctm_step_backward: ") + cudaGetErrorString(e)));
+    }
     {
         // entries weighted by |omega| of both block legs (device layout
         // a + m (s + q g)): states deep in the spectrum with nearly equal
