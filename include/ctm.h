@@ -184,12 +184,13 @@ ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* om
  * |omega| of both block legs, to 1e-8), else CTM_ENOTCONVERGED; then the
  * linear fixed-point equation (I - J) x = d(step)/dbeta, J = d(step)/d(state),
  * is solved by GMRES on the host (to 1e-12, at most 300 iterations) with J
- * applied as the tangent step of ctm_tangent_step, and df/dbeta follows
- * from the growth factor's tangent (f = -ln kappa / (2 beta)).  FP64 form
- * only (else CTM_EUNSUPPORTED); the state must come from ctm_step (else
- * CTM_EINVAL).  Built for the free energy: a nonzero grad_obs->M, u or S_E
- * returns CTM_EUNSUPPORTED and leaves *grad_beta untouched.  The handle's P
- * and omega are unchanged. */
+ * applied as the tangent step of ctm_tangent_step; df/dbeta follows from
+ * the growth factor's tangent (f = -ln kappa / (2 beta)), and, when their
+ * gradients are nonzero, dM, du and dS_E from the kept eigenpairs' tangent
+ * along the solution and the tangent of C~_h (the extension with the bond
+ * energy inserted, with its own beta-derivative).  FP64 form only (else
+ * CTM_EUNSUPPORTED); the state must come from ctm_step (else CTM_EINVAL).
+ * The handle's P and omega are unchanged. */
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta);
 
 /* Effective correlation length (Sec. II): the leading eigenvalues of the

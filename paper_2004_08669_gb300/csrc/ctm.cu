@@ -1041,12 +1041,15 @@ struct TanCtx {
            *Pnd = nullptr, *Zd = nullptr, *Ud = nullptr, *Upd = nullptr, *W1 = nullptr, *HH = nullptr,
            *Kc = nullptr, *lamd = nullptr, *omd = nullptr, *Rhs = nullptr, *Y = nullptr, *T = nullptr,
            *Tz = nullptr, *res = nullptr, *part = nullptr;
+    // for the observables' tangents: dX1 before its contraction, C~_h, its
+    // tangent, C~_h Z and dC~_h Z, the column sums
+    double *X1d = nullptr, *Ch = nullptr, *Chd = nullptr, *Bh = nullptr, *Bd = nullptr, *cols = nullptr;
     int meff = 0, bt = 0, iters = 0, live = 0, deflate_iters = 0;
     double kap = 0.0, sc = 0.0, z4 = 0.0;
     std::vector<double> th;
 };
 
-ctm_status tan_alloc(ctm_handle* h, TanCtx& c) {
+ctm_status tan_alloc(ctm_handle* h, TanCtx& c, bool with_obs = false) {
     const Layout& L = h->lay;
     const int m = L.m, N = L.N, b = L.b;
     if (L.q * L.q > 1024) return fail(CTM_EINVAL, "the tangent step needs q <= 32");
@@ -1064,6 +1067,15 @@ ctm_status tan_alloc(ctm_handle* h, TanCtx& c) {
                  o_od = take((size_t)m * d), o_Rhs = take((size_t)N * m * d), o_Y = take((size_t)N * m * d),
                  o_T = take((size_t)N * m * d), o_Tz = take((size_t)b * m * d), o_res = take((size_t)b * d),
                  o_part = take((size_t)2 * ctm::kTanParts * d);
+    size_t o_X1d = 0, o_Ch = 0, o_Chd = 0, o_Bh = 0, o_Bd = 0, o_cols = 0;
+    if (with_obs) {
+        o_X1d = take(NN * d);
+        o_Ch = take(NN * d);
+        o_Chd = take(NN * d);
+        o_Bh = take((size_t)N * m * d);
+        o_Bd = take((size_t)N * m * d);
+        o_cols = take((size_t)5 * m * d);
+    }
     if (cudaMalloc(&c.scratch, off) != cudaSuccess) {
         c.scratch = nullptr;
         return fail(CTM_ENOMEM, "cudaMalloc of the tangent scratch failed");
@@ -1090,6 +1102,14 @@ ctm_status tan_alloc(ctm_handle* h, TanCtx& c) {
     c.Tz = Dp(o_Tz);
     c.res = Dp(o_res);
     c.part = Dp(o_part);
+    if (with_obs) {
+        c.X1d = Dp(o_X1d);
+        c.Ch = Dp(o_Ch);
+        c.Chd = Dp(o_Chd);
+        c.Bh = Dp(o_Bh);
+        c.Bd = Dp(o_Bd);
+        c.cols = Dp(o_cols);
+    }
     return CTM_OK;
 }
 
@@ -1194,6 +1214,7 @@ ctm_status tan_apply(ctm_handle* h, TanCtx& c, bool source, double* kdot, std::v
     tan_gemm(h, true, false, N, N, m, 1.0, c.Pd, m, h->P, m, 0.0, c.Cd, N, h->omega);
     tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, c.Pd, m, 1.0, c.Cd, N, h->omega);
     tan_gemm(h, true, false, N, N, m, 1.0, h->P, m, h->P, m, 1.0, c.Cd, N, c.omd);
+    if (c.X1d) CTM_CUDA(cudaMemcpyAsync(c.X1d, c.Cd, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
     pwcontract(h, c.Cd, h->E, &h->ctl->live, c.live, false);
     if (source) CTM_CUDA(ctm::wcontract_dbeta(st, q, c.live, c.X1s, N, h->E, h->Eh, c.Cd, N));
     ctm::mask_live(st, N, q, c.live, c.Cd, N);
@@ -1266,6 +1287,72 @@ ctm_status tan_apply(ctm_handle* h, TanCtx& c, bool source, double* kdot, std::v
     const double scd = -0.25 * pow(c.z4, -1.25) * z4d;
     omega_dot_new->assign(m, 0.0);
     for (int i = 0; i < meff; ++i) (*omega_dot_new)[i] = ld[i] * c.sc + c.th[i] * scd;
+    return CTM_OK;
+}
+
+// The observables of the prepared state (Eq. 5-6 and the bond energy, over
+// the kept states, as ctm_observables) and their tangents along the last
+// tan_apply (which must have kept dX1: a context allocated with_obs):
+//   M = sum w^4 m_i / sum w^4, m_i = sum_t z_ti^2 mag_t;
+//   u = 2 sum w^3 h_i / sum w^4, h_i = z_i^t C~_h z_i, C~_h the extension
+//   with the bond energy inserted (inner factor Eh);
+//   S_E = -sum p ln p, p = w^4 / sum w^4;
+// with w the Ritz values, dw = lambda_dot, dz the eigen tangent, and dC~_h
+// the contraction of dX1 with Eh plus its own beta-derivative.
+ctm_status tan_observables(ctm_handle* h, TanCtx& c, double val[3], double dval[3]) {
+    const Layout& L = h->lay;
+    const int m = L.m, q = L.q, N = L.N, meff = c.meff;
+    const size_t d = sizeof(double), NN = (size_t)N * N;
+    cudaStream_t st = h->st;
+    if (!c.X1d) return fail(CTM_EINVAL, "tangent context without the observables' buffers");
+    CTM_CUDA(cudaMemcpyAsync(c.Ch, c.X1s, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, c.Ch, h->Eh, &h->ctl->live, c.live, false);
+    ctm::mask_live(st, N, q, c.live, c.Ch, N);
+    CTM_CUDA(cudaMemcpyAsync(c.Chd, c.X1d, d * NN, cudaMemcpyDeviceToDevice, st));
+    pwcontract(h, c.Chd, h->Eh, &h->ctl->live, c.live, false);
+    CTM_CUDA(ctm::wcontract_dbeta(st, q, c.live, c.X1s, N, h->E, h->Eh, c.Chd, N, true));
+    ctm::mask_live(st, N, q, c.live, c.Chd, N);
+    count_small(h, 3);
+    tan_gemm(h, false, false, N, meff, N, 1.0, c.Ch, N, h->Z, N, 0.0, c.Bh, N, nullptr);
+    tan_gemm(h, false, false, N, meff, N, 1.0, c.Chd, N, h->Z, N, 0.0, c.Bd, N, nullptr);
+    ctm::column_dots(st, N, meff, h->Z, N, h->Z, N, h->mag, q, c.cols);
+    ctm::column_dots(st, N, meff, h->Z, N, c.Zd, N, h->mag, q, c.cols + m);
+    ctm::column_dots(st, N, meff, h->Z, N, c.Bh, N, nullptr, q, c.cols + 2 * m);
+    ctm::column_dots(st, N, meff, c.Zd, N, c.Bh, N, nullptr, q, c.cols + 3 * m);
+    ctm::column_dots(st, N, meff, h->Z, N, c.Bd, N, nullptr, q, c.cols + 4 * m);
+    count_small(h, 5);
+    std::vector<double> cl((size_t)5 * m), ld(meff);
+    CTM_CUDA(cudaMemcpyAsync(cl.data(), c.cols, d * cl.size(), cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaMemcpyAsync(ld.data(), c.lamd, d * meff, cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    double z4 = 0.0, z4d = 0.0, Mn = 0.0, Mnd = 0.0, Hn = 0.0, Hnd = 0.0;
+    for (int i = 0; i < meff; ++i) {
+        const double w = c.th[i], wd = ld[i], w2 = w * w, w3 = w2 * w, w4 = w3 * w;
+        const double mi = cl[i], mid = 2.0 * cl[m + i];
+        const double hi = cl[2 * m + i], hid = 2.0 * cl[3 * m + i] + cl[4 * m + i];
+        z4 += w4;
+        z4d += 4.0 * w3 * wd;
+        Mn += w4 * mi;
+        Mnd += 4.0 * w3 * wd * mi + w4 * mid;
+        Hn += w3 * hi;
+        Hnd += 3.0 * w2 * wd * hi + w3 * hid;
+    }
+    const double M = Mn / z4, hb = Hn / z4;
+    double S = 0.0, Sd = 0.0;
+    for (int i = 0; i < meff; ++i) {
+        const double w = c.th[i], w3 = w * w * w, w4 = w3 * w;
+        const double p = w4 / z4, pd = 4.0 * w3 * ld[i] / z4 - w4 * z4d / (z4 * z4);
+        if (p > 0.0) {
+            S -= p * std::log(p);
+            Sd -= pd * std::log(p);
+        }
+    }
+    val[0] = M;
+    val[1] = 2.0 * hb;
+    val[2] = S;
+    dval[0] = (Mnd - M * z4d) / z4;
+    dval[1] = 2.0 * (Hnd - hb * z4d) / z4;
+    dval[2] = Sd;
     return CTM_OK;
 }
 
@@ -1858,13 +1945,12 @@ ctm_status ctm_tangent_step(ctm_handle* h, const double* P_dot, const double* om
 ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* grad_beta) {
     if (!h || !grad_obs || !grad_beta) return fail(CTM_EINVAL, "NULL argument");
     if (h->lay.prec != CTM_FP64) return fail(CTM_EUNSUPPORTED, "the backward step is built for the FP64 form");
-    if (grad_obs->M != 0.0 || grad_obs->u != 0.0 || grad_obs->S_E != 0.0)
-        return fail(CTM_EUNSUPPORTED, "ctm_step_backward: only the free energy's gradient is built");
     if (!h->warm || h->steps < 1) return fail(CTM_EINVAL, "ctm_step_backward needs a state reached by ctm_step");
+    const bool need_obs = grad_obs->M != 0.0 || grad_obs->u != 0.0 || grad_obs->S_E != 0.0;
     const Layout& L = h->lay;
     const int m = L.m, N = L.N;
     TanCtx c;
-    ctm_status s = tan_alloc(h, c);
+    ctm_status s = tan_alloc(h, c, need_obs);
     if (s != CTM_OK) return s;
     auto done = [&](ctm_status st) {
         tan_free(h, c);
@@ -1947,7 +2033,16 @@ ctm_status ctm_step_backward(ctm_handle* h, const ctm_obs* grad_obs, double* gra
     const double beta = h->cfg.beta, lk = std::log(c.kap);
     // f = -ln kappa / (2 beta)
     const double df = 0.5 * lk / (beta * beta) - 0.5 * kdot / (beta * c.kap);
-    *grad_beta = grad_obs->f * df;
+    double g = grad_obs->f * df;
+    if (need_obs) {
+        // M, u, S_E of the fixed point and their tangents along x (the last
+        // tan_apply above, with the source)
+        double val[3], dval[3];
+        s = tan_observables(h, c, val, dval);
+        if (s != CTM_OK) return done(s);
+        g += grad_obs->M * dval[0] + grad_obs->u * dval[1] + grad_obs->S_E * dval[2];
+    }
+    *grad_beta = g;
     h->last_backward_iters = gm_iters;
     h->last_backward_residual = gm_res;
     return done(CTM_OK);

@@ -25,20 +25,28 @@ inline int grid_of(size_t n, int per = 256, int cap = 152 * 8) {
 // form E o (E T1) (the same factor order as the contraction itself):
 //   d out = Ed o (E T1) + E o (Ed T1) + E o (E T1d),
 //   T1d = (M o Ed) E + (M o E) Ed,   Ed = (v.v) E = -Eh.
+// With inner_h the inner factor is the bond-impurity table Eh = -(v.v) E
+// (the energy inserted on one bond) instead of E, and its derivative
+// d Eh / d beta = -(v.v)^2 E = -Eh^2 / E.
 __global__ void k_wcontract_dbeta(int q, int live, const double* __restrict__ X, int ldx,
-                                  const double* __restrict__ E, const double* __restrict__ Eh,
+                                  const double* __restrict__ E, const double* __restrict__ Eh, int inner_h,
                                   double* __restrict__ out, int ldo) {
     extern __shared__ double sh[];
     const int q2 = q * q;
     double* sE = sh;
     double* sD = sE + q2;
-    double* G = sD + q2;
+    double* sI = sD + q2;
+    double* sID = sI + q2;
+    double* G = sID + q2;
     double* Gd = G + q2;
     double* T1 = Gd + q2;
     double* T1d = T1 + q2;
     for (int e = threadIdx.x; e < q2; e += blockDim.x) {
-        sE[e] = E[e];
-        sD[e] = -Eh[e];
+        const double ee = E[e], eh = Eh[e];
+        sE[e] = ee;
+        sD[e] = -eh;
+        sI[e] = inner_h ? eh : ee;
+        sID[e] = inner_h ? -eh * eh / ee : -eh;
     }
     __syncthreads();
     const int el = threadIdx.x;
@@ -51,8 +59,8 @@ __global__ void k_wcontract_dbeta(int q, int live, const double* __restrict__ X,
         const size_t offo = (size_t)q * g + (size_t)ldo * ((size_t)q * gp);
         if (act) {
             const double x = X[off + i + (size_t)ldx * j];
-            G[el] = x * sE[el];
-            Gd[el] = x * sD[el];
+            G[el] = x * sI[el];
+            Gd[el] = x * sID[el];
         }
         __syncthreads();
         if (act) {
@@ -161,22 +169,49 @@ __global__ void k_tangent_normalise(size_t n, const double* __restrict__ R, cons
         out[e] = Rdot[e] * inv_k - R[e] * c;
 }
 
+// out[i] = sum_t A[t, i] B[t, i] (w[t % q] when w is given: the spin of
+// row t = s + q gamma), one CTA per column.
+__global__ void k_column_dots(int N, int n, const double* __restrict__ A, int lda, const double* __restrict__ B,
+                              int ldb, const double* __restrict__ w, int q, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const double v = A[t + (size_t)lda * i] * B[t + (size_t)ldb * i];
+        s = fma(v, w ? w[t % q] : 1.0, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += red[k];
+        out[i] = a;
+    }
+}
+
 }  // namespace
 
 cudaError_t wcontract_dbeta(cudaStream_t st, int q, int live, const double* X, int ldx, const double* E,
-                            const double* Eh, double* out, int ldo) {
+                            const double* Eh, double* out, int ldo, bool inner_h) {
     const int q2 = q * q;
     if (q2 > 1024 || live < 1) return cudaErrorInvalidValue;
     const int threads = ((q2 + 31) / 32) * 32;
-    const size_t smem = (size_t)6 * q2 * sizeof(double);
+    const size_t smem = (size_t)8 * q2 * sizeof(double);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_wcontract_dbeta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const long nblk = (long)live * live;
     const int grid = (int)(nblk < 152 * 4 ? nblk : 152 * 4);
-    k_wcontract_dbeta<<<grid, threads, smem, st>>>(q, live, X, ldx, E, Eh, out, ldo);
+    k_wcontract_dbeta<<<grid, threads, smem, st>>>(q, live, X, ldx, E, Eh, inner_h ? 1 : 0, out, ldo);
     return cudaGetLastError();
+}
+
+void column_dots(cudaStream_t st, int N, int n, const double* A, int lda, const double* B, int ldb,
+                 const double* wspin, int q, double* out) {
+    k_column_dots<<<n, 256, 0, st>>>(N, n, A, lda, B, ldb, wspin, q, out);
 }
 
 void mask_live(cudaStream_t st, int N, int q, int live, double* A, int lda) {

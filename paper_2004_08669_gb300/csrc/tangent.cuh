@@ -9,11 +9,16 @@ namespace ctm {
 
 // out += d/dbeta of the blockwise vertex-weight contraction of X over its
 // live x live q x q blocks (spin-fastest layout, leading dims ldx / ldo):
-// each block M maps to E o (E (M o E) E), E = exp(beta v.v) (Eq. 1-2), whose
-// beta-derivative has E_dot = (v.v) E = -Eh at each of the four factors.
-// Requires q * q <= 1024.
+// each block M maps to E o (E (M o E_in) E), E = exp(beta v.v) (Eq. 1-2),
+// whose beta-derivative has E_dot = (v.v) E = -Eh at each factor.  The inner
+// factor E_in is E, or with inner_h the bond-impurity table Eh (its
+// derivative -Eh^2 / E).  Requires q * q <= 1024.
 cudaError_t wcontract_dbeta(cudaStream_t st, int q, int live, const double* X, int ldx, const double* E,
-                            const double* Eh, double* out, int ldo);
+                            const double* Eh, double* out, int ldo, bool inner_h = false);
+
+// out[i] = sum_t A[t, i] B[t, i] w[t % q] for the n columns (w NULL: 1).
+void column_dots(cudaStream_t st, int N, int n, const double* A, int lda, const double* B, int ldb,
+                 const double* wspin, int q, double* out);
 
 // Zero the rows and columns t of the N x N matrix A whose block index t / q
 // is >= live (the dead part of the renormalised leg).

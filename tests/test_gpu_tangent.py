@@ -138,11 +138,6 @@ def test_backward_free_energy_derivative_matches_the_oracle(ctm, T):
         g.run(5000)
         o = g.observables()
         df = g.df_dbeta()
-        with pytest.raises(ctm.CtmError) as e:
-            go = ctm.ctm_obs()
-            go.M = 1.0
-            ctm.ctm_step_backward(g.h, go)
-        assert e.value.status == ctm.CTM_EUNSUPPORTED
     finally:
         g.close()
     print(f"\nT = {T}: df/dbeta GPU {df:.12e}, oracle {ob['df_dbeta']:.12e}; f + beta df/dbeta "
@@ -168,3 +163,34 @@ def test_free_energy_autograd_function(ctm):
     f.backward()
     assert f.item() == pytest.approx(ob["f"], rel=1e-12)
     assert beta.grad.item() == pytest.approx(ob["df_dbeta"], rel=1e-8)
+
+
+
+@pytest.mark.xfail(strict=False, reason="the device tangents of M, u and S_E were written after the last GPU "
+                                        "run of their author and have not yet run on a GB300")
+def test_backward_observable_derivatives_match_the_oracle(ctm):
+    """ctm_step_backward with the gradient of M, u or S_E: the observables'
+    tangents at the fixed point along the implicit solution (the eigen
+    tangent's dz and dlambda, and C~_h with its own beta-derivative) against
+    the oracle's fixed-point derivative, at q = 20, m = 8, T = 0.44."""
+    spins, m, T = W.dodecahedron(), 8, 0.44
+    beta = 1.0 / T
+    t = TG.TangentCTMRG(spins, m, beta)
+    assert t.run_primal(3000, 1e-13)[-1]["delta"] < 1e-13
+    t.fixed_point_derivative()
+    ob = t.observables()
+    g = ctm.CTMRG(spins, m, beta, device="cuda:0")
+    try:
+        g.run(5000)
+        got = {}
+        for name in ("M", "u", "S_E"):
+            go = ctm.ctm_obs()
+            setattr(go, name, 1.0)
+            got[name] = ctm.ctm_step_backward(g.h, go)
+    finally:
+        g.close()
+    print(f"\ndM/dbeta {got['M']:.12e} (oracle {ob['dM_dbeta']:.12e}), du/dbeta {got['u']:.12e} "
+          f"(oracle {ob['du_dbeta']:.12e}), dS/dbeta {got['S_E']:.12e} (oracle {ob['dS_dbeta']:.12e})")
+    assert got["M"] == pytest.approx(ob["dM_dbeta"], rel=1e-7)
+    assert got["u"] == pytest.approx(ob["du_dbeta"], rel=1e-7)
+    assert got["S_E"] == pytest.approx(ob["dS_dbeta"], rel=1e-7)
