@@ -44,7 +44,9 @@ At a gauge-fixed fixed point the same derivative comes from the implicit
 equation (I - J) x = dF/dbeta (fixed_point_derivative), and in reverse mode
 from the adjoint equation (I - J^t) x_bar = g with J^t applied as the
 transpose of one step (_vjp: transposed contractions, inverse permutations,
-the symmetric-eigen adjoint; adjoint_dlnkappa_dbeta).
+the symmetric-eigen adjoint; adjoint_dlnkappa_dbeta for the free energy,
+adjoint_observables for M, u and S_E, whose cotangents come from
+_observables_vjp).
 """
 from __future__ import annotations
 
@@ -597,6 +599,76 @@ class TangentCTMRG:
         x_bar, iters, res = _gmres(one_minus_Jt, pack(gP, go), tol, max_iter)
         _, _, b_beta = self._vjp(pr, *unpack(x_bar), 0.0, source=True)
         return {"dlnkappa_dbeta": g_beta + b_beta, "iterations": iters, "residual": res}
+
+    def _observables_vjp(self, M_bar: float, u_bar: float, S_bar: float):
+        """Reverse mode of the observables at the current state: the
+        cotangents of (P, omega) and the explicit beta cotangent (through W
+        and the bond-impurity weight) of M_bar M + u_bar u + S_bar S_E, with
+        M = sum w^4 m_i / sum w^4, u = 2 sum w^3 h_i / sum w^4, S_E = -sum p
+        ln p over the kept states (as observables())."""
+        m, N = self.m, self.N
+        P, omega = self.P, self.omega
+        Pp = np.asfortranarray(omega[:m, None] * P)
+        C = self._sub(P, Pp, self.w)
+        Ch = self._sub(P, Pp, self.wh)
+        idx = self._live_idx()
+        A = C[np.ix_(idx, idx)]
+        A = 0.5 * (A + A.T)
+        ev, Z = O.eigh(A)
+        meff = _kept_count(ev, m, self.tol_c, self.tol_z)
+        w, Zk = ev[:meff], Z[:, :meff]
+        Hh = Ch[np.ix_(idx, idx)]
+        vb = self.spins[self.bspin]
+        mag = np.array([vb @ self.spins[t // m] for t in idx])
+        mi = (Zk * Zk * mag[:, None]).sum(axis=0)
+        hi = np.einsum("ti,tu,ui->i", Zk, Hh, Zk)
+        w3, w4 = w ** 3, w ** 4
+        z4 = w4.sum()
+        M = (w4 * mi).sum() / z4
+        u = 2.0 * (w3 * hi).sum() / z4
+        p = w4 / z4
+        lp = np.where(p > 0.0, np.log(np.where(p > 0.0, p, 1.0)), 0.0)
+        S = -(p * lp).sum()
+        # cotangents of the eigenvalues, of m_i and h_i
+        w_bar = (M_bar * 4.0 * w3 * (mi - M) + u_bar * (6.0 * w * w * hi - 4.0 * u * w3)
+                 - S_bar * 4.0 * w3 * (lp + S)) / z4
+        m_bar = M_bar * w4 / z4
+        h_bar = u_bar * 2.0 * w3 / z4
+        Z_bar = np.zeros_like(Z)
+        Z_bar[:, :meff] = 2.0 * Zk * mag[:, None] * m_bar + ((Hh + Hh.T) @ Zk) * h_bar
+        A_bar = self._eig_v(A, ev, Z, w_bar, Z_bar[:, :meff], meff)
+        Hh_bar = (Zk * h_bar) @ Zk.T
+        C_bar = np.zeros((N, N), order="F")
+        Ch_bar = np.zeros((N, N), order="F")
+        C_bar[np.ix_(idx, idx)] = A_bar
+        Ch_bar[np.ix_(idx, idx)] = Hh_bar
+        Pa, Ppa, wa = self._sub_vjp(P, Pp, self.w, C_bar)
+        Pb, Ppb, wb = self._sub_vjp(P, Pp, self.wh, Ch_bar)
+        Pp_bar = Ppa + Ppb
+        P_bar = Pa + Pb + omega[:m, None] * Pp_bar
+        omega_bar = np.zeros(N)
+        omega_bar[:m] = (P * Pp_bar).sum(axis=1)
+        beta_bar = float((wa * self.w_dot).sum() + (wb * self.wh_dot).sum())
+        return np.asfortranarray(P_bar), omega_bar, beta_bar
+
+    def adjoint_observables(self, M_bar: float = 0.0, u_bar: float = 0.0, S_bar: float = 0.0,
+                            tol: float = 1e-12, max_iter: int = 500, tol_fixed: float = 1e-10) -> dict:
+        """d(M_bar M + u_bar u + S_bar S_E)/d beta of the fixed point in
+        reverse mode: the observables' cotangent g = (g_x, g_beta) at the
+        gauge-fixed fixed point, the adjoint equation (I - J^t) x_bar = g_x by
+        GMRES, and g_beta + x_bar . dF/dbeta (one reverse step's beta
+        cotangent)."""
+        pr = self.gauge_fixed_point(tol_fixed)
+        pack, unpack = self._packing(pr["meff"])
+        gP, go, g_beta = self._observables_vjp(M_bar, u_bar, S_bar)
+
+        def one_minus_Jt(y):
+            P_b, om_b, _ = self._vjp(pr, *unpack(y), 0.0, source=False)
+            return y - pack(P_b, om_b)
+
+        x_bar, iters, res = _gmres(one_minus_Jt, pack(gP, go), tol, max_iter)
+        _, _, b_beta = self._vjp(pr, *unpack(x_bar), 0.0, source=True)
+        return {"derivative": g_beta + b_beta, "iterations": iters, "residual": res}
 
     def run(self, max_steps: int, tol: float = 1e-12, tol_tangent: float = 1e-10) -> list:
         hist = []

@@ -454,3 +454,25 @@ def test_ritz_block_run_gives_the_same_derivatives(model, m, beta):
     assert t.block_iterations > 0
     for k in ("df_dbeta", "du_dbeta", "dM_dbeta", "dS_dbeta"):
         assert blk[k] == pytest.approx(full[k], rel=1e-11, abs=1e-13), k
+
+
+@pytest.mark.parametrize("model,m,beta", [("cube", 8, 1 / 0.5), ("dodecahedron", 6, 1 / 0.5), ("ising", 16, 1 / 1.8)])
+def test_adjoint_observables_equal_forward(model, m, beta):
+    """Reverse mode of M, u and S_E (their cotangents at the fixed point and
+    the adjoint equation) gives the forward implicit derivatives; for Ising
+    they are Yang's dM/dK and Onsager's du/dK."""
+    spins = MODELS[model]()
+    fw = TG.TangentCTMRG(spins, m, beta)
+    fw.run_primal(3000, 1e-13)
+    fw.fixed_point_derivative()
+    ob = fw.observables()
+    t = TG.TangentCTMRG(spins, m, beta)
+    t.run_primal(3000, 1e-13)
+    rev = {"dM_dbeta": t.adjoint_observables(M_bar=1.0)["derivative"],
+           "du_dbeta": t.adjoint_observables(u_bar=1.0)["derivative"],
+           "dS_dbeta": t.adjoint_observables(S_bar=1.0)["derivative"]}
+    for k, v in rev.items():
+        assert v == pytest.approx(ob[k], rel=1e-9, abs=1e-13), k
+    if model == "ising":
+        assert rev["dM_dbeta"] == pytest.approx(E.yang_dm_dK(beta), rel=1e-9)
+        assert rev["du_dbeta"] == pytest.approx(E.onsager_du_dK(beta), rel=1e-9)
