@@ -476,3 +476,19 @@ def test_adjoint_observables_equal_forward(model, m, beta):
     if model == "ising":
         assert rev["dM_dbeta"] == pytest.approx(E.yang_dm_dK(beta), rel=1e-9)
         assert rev["du_dbeta"] == pytest.approx(E.onsager_du_dK(beta), rel=1e-9)
+
+
+def test_cube_derivatives_are_three_isings():
+    """q = 8 is three Ising models at K = beta / 3: M = M_Yang(K) and u =
+    u_Onsager(K) per spin, so dM/dbeta = Yang'(K) / 3 and du/dbeta =
+    Onsager's du/dK / 3.  At T = 0.5 the tangent's error falls from ~1e-5 at
+    m = 8 to ~1e-12 at m = 24 (the truncation of the product spectrum)."""
+    beta = 1 / 0.5
+    K = beta / 3
+    dM_ex, du_ex = E.yang_dm_dK(K) / 3, E.onsager_du_dK(K) / 3
+    errs = []
+    for m in (8, 24):
+        ob = converged(W.cube(), m, beta)
+        errs.append((abs(ob["dM_dbeta"] / dM_ex - 1), abs(ob["du_dbeta"] / du_ex - 1)))
+    assert errs[1][0] < 1e-10 and errs[1][1] < 1e-10
+    assert errs[0][0] > 100 * errs[1][0] and errs[0][1] > 100 * errs[1][1]
