@@ -273,7 +273,11 @@ ctm_status ctm_symeig(int n, const double* A, int lda, double* evals, double* ve
  *  - n > CTM_SYMEIG_NOALLOC_MAX_N (or n < 1) returns CTM_EINVAL with a message.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The scratch is picked by the device that is
+ *    current at the call: pass a stream and pointers of that device.  The
+ *    address is kept for the life of the process and does not survive a
+ *    cudaDeviceReset of that device (calls after a reset would use a stale
+ *    address): do not reset a device between calls.
  *  - All calls share the one array and each call clears the parts that must
  *    start at zero.  Calls whose work overlaps on the GPU (concurrent streams
  *    or host threads) race on the array and give wrong results: serialise

@@ -461,16 +461,22 @@ static int kept_count(const double* ev, int L, int m, double tol_c, double tol_z
     return meff;
 }
 
-static double entropy4(const double* ev, int n) {
+/* Entanglement entropy of Eq. (6): S = -sum_i p_i ln p_i with the weights
+ * p_i = |ev_i|^power / sum_j |ev_j|^power of the density matrix.  The method
+ * takes power = 4 (rho~ = C~^4 / Tr C~^4, Eq. 4); the power is a parameter only
+ * so that a test can show that another power fails the exact pin. */
+double or_entropy(const double* ev, int n, int power) {
     double z = 0.0;
-    for (int i = 0; i < n; ++i) z += pow(ev[i], 4);
+    for (int i = 0; i < n; ++i) z += pow(fabs(ev[i]), power);
     double S = 0.0;
     for (int i = 0; i < n; ++i) {
-        double p = pow(ev[i], 4) / z;
+        double p = pow(fabs(ev[i]), power) / z;
         if (p > 0.0) S -= p * log(p);
     }
     return S;
 }
+
+static double entropy4(const double* ev, int n) { return or_entropy(ev, n, 4); }
 
 /* Diagonalise the live block of C (N x N).  Returns L; fills ev (L) and
  * Z (L x L) and idx (L). */

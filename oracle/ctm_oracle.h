@@ -83,6 +83,10 @@ int or_eigh(int n, double* A, double* evals, double* Z);
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);
 
+/* Entropy -sum p ln p of the weights p_i = |ev_i|^power / sum |ev|^power
+ * (Eq. 6 with power = 4, the density matrix rho~ = C~^4 / Tr C~^4 of Eq. 4). */
+double or_entropy(const double* ev, int n, int power);
+
 typedef struct or_state or_state;
 
 or_state* or_create(int q, int dim, const double* spins, int m, double beta,

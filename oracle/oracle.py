@@ -56,6 +56,8 @@ def lib():
             L.or_eigh.argtypes = [ctypes.c_int, _dp, _dp, _dp]
             L.or_eigh.restype = ctypes.c_int
             L.or_num_threads.restype = ctypes.c_int
+            L.or_entropy.argtypes = [_dp, ctypes.c_int, ctypes.c_int]
+            L.or_entropy.restype = ctypes.c_double
             L.or_create.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_double]
             L.or_create.restype = ctypes.c_void_p
@@ -88,6 +90,12 @@ def _f64(a) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def entropy(ev, power: int = 4) -> float:
+    """-sum p ln p with p_i = |ev_i|^power / sum |ev|^power (Eq. 6: power 4)."""
+    ev = np.ascontiguousarray(ev, dtype=np.float64)
+    return float(lib().or_entropy(ev.ctypes.data_as(_dp), len(ev), int(power)))
 
 
 def weight_matrix(spins: np.ndarray, beta: float, bond: bool = False) -> np.ndarray:

@@ -43,7 +43,11 @@ class FreeEnergy(torch.autograd.Function):
         return beta.new_tensor(o["f"])
 
     @staticmethod
+    @torch.autograd.function.once_differentiable
     def backward(ctx, grad_f):
+        # First derivative only: a double backward (d2f/dbeta2) is not
+        # available here.  The specific heat and dM/dT come from
+        # ctm_step_backward with the gradient of u or M (ctm.ctm_step_backward).
         (df,) = ctx.saved_tensors
         return grad_f * df.to(grad_f.device), None, None, None, None
 

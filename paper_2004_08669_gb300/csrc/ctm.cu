@@ -2632,6 +2632,8 @@ ctm_status ctm_scan_get_spectrum(ctm_scan* sc, int ibeta, double* omega) {
 namespace {
 constexpr int kNoAllocMaxN = CTM_SYMEIG_NOALLOC_MAX_N;
 constexpr size_t kNoAllocPad = (size_t)kNoAllocMaxN + (kNoAllocMaxN & 1);
+// Upper bound of symeig_layout(kNoAllocMaxN).total (every piece rounded up to
+// 256 bytes); checked against the layout at every call.
 constexpr size_t kNoAllocBytes = 3 * ((kNoAllocPad * kNoAllocPad * sizeof(double) + 255) / 256 * 256) +
                                  (kNoAllocPad * sizeof(double) + 255) / 256 * 256 +
                                  (kNoAllocPad * sizeof(int) + 255) / 256 * 256 +
@@ -2668,23 +2670,18 @@ extern "C" ctm_status ctm_symeig_noalloc(int n, const double* A, int lda, double
         }
         base = g_scratch_ptr[dev];
     }
-    // Carve the scratch exactly as the workspace of ctm_symeig is carved.
-    const size_t np = (size_t)(n + (n & 1) < 2 ? 2 : n + (n & 1));
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = o;
-        o = align256(o + bytes);
-        return r;
-    };
+    // The scratch is carved exactly as the workspace of ctm_symeig is.
+    const SymeigLayout L = symeig_layout(n);
+    if (L.total > kNoAllocBytes || symeig_layout(kNoAllocMaxN).total > kNoAllocBytes)
+        return fail(CTM_EINVAL, "ctm_symeig_noalloc: scratch layout exceeds its array");
     char* ws = (char*)base;
     ctm::EigWork w{};
-    w.A0 = (double*)(ws + take(np * np * sizeof(double)));
-    w.A1 = (double*)(ws + take(np * np * sizeof(double)));
-    w.S = (double*)(ws + take(np * np * sizeof(double)));
-    w.diag = (double*)(ws + take(np * sizeof(double)));
-    w.rank = (int*)(ws + take(np * sizeof(int)));
-    ctm::DevCtl* ctl = (ctm::DevCtl*)(ws + take(sizeof(ctm::DevCtl)));
-    if (o > kNoAllocBytes) return fail(CTM_EINVAL, "ctm_symeig_noalloc: scratch layout exceeds its array");
+    w.A0 = (double*)(ws + L.A0);
+    w.A1 = (double*)(ws + L.A1);
+    w.S = (double*)(ws + L.S);
+    w.diag = (double*)(ws + L.diag);
+    w.rank = (int*)(ws + L.rank);
+    ctm::DevCtl* ctl = (ctm::DevCtl*)(ws + L.ctl);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // The array keeps the previous call's contents: the control block (barrier
     // words, counters, status) must start at zero.

@@ -415,9 +415,11 @@ def ctm_symeig_noalloc(A, max_sweeps: int = 0):
     Ac = A.t().contiguous()
     ev = torch.empty(n, dtype=torch.float64, device=A.device)
     vt = torch.empty(n, n, dtype=torch.float64, device=A.device)
-    st = torch.cuda.current_stream(A.device).cuda_stream
-    status = _check(lib.ctm_symeig_noalloc(n, Ac.data_ptr(), n, ev.data_ptr(), vt.data_ptr(), n, int(max_sweeps),
-                                           ctypes.c_void_p(st)), (CTM_OK, CTM_ENOTCONVERGED))
+    # the library picks its static scratch by the current device: make A's current
+    with torch.cuda.device(A.device):
+        st = torch.cuda.current_stream(A.device).cuda_stream
+        status = _check(lib.ctm_symeig_noalloc(n, Ac.data_ptr(), n, ev.data_ptr(), vt.data_ptr(), n,
+                                               int(max_sweeps), ctypes.c_void_p(st)), (CTM_OK, CTM_ENOTCONVERGED))
     return ev, vt.t(), status
 
 

@@ -9,6 +9,12 @@ Nothing here shares code with the oracle or with the CUDA path.
 - Their exact derivatives in K: d u/dK from the closed form of u with the
   derivative of the complete elliptic integral,
   dK(k)/dk = E(k) / (k (1 - k^2)) - K(k) / k, and d M/dK of Yang's formula.
+- Baxter's corner transfer matrix spectrum of the off-critical Ising model
+  (R. J. Baxter, J. Stat. Phys. 15, 485 (1976) and 17, 1 (1977); in the
+  free-fermion form of I. Peschel, M. Kaulke and O. Legeza, Ann. Phys.
+  (Leipzig) 8, 153 (1999)): the density matrix of a half-infinite cut is
+  rho ~ exp(-sum_j eps_j n_j), n_j in {0, 1}, with single-particle levels
+  eps_j linear in j and spacing set by the elliptic modulus of the model.
 - Exact corner transfer matrices of a k x k quadrant of vertex tensors by
   direct contraction of the network drawn from its geometry.
 """
@@ -138,3 +144,40 @@ def normalised_abs_spectrum(C: np.ndarray, n: int) -> np.ndarray:
     ev = np.linalg.eigvalsh(0.5 * (C + C.T))
     ev = ev[np.argsort(-np.abs(ev))][:n]
     return ev / ev[0]
+
+
+def baxter_ctm_levels(K: float, nmax: int = 80) -> list:
+    """Single-particle levels eps_j of the isotropic square-lattice Ising
+    model's corner transfer matrix (rho = A^4 in the thermodynamic limit), at
+    coupling K != K_CRIT, with the boundary spins fixed:
+      eps = pi K(k') / K(k), K() the complete elliptic integral of the first
+      kind, k' = sqrt(1 - k^2);
+      ordered phase (sinh 2K > 1):    k = sinh^-2 2K, eps_j = 2 j eps, j = 1, 2, ...
+        (the fixed boundary selects one of the two ordered states, which
+        removes the zero mode j = 0 of the symmetric corner);
+      disordered phase (sinh 2K < 1): k = sinh^2 2K,  eps_j = (2 j + 1) eps, j = 0, 1, ...
+    Levels above 700 (weights below 1e-304) are dropped."""
+    s = math.sinh(2.0 * K)
+    k = 1.0 / (s * s) if s > 1.0 else s * s
+    eps = math.pi * special.ellipk(1.0 - k * k) / special.ellipk(k * k)
+    js = range(1, nmax + 1) if s > 1.0 else range(nmax)
+    lev = [(2 * j if s > 1.0 else 2 * j + 1) * eps for j in js]
+    return [e for e in lev if e < 700.0]
+
+
+def baxter_rho_spectrum(K: float, n: int) -> np.ndarray:
+    """The n largest eigenvalues of rho (normalised to trace 1 over all
+    states) as sums of distinct levels: every subset {j} gives exp(-sum eps_j)."""
+    lev = baxter_ctm_levels(K)
+    sums = [0.0]
+    for e in lev:
+        sums = sorted(sums + [x + e for x in sums])[:max(4 * n, 64)]
+    sums = np.array(sums)
+    logZ = sum(math.log1p(math.exp(-e)) for e in lev)
+    return np.exp(-sums[:n] - logZ)
+
+
+def baxter_entropy(K: float) -> float:
+    """Von Neumann entropy of rho from the free-fermion levels:
+    S = sum_j [ln(1 + e^-eps_j) + eps_j / (e^eps_j + 1)]."""
+    return float(sum(math.log1p(math.exp(-e)) + e / (math.exp(e) + 1.0) for e in baxter_ctm_levels(K)))

@@ -165,8 +165,6 @@ def test_free_energy_autograd_function(ctm):
     assert beta.grad.item() == pytest.approx(ob["df_dbeta"], rel=1e-8)
 
 
-@pytest.mark.xfail(strict=False, reason="the device tangents of M, u and S_E were written after the last GPU "
-                                        "run of their author and have not yet run on a GB300")
 def test_backward_observable_derivatives_match_the_oracle(ctm):
     """ctm_step_backward with the gradient of M, u or S_E: the observables'
     tangents at the fixed point along the implicit solution (the eigen

@@ -267,6 +267,44 @@ def test_entropy_bounds():
         assert r["S_E_paper"] <= math.log(r["live_dim"]) + 1e-12
 
 
+# --- Baxter's exact corner spectrum (off-critical Ising) -----------------------
+
+@pytest.mark.parametrize("T,m,tol_w", [(1.5, 32, 1e-11), (1.8, 32, 1e-9), (3.0, 32, 1e-9), (4.0, 32, 1e-11)])
+def test_ising_kept_spectrum_and_entropy_match_baxter(T, m, tol_w):
+    """The converged Ising corner on both sides of T_c = 2.269 against
+    Baxter's exact corner transfer matrix spectrum: the normalised kept
+    spectrum |w_i| / |w_1| = (rho_i / rho_1)^(1/4) (rho = C^4, Eq. 4), and
+    S_E of Eq. (6) against the free-fermion entropy of the same levels.  Away
+    from T_c the spectrum decays fast enough that m = 32 holds all of rho's
+    weight above 1e-30, so S_E is exact to rounding."""
+    K = 1.0 / T
+    c = O.CTMRG(W.ising(), m, K)
+    c.run(5000, 1e-13)
+    _, om, _ = c.get_state()
+    w = np.sort(np.abs(om[:m]))[::-1]
+    w = w[w > 0]
+    rho = E.baxter_rho_spectrum(K, len(w))
+    np.testing.assert_allclose(w / w[0], (rho / rho[0]) ** 0.25, rtol=0, atol=tol_w)
+    S = c.observables()["S_E_kept"]
+    assert S == pytest.approx(E.baxter_entropy(K), abs=1e-13)
+    assert S > 1e-4  # a non-trivial spectrum
+
+
+def test_planted_entropy_power_fails_baxter():
+    """The entropy with weights w^2 (or w^8) instead of w^4 = eigenvalues of
+    rho~ = C~^4 misses Baxter's exact entropy by far more than the tolerance
+    above, on both sides of T_c."""
+    for T in (1.8, 3.0):
+        K = 1.0 / T
+        c = O.CTMRG(W.ising(), 32, K)
+        c.run(5000, 1e-13)
+        _, om, _ = c.get_state()
+        exact = E.baxter_entropy(K)
+        assert O.entropy(om[:32], 4) == pytest.approx(exact, abs=1e-13)
+        for power in (2, 8):
+            assert abs(O.entropy(om[:32], power) - exact) > 1e-3
+
+
 # --- planted mistakes: each must fail a pin ------------------------------------
 
 def _twisted_weight(spins, beta):
