@@ -29,8 +29,9 @@ if ROOT not in sys.path:
 
 METRIC = "CTMRG steps/s at q=20 m=256, mixed vs FP64 at |\u0394f|/f\u22641e-10; % tensor peak"
 UNIT = "steps/s"
-# FP64 peak of the CUDA cores: 152 SMs x 2 DFMA/clk/SM x 2 FLOP x SM clock.
+# ALU peaks of the CUDA cores: 152 SMs x (2 DFMA or 128 FFMA)/clk/SM x 2 FLOP x SM clock.
 FP64_DFMA_PER_CLK_PER_SM = 2
+FP32_FFMA_PER_CLK_PER_SM = 128
 N_SMS = 152
 
 
@@ -186,7 +187,8 @@ def run_reference(args):
               f"state after {nwarm} untimed step(s); each step is a full dense diagonalisation of C~ "
               f"(N={m * q}); the rate is per step")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+           "steps": done, "warmup": nwarm, "steps_requested": args.steps, "warmup_requested": args.warmup,
+           "ms_per_step": 1e3 * el / done, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"dodecahedron q=20 m={m} T={args.T} fp64 (CPU oracle)", "q": q, "m": m,
                       "T": args.T, "parallelism": "host threads"},
@@ -197,22 +199,27 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(g, args):
-    """The oracle, as it stands, on one full-size step from the GPU's state."""
+def cpu_baseline(args, steps: int = 3):
+    """The oracle, as it stands, timed over `steps` full-size steps from a
+    seeded full-size state (workloads.random_state; nothing from the GPU run
+    enters the oracle).  Each step is a dense diagonalisation of C~."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_2004_08669_gb300 import workloads as W
     O.build()
-    P, om, live = g.get_state()
-    c = O.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T)
-    c.set_state(P, np.concatenate([om, np.zeros(args.m * 20 - args.m)]), live)
+    m, q = args.m, 20
+    P, om = W.random_state(m, q, m, seed=2004086690)
+    c = O.CTMRG(W.dodecahedron(), m, 1.0 / args.T)
+    c.set_state(P, np.concatenate([om[:m], np.zeros(m * q - m)]), m)
     t = time.perf_counter()
-    c.step()
+    for _ in range(steps):
+        c.step()
     el = time.perf_counter() - t
-    return {"value": 1.0 / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"1 oracle step (full dense diagonalisation, N={args.m * 20}) from the GPU run's state, "
-                      f"{el:.1f} s"}
+    c.close()
+    return {"value": steps / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{steps} oracle steps (each a full dense diagonalisation of C~, N={m * q}) from a seeded "
+                      f"full-size state, {el:.1f} s in total"}
 
 
 def tensor_peak(prec: str):
@@ -285,6 +292,7 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
     # roofline of the dominant kernel class (algorithmic FLOPs of its launches /
     # their event-timed duration), and of the tensor-core contraction class
     workload = f"dodecahedron q=20 m={m} T={args.T} {prec}"
+    b_blk = min(20 * m, m + max(8, m // 8))
     sm_max = clk.get("sm_max_mhz") or 2070.0
 
     def roof_of(cls):
@@ -295,18 +303,58 @@ def run_mode(args, prec, local, world, barrier, timed_steps):
             r = {"kernel": cls, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": traffic_for(cls, workload), "peak_source": src}
         else:
-            peak = N_SMS * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+            # the FP64 form's solvers and GEMMs run on the FP64 pipe; the other
+            # forms' Jacobi and Cholesky in double-float on the FP32 pipe
+            fp32 = prec != "fp64" and cls in ("jacobi_f64", "cholqr_f64", "rr_refine")
+            per = FP32_FFMA_PER_CLK_PER_SM if fp32 else FP64_DFMA_PER_CLK_PER_SM
+            peak = N_SMS * per * 2 * sm_max * 1e6 / 1e12
             r = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": traffic_for(cls, workload),
-                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x max SM clock"}
+                 "peak_source": (f"derived: 152 SMs x {per} {'FFMA' if fp32 else 'DFMA'}/clk x 2 FLOP x max SM "
+                                 f"clock ({'FP32 pipe: double-float arithmetic' if fp32 else 'FP64 pipe'})")}
+            if cls == "jacobi_f64":
+                # the same solves under the coarser count b^3 per sweep
+                n_solves = max(rr_paths["jacobi"], 1)
+                sw = float(np.mean(sweeps))
+                r["flops_count"] = ("18 npad FP64-equivalent FLOP per rotation (rows p, q and columns p, q of A "
+                                    "and columns p, q of S: 3 x 2 npad elements, 3 FLOP each), rotations "
+                                    "counted on the device")
+                r["b3_sweeps_flops_per_solve"] = float(b_blk) ** 3 * sw
+                r["b3_sweeps_achieved"] = float(b_blk) ** 3 * sw * n_solves / (d["ms"] / 1e3) / 1e12
+                r["b3_sweeps_frac"] = r["b3_sweeps_achieved"] / peak
         r.update({"share_of_step": d["ms"] / ms, "launches": d["launches"]})
         return r
 
     roof = roof_of(dom)
     tcls = {"ozaki64": "oz_gemm", "tf32": "tc_gemm", "bf16": "tc_gemm"}.get(prec)
     roof_t = roof_of(tcls) if tcls in kern else None
+    # Step-level throughput.  FP64-equivalent FLOPs of one step by the dense
+    # count of the method: the three N x N x m products (X1 = P^t Omega P,
+    # X1' = P^t U', P_new = U^t X; counted dense), the two products with the
+    # q^2 x q^2 matrix form of W as the paper writes them (2 m^2 q^4 each; the
+    # build contracts the factorised weight at 4 m^2 q^3), per subspace
+    # iteration C~ V (2 N^2 b) and the orthonormalisation (4 N b^2), and the
+    # Rayleigh-Ritz solve at b^3 per Jacobi sweep.
+    Nn, qq = 20 * m, 20
+    it_mean, sw_mean = float(np.mean(iters)), float(np.mean(sweeps))
+    F = (3 * 2.0 * m * Nn * Nn + 2 * 2.0 * m * m * qq ** 4 + it_mean * (2.0 * Nn * Nn * b_blk + 4.0 * Nn * b_blk ** 2)
+         + float(b_blk) ** 3 * sw_mean)
+    sps = timed_steps / (ms / 1e3)
+    step_roof = {"fp64_equiv_flops_per_step": F, "fp64_equiv_tflops": F * sps / 1e12,
+                 "count": "3 x 2 m N^2 + 2 x 2 m^2 q^4 + iters x (2 N^2 b + 4 N b^2) + b^3 x sweeps (dense, "
+                          "FP64-equivalent)",
+                 "subspace_iters_mean": it_mean, "jacobi_sweeps_mean": sw_mean}
+    if tcls in kern:
+        tflops = kern[tcls]["flops"] / timed_steps * sps / 1e12
+        peak_t, src_t = tensor_peak(prec)
+        step_roof.update({"tensor_flops_per_step": kern[tcls]["flops"] / timed_steps,
+                          "tensor_tflops": tflops, "tensor_peak": peak_t, "tensor_frac": tflops / peak_t,
+                          "tensor_count": ("bf16 digit-pair products (28 per FP64 product)" if prec == "ozaki64"
+                                           else f"{prec} tensor-core products"),
+                          "tensor_peak_source": src_t})
     res = {"prec": prec, "value": world * timed_steps / (ms_max / 1e3), "ms_per_step": ms_max / timed_steps,
-           "roofline": roof, "roofline_tensor": roof_t, "gpu_launches": launches, "clocks": clk,
+           "roofline": roof, "roofline_tensor": roof_t, "step_roofline": step_roof, "gpu_launches": launches,
+           "clocks": clk,
            "subspace_iters_mean": float(np.mean(iters)), "jacobi_sweeps_mean": float(np.mean(sweeps)),
            "rayleigh_ritz_paths": rr_paths,
            "kernels_ms_per_step": {k: round(v["ms"] / timed_steps, 3) for k, v in kern.items()},
@@ -345,6 +393,43 @@ def accuracy_gate(args, blob, local):
         d = max(abs(a - b) / abs(b) for a, b in zip(runs[prec], ref))
         res[prec] = {"max_rel_df": d, "passes": d <= 1e-10}
     return res
+
+
+def errors_vs_oracle(args, local):
+    """Every precision form against the stored oracle trajectory
+    (tests/golden/oracle_q20_m256_T0.4398_20steps.json, written by a script
+    that calls only the CPU oracle): 20 steps of Algorithm 3 from the
+    fixed-boundary state with converged subspace iterations, then the
+    observables.  Per form: the largest |df|/|f| over the steps (f from kappa,
+    reading R5) and |df|/|f|, |dM|, |dS_E| of the observables."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_q20_m{args.m}_T{args.T}_20steps.json")
+    if not os.path.exists(path):
+        return None
+    ref = json.load(open(path))
+    from paper_2004_08669_gb300 import ctm, workloads as W
+    T = ref["T"]
+    out = {"reference": os.path.relpath(path, ROOT), "steps": len(ref["steps"]),
+           "note": "GPU forms vs the FP64 CPU oracle (dense diagonalisation) from the fixed-boundary state"}
+    o = ref["observables"]
+    for prec in ("fp64", "ozaki64", "tf32", "bf16"):
+        # Ritz tolerances at the forms' rounding floors for K = N = 5120
+        tol = {"fp64": 3e-13, "ozaki64": 1e-11}.get(prec, 0.0)
+        g = ctm.CTMRG(W.dodecahedron(), ref["m"], ref["beta"], prec=prec, device=f"cuda:{local}",
+                      subspace_tol=tol, max_subspace_iters=200)
+        try:
+            dfm = 0.0
+            for r in ref["steps"]:
+                _, info, _ = g.step(1)
+                fg, fo = -0.5 * T * math.log(info["kappa"]), -0.5 * T * math.log(r["kappa"])
+                dfm = max(dfm, abs(fg - fo) / abs(fo))
+            ob = g.observables()
+            out[prec] = {"max_rel_df_per_step": dfm, "rel_df": abs(ob["f"] - o["f"]) / abs(o["f"]),
+                         "abs_dM": abs(ob["M"] - o["M"]), "abs_dS_E": abs(ob["S_E"] - o["S_E"])}
+        except Exception as e:
+            out[prec] = {"error": f"{type(e).__name__}: {e}"}
+        finally:
+            g.close()
+    return out
 
 
 def run_ours(args):
@@ -393,17 +478,19 @@ def run_ours(args):
            "d2h_bytes_per_step": 8 * m}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, args)
+        cpu = cpu_baseline(args)
     gate = None
     if args.gate_steps > 0 and rank == 0:
         gate = accuracy_gate(args, blob, local)
+        gate["vs_oracle"] = errors_vs_oracle(args, local)
     g.close()
     others = {}
     for p in modes[1:]:
         try:
             g2, r2 = run_mode(args, p, local, world, barrier, args.steps)
             g2.close()
-            others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "roofline_tensor", "gpu_launches",
+            others[p] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "roofline_tensor", "step_roofline",
+                                            "gpu_launches",
                                             "subspace_iters_mean", "jacobi_sweeps_mean", "rayleigh_ritz_paths",
                                             "kernels_ms_per_step", "clocks", "tuned_shapes")}
         except Exception as e:  # a failing form must not lose the others' numbers
@@ -418,7 +505,8 @@ def run_ours(args):
                       "subspace_iters_mean": res["subspace_iters_mean"],
                       "jacobi_sweeps_mean": res["jacobi_sweeps_mean"],
                       "rayleigh_ritz_paths": res["rayleigh_ritz_paths"], "prep_steps": args.prep},
-           "roofline": res["roofline"], "roofline_tensor": res["roofline_tensor"], "e2e": e2e,
+           "roofline": res["roofline"], "roofline_tensor": res["roofline_tensor"],
+           "step_roofline": res["step_roofline"], "e2e": e2e,
            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
            "kernels_ms_per_step": res["kernels_ms_per_step"], "tuned_shapes": res["tuned_shapes"]}
     if others:
@@ -724,8 +812,9 @@ def run_profile(args):
     """The timed workload's steps bracketed for a profiler, nothing measured."""
     import torch
 
-    from paper_2004_08669_gb300 import build, ctm, workloads as W
+    from paper_2004_08669_gb300 import build
     build.build()
+    from paper_2004_08669_gb300 import ctm, workloads as W
     prec = args.modes.split(",")[0]
     g = ctm.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T, prec=prec, device="cuda:0",
                   max_subspace_iters=args.subspace_iters)

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["ctm.cu", "gemm_f64.cu", "eig_f64.cu", "tc_gemm.cu", "oz_gemm.cu", "xi.cu", "tangent.cu"]
+SOURCES = ["ctm.cu", "gemm_f64.cu", "eig_f64.cu", "rr_refine.cu", "tc_gemm.cu", "oz_gemm.cu", "xi.cu", "tangent.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -66,7 +66,7 @@ struct Layout {
         off_part, off_red, off_A0, off_A1, off_S, off_diag, off_rank, off_gd, off_gQ, off_gk, off_ctl,
         off_S1, off_mfull, off_colv, off_opP, off_opPw, off_opC, off_opV, off_opUp, off_opU, off_tcerr, off_ozP, off_ozBig,
         off_ozSA, off_ozSB, off_ozeP, off_ozeBig, off_ozeSA, off_ozeSB, off_oaX, off_oaW1, off_oaS, off_oaR, off_oaE,
-        off_oapart, off_oaclus, off_tcpart, total;
+        off_oapart, off_oaclus, off_tcpart, off_rrc, total;
     size_t tcpart_cap;  // doubles of the split-K partial buffer of the tensor-core GEMM
     int slices;     // digit planes of the FP64-emulating form
     size_t part_cap;  // doubles of the split-K partial buffer
@@ -141,6 +141,8 @@ Layout make_layout(const ctm_config& c) {
     L.off_oaE = take(b * b * d);
     L.off_oapart = take(1024 * d);
     L.off_oaclus = take(np * sizeof(int));
+    // cluster-aware refinement of the Rayleigh-Ritz solve (mixed forms)
+    L.off_rrc = (c.prec != CTM_FP64 && ctm::rrc_supported(L.b)) ? take(ctm::rrc_workspace_bytes(L.b)) : 0;
     L.prec = c.prec;
     L.slices = c.ozaki_slices > 0 ? c.ozaki_slices : 7;
     L.esz = (c.prec == CTM_BF16) ? 2 : (c.prec == CTM_TF32 ? 4 : 0);
@@ -207,6 +209,9 @@ struct ctm_handle {
     int *ozeP = nullptr, *ozeBig = nullptr, *ozeSA = nullptr, *ozeSB = nullptr;
     ctm::EigWork ew;
     ctm::OaWork oa;
+    ctm::RrcWork rrc{};
+    bool have_rrc = false;
+    long long rrc_solves = 0, rrc_fails = 0;  // cluster refinement attempts that failed
     long long rr_refined = 0, rr_jacobi = 0;  // Rayleigh-Ritz solves by path
     int last_backward_iters = 0;              // GMRES iterations of the last ctm_step_backward
     double last_backward_residual = 0.0;
@@ -494,11 +499,11 @@ inline int grid_for(size_t work, int cap = 152 * 8) {
 // --------------------------------------------------------------- profiling
 enum ProfClass {
     PC_GEMM = 0, PC_WCONTRACT, PC_JACOBI, PC_CHOLQR, PC_TCGEMM, PC_CONVERT, PC_OZGEMM, PC_OZSPLIT, PC_SMALL,
-    PC_XI_W, PC_XI_VEC, PC_COUNT
+    PC_XI_W, PC_XI_VEC, PC_RRC, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT + 1] = {"gemm_f64", "wcontract_f64", "jacobi_f64", "cholqr_f64", "tc_gemm",
                                               "to_operand", "oz_gemm",  "oz_split",    "small",      "xi_wcontract",
-                                              "xi_lanczos", "all"};
+                                              "xi_lanczos", "rr_refine", "all"};
 
 cudaEvent_t take_event(ctm_handle* h) {
     if (h->evnext == h->evpool.size()) {
@@ -847,18 +852,49 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         // Rayleigh-Ritz: simultaneous Jacobi rotations when the block is warm
         // (H nearly diagonal), the cooperative Jacobi solver otherwise or as a
         // fallback.
-        cudaEvent_t ja = prof_begin(h);
+        int rrc_rec = -1;
+        bool rrc_tried = false;
+        if (h->have_rrc) {
+            // Mixed-precision forms: the cluster-aware refinement in one
+            // cooperative launch; the double-float Jacobi solver behind it
+            // runs only if the refinement gave up (a device-side flag), so
+            // the host does not wait for the outcome.  A cold block (H far
+            // from diagonal) goes to Jacobi directly.  A warm block whose
+            // strongly coupled pairs form a cluster above 32 states is
+            // recognised at the refinement's first check (no product is
+            // formed there), so it is tried at every warm solve.
+            rrc_tried = (!cold || it > 0);
+            CTM_CUDA(cudaMemsetAsync(&h->ctl->rrc_ok, 0, sizeof(int), h->st));
+            if (rrc_tried) {
+                cudaEvent_t ra = prof_begin(h);
+                CTM_CUDA(ctm::rr_cluster_refine(h->st, b, h->H, b, h->rrc, h->ew, h->ctl, 12));
+                prof_end(h, ra, PC_RRC, 1);
+                rrc_rec = (h->prof_on && ra) ? (int)h->recs.size() - 1 : -1;
+                ++h->rrc_solves;
+            }
+            cudaEvent_t ja2 = prof_begin(h);
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, 0.0, 0.0, true,
+                                     rrc_tried ? &h->ctl->rrc_ok : nullptr));
+            prof_end(h, ja2, PC_JACOBI, 4);
+            h->jac_rec = (h->prof_on && ja2) ? (int)h->recs.size() - 1 : -1;
+        }
+        cudaEvent_t ja = h->have_rrc ? nullptr : prof_begin(h);
         int nk_rr = 0, used = -1;
         // After repeated failures (a dense spectrum whose near-degenerate
         // Ritz values are not yet separated) the refinement is only retried
         // every 16th solve, so a failing attempt does not tax every step.
-        const bool try_refine = (!cold || it > 0) && (h->rr_fail_streak < 3 || (h->rr_jacobi % 16) == 0);
-        if (try_refine) {
+        const bool try_refine =
+            !h->have_rrc && (!cold || it > 0) && (h->rr_fail_streak < 3 || (h->rr_jacobi % 16) == 0);
+        if (h->have_rrc) {
+            // outcome known after the next synchronisation
+        } else if (try_refine) {
             used = ctm::rr_refine_f64(h->st, b, std::min(b, m + 2), h->H, b, h->oa, h->ew, h->theta, h->Sb, b, 1e-13,
                                       8, h->ctl, h->hctl, &nk_rr);
             h->rr_fail_streak = used < 0 ? h->rr_fail_streak + 1 : 0;
         }
-        if (used < 0) {
+        if (h->have_rrc) {
+            // recorded above
+        } else if (used < 0) {
             // Full FP64 accuracy: the corner is stored diagonal in the Ritz
             // basis, so any coupling left unrotated enters the next extension
             // at first order.
@@ -871,9 +907,11 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         } else {
             ++h->rr_refined;
         }
-        prof_end(h, ja, PC_JACOBI, nk_rr);
-        // the solve's algorithmic FLOPs are known after the next sync
-        h->jac_rec = (used < 0 && h->prof_on && ja) ? (int)h->recs.size() - 1 : -1;
+        if (!h->have_rrc) {
+            prof_end(h, ja, PC_JACOBI, nk_rr);
+            // the solve's algorithmic FLOPs are known after the next sync
+            h->jac_rec = (used < 0 && h->prof_on && ja) ? (int)h->recs.size() - 1 : -1;
+        }
         if (oz_small(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {h->V, 1, N, nullptr}, OZ_SA, true, {h->Sb, b, 1, nullptr}, OZ_SB, true,
                                  h->Z, N);
@@ -892,6 +930,31 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         ctm_status s = sync_ctl(h);
         if (s != CTM_OK) return s;
         h->last_resid = h->hctl->resid;
+        if (h->have_rrc) {
+            const bool ok = rrc_tried && h->hctl->rrc_ok == 1;
+            if (ok) {
+                ++h->rr_refined;
+                h->rr_fail_streak = 0;
+            } else {
+                ++h->rr_jacobi;
+                if (rrc_tried) {
+                    ++h->rrc_fails;
+                    ++h->rr_fail_streak;
+                }
+            }
+            h->oa.fail_reason = rrc_tried ? h->hctl->rrc_fail : 0;
+            h->oa.last_iter = h->hctl->rrc_iters;
+            float mc;
+            memcpy(&mc, &h->hctl->rrc_maxc, sizeof(float));
+            h->oa.last_max = (double)mc;
+            if (rrc_rec >= 0 && rrc_rec < (int)h->recs.size()) {
+                // per measured iteration H X, X^t X (half) and X^t (H X)
+                // (half); per update X (I + E) Q: 2 b^3 FLOP per full product
+                const double b3 = (double)b * b * b;
+                const int iters = h->hctl->rrc_iters;
+                h->recs[rrc_rec].flops = 2.0 * b3 * (2.0 * iters + (iters > 0 ? iters - 1 : 0));
+            }
+        }
         if (h->jac_rec >= 0 && h->jac_rec < (int)h->recs.size()) {
             // a rotation of (p, q) updates rows p, q and columns p, q of A and
             // columns p, q of S: 3 x 2 x npad elements at 3 FLOP each
@@ -1468,6 +1531,10 @@ ctm_status ctm_init(ctm_handle** out, const ctm_config* cfg, void* cuda_stream) 
     h->oa.clus = (int*)(h->ws + L.off_oaclus);
     h->oa.gpart = D(L.off_part);
     h->oa.max_splits = L.splits;
+    if (L.off_rrc) {
+        ctm::rrc_carve(h->ws + L.off_rrc, L.b, h->rrc);
+        h->have_rrc = true;
+    }
     h->mfull = (int*)(h->ws + L.off_mfull);
     h->spins_h.assign(cfg->spins, cfg->spins + (size_t)cfg->q * cfg->dim);
 

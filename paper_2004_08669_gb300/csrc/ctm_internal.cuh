@@ -45,6 +45,27 @@ struct DevCtl {
     double obs_M_num, obs_u_num, obs_z4, obs_SE;
     // warm Rayleigh-Ritz refinement
     double oa_maxE;
+    // cluster-aware refinement of the mixed-precision forms (rr_refine.cu)
+    int rrc_ok;            // 1: the refinement produced the eigenpairs
+    int rrc_iters;         // its iterations (couplings measured)
+    int rrc_fail;          // 0 ok, 1 edge list full, 2 cluster too large, 3 iteration cap, 4 non-finite
+    int rrc_done;          // converged at the last check (read by all blocks)
+    int rrc_nedges;        // strongly coupled pairs found in the last check
+    int rrc_ncl;           // clusters (> 1 member) of the last check
+    int rrc_maxcl;         // largest cluster seen
+    unsigned int rrc_maxc;  // bits of the largest relative coupling (non-negative float)
+    unsigned int rrc_maxr;  // bits of the largest orthonormality defect
+    int rrc_pad;
+    // per iteration of the last refinement: largest coupling, largest
+    // orthonormality defect, strongly coupled pairs, largest cluster
+    float rrc_hist_c[16];
+    float rrc_hist_r[16];
+    int rrc_hist_ne[16];
+    int rrc_hist_cl[16];
+    // block 0's clock (ns) at the end of each phase of the last refinement's
+    // first 16 iterations: after P1, P2, P3a, P3b, P3c, P3e, P4
+    unsigned long long rrc_t0;
+    unsigned int rrc_tph[16][8];
 };
 
 // FP32 -> FP64 by bit construction (the conversion instruction runs on the

@@ -42,6 +42,32 @@ struct OaWork {
 
 int coop_grid_limit(const void* fn, int block, size_t smem);
 
+// Scratch of the cluster-aware Rayleigh-Ritz refinement (rr_refine.cu):
+// n x n double-float matrices (H, two X buffers, H X, X^t H X, X^t X, the
+// update), the clusters' rotations (32 x n), Ritz values, cluster lists and
+// the strongly coupled pairs.
+struct RrcWork {
+    float2 *Hd, *X0, *X1, *W, *S, *G, *F, *Qc;
+    double* lam;
+    int *root, *cid, *cpos, *clist, *coff, *edges;
+    int edge_cap;
+    int nmax;
+};
+size_t rrc_workspace_bytes(int n);
+void rrc_carve(void* base, int n, RrcWork& w);
+bool rrc_supported(int n);
+
+// Eigenpairs of the warm Rayleigh-Ritz matrix H (n x n, FP64, nearly
+// diagonal) by cluster-aware iterative refinement in double-float, one
+// cooperative launch.  On success it writes the eigenvectors into ew.S
+// (double-float, npad layout) and the Ritz values into ew.diag, exactly where
+// the double-float Jacobi solver leaves them, and sets ctl->rrc_ok = 1;
+// otherwise ctl->rrc_ok stays 0.  Launch jacobi_f64(..., df = true, skip =
+// &ctl->rrc_ok) behind it: it solves only when the refinement gave up, and
+// sorts in either case.
+cudaError_t rr_cluster_refine(cudaStream_t st, int n, const double* H, int ldh, RrcWork& w, EigWork& ew,
+                              DevCtl* ctl, int max_iter);
+
 // Warm-start Rayleigh-Ritz by simultaneous Jacobi rotations (Ogita-Aishima
 // refinement from X = I).  Returns iterations used, or -1 when it did not
 // converge (largest rotation <= tol) in max_iter iterations: fall back to Jacobi.
@@ -58,9 +84,11 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
 // keeps the purely relative criterion).
 // df: hold A and S as double-float pairs and compute on the FP32 pipe (about
 // 48 significant bits; for the mixed-precision forms).
+// skip (device, may be NULL): when *skip != 0 at run time the solve is left
+// out (another solver already wrote w.S and w.diag) and only the sort runs.
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
                        double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0,
-                       double floor_rel = 0.0, bool df = false);
+                       double floor_rel = 0.0, bool df = false, const int* skip = nullptr);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 // df: double-float arithmetic on the FP32 pipe (mixed-precision forms).
