@@ -288,7 +288,9 @@ ctm_config with_defaults(const ctm_config& c) {
         r.tol_cluster = (c.prec == CTM_BF16) ? 3e-2 : (c.prec == CTM_TF32 ? 3e-4 : 1e-10);
         // the digit expansion is relative to each row's largest entry, so the
         // small eigenvalues of C~ carry errors near 2^(-7s) K times |w_1|
-        if (c.prec == CTM_OZAKI64) r.tol_cluster = (c.ozaki_slices == 0 || c.ozaki_slices == 7) ? 1e-9 : 1e-8;
+        // with converged Ritz pairs (residual ~1e-11 |w_1|) seven slices resolve
+        // multiplets as the FP64 form does
+        if (c.prec == CTM_OZAKI64) r.tol_cluster = (c.ozaki_slices == 0 || c.ozaki_slices == 7) ? 1e-10 : 1e-8;
     }
     return r;
 }
@@ -725,7 +727,9 @@ void stage_extend(ctm_handle* h, const double* E1) {
 
 // Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR,
 // then one Newton-Schulz correction) or 3 (shifted CholQR, CholQR, then the
-// correction).  tmp is clobbered.
+// correction).  (Newton-Schulz corrections in place of the second
+// factorisation were measured: some warm blocks leave the shifted factor a
+// defect near 1, where they do not converge.)  tmp is clobbered.
 ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int passes) {
     const Layout& L = h->lay;
     const int N = L.N, b = L.b;
@@ -796,7 +800,14 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
     bool conv = false;
     int it = 0;
     // last measured Ritz residual (the previous stage's final one to start)
+    // A warm block starts from the previous step's Ritz pairs, whose C~ has
+    // since changed by about the step's convergence measure delta: the
+    // residual is predicted from the larger of the two.
     double r_meas = h->last_resid > 0.0 ? h->last_resid : 1.0;
+    if (!cold && h->steps > 0) {
+        const double dprev = h->last.delta;
+        r_meas = std::max(r_meas, std::isfinite(dprev) ? std::min(dprev, 1.0) : 1.0);
+    }
     int it_meas = -1;
     bool meas_here = false;
     if (L.esz) pconvert(h, N, N, h->C, N, nullptr, h->opC, L.ldN);  // C~ rows (symmetric)
@@ -2172,6 +2183,10 @@ struct SaveHeader {
     int live, steps, warm, warm_live;
     uint64_t seed;
     ctm_step_info last;
+    // host-side state of the subspace iteration's schedule (Rayleigh-Ritz
+    // timing), so that a resumed run repeats the uninterrupted one
+    double last_resid, resid_rate;
+    int rr_fail_streak, pad;
 };
 const uint64_t kMagic = 0x43544d5247423330ull;  // "CTMRGB30"
 }  // namespace
@@ -2179,14 +2194,17 @@ const uint64_t kMagic = 0x43544d5247423330ull;  // "CTMRGB30"
 ctm_status ctm_save(ctm_handle* h, void* buf, size_t* len) {
     if (!h || !len) return fail(CTM_EINVAL, "NULL argument");
     const Layout& L = h->lay;
-    size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b) +
+    size_t need = sizeof(SaveHeader) +
+                  sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b + (size_t)L.npad) +
                   sizeof(ctm::DevCtl);
     if (!buf) {
         *len = need;
         return CTM_OK;
     }
     if (*len < need) return fail(CTM_EINVAL, "buffer too small");
-    SaveHeader hd{kMagic, L.q, L.m, L.b, L.N, h->live, h->steps, h->warm ? 1 : 0, h->warm_live, h->seed, h->last};
+    SaveHeader hd{kMagic,      L.q,       L.m,           L.b,           L.N,     h->live,
+                  h->steps,    h->warm ? 1 : 0, h->warm_live, h->seed,    h->last, h->last_resid,
+                  h->resid_rate, h->rr_fail_streak, 0};
     char* p = (char*)buf;
     memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
@@ -2198,6 +2216,9 @@ ctm_status ctm_save(ctm_handle* h, void* buf, size_t* len) {
     p += sizeof(double) * L.m;
     CTM_CUDA(cudaMemcpyAsync(p, h->Zprev, sizeof(double) * L.N * L.b, cudaMemcpyDeviceToHost, h->st));
     p += sizeof(double) * L.N * L.b;
+    // the last Ritz values scale the next step's first block
+    CTM_CUDA(cudaMemcpyAsync(p, h->theta, sizeof(double) * L.npad, cudaMemcpyDeviceToHost, h->st));
+    p += sizeof(double) * L.npad;
     CTM_CUDA(cudaMemcpyAsync(p, h->ctl, sizeof(ctm::DevCtl), cudaMemcpyDeviceToHost, h->st));
     CTM_CUDA(cudaStreamSynchronize(h->st));
     *len = need;
@@ -2207,7 +2228,8 @@ ctm_status ctm_save(ctm_handle* h, void* buf, size_t* len) {
 ctm_status ctm_load(ctm_handle* h, const void* buf, size_t len) {
     if (!h || !buf) return fail(CTM_EINVAL, "NULL argument");
     const Layout& L = h->lay;
-    size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b) +
+    size_t need = sizeof(SaveHeader) +
+                  sizeof(double) * ((size_t)L.m * L.N + 2 * (size_t)L.m + (size_t)L.N * L.b + (size_t)L.npad) +
                   sizeof(ctm::DevCtl);
     if (len < need) return fail(CTM_EINVAL, "buffer too small");
     SaveHeader hd;
@@ -2223,6 +2245,8 @@ ctm_status ctm_load(ctm_handle* h, const void* buf, size_t len) {
     p += sizeof(double) * L.m;
     CTM_CUDA(cudaMemcpyAsync(h->Zprev, p, sizeof(double) * L.N * L.b, cudaMemcpyHostToDevice, h->st));
     p += sizeof(double) * L.N * L.b;
+    CTM_CUDA(cudaMemcpyAsync(h->theta, p, sizeof(double) * L.npad, cudaMemcpyHostToDevice, h->st));
+    p += sizeof(double) * L.npad;
     CTM_CUDA(cudaMemcpyAsync(h->ctl, p, sizeof(ctm::DevCtl), cudaMemcpyHostToDevice, h->st));
     CTM_CUDA(cudaStreamSynchronize(h->st));
     h->live = hd.live;
@@ -2231,6 +2255,9 @@ ctm_status ctm_load(ctm_handle* h, const void* buf, size_t len) {
     h->warm_live = hd.warm_live;
     h->seed = hd.seed;
     h->last = hd.last;
+    h->last_resid = hd.last_resid;
+    h->resid_rate = hd.resid_rate;
+    h->rr_fail_streak = hd.rr_fail_streak;
     return CTM_OK;
 }
 

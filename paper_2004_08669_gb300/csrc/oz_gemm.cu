@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(256) k_oz_split_rows(int R, int K, int s, cons
 }
 
 // Stages of the TMA ring: all S digit planes of A (8 KB each) and B (4 KB
-// each) per stage; three stages fit in shared memory up to S = 6.
+// each) per stage; three stages fit in shared memory up to S = 6.  (A 16-wide
+// K-tile with a four-stage ring was measured slower at S = 7.)
 template <int S>
 struct OzStages {
     static constexpr int value = (S <= 6) ? 3 : 2;
@@ -319,11 +320,16 @@ __global__ void __launch_bounds__(320, 1)
     // tile t: its origin, K range, and whether it has work (lower q x q block
     // triangle only when lowq > 0: a tile whose block rows all lie above its
     // first block column is skipped)
+    // The tile index runs fastest over the dimension with fewer tiles: the
+    // CTAs that take consecutive tiles then share the other operand's tile
+    // (C~'s digit planes in C~ V, X's in U^t X), read once from DRAM and
+    // from L2 by the rest.
+    const bool n_fast = tn < tm;
     auto tile_of = [&](long t, int& m0, int& n0, int& kbeg, int& nk) -> bool {
         const int z = (int)(t / ((long)tm * tn));
         const long xy = t - (long)z * tm * tn;
-        m0 = (int)(xy % tm) * kOzBM;
-        n0 = (int)(xy / tm) * kOzBN;
+        m0 = (int)(n_fast ? xy / tn : xy % tm) * kOzBM;
+        n0 = (int)(n_fast ? xy % tn : xy / tm) * kOzBN;
         kbeg = z * kper;
         nk = (min(K, kbeg + kper) - kbeg + kOzKT - 1) / kOzKT;
         return !(lowq > 0 && (min(m0 + kOzBM, M) - 1) / lowq < n0 / lowq);

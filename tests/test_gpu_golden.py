@@ -1,14 +1,14 @@
 """GPU runs against stored oracle runs (tests/golden/, written by
 tests/golden/make_oracle_runs.py, which calls only the CPU oracle).
 
-1. The benchmark's regime reaches the oracle's fixed point.  The timed steps
-   cap the subspace iteration at two iterations per step, so a step's Ritz
-   pairs are not converged: the trajectory is not the oracle's.  Its fixed
-   point is, because at the fixed point the warm start (the previous step's
-   Ritz block) is the exact leading eigenspace.  At q = 20, T = 0.4398 with
-   m = 32 and 64 (N = 640, 1280) the capped run, FP64 and FP64 emulated on the
-   tensor cores, is taken to delta < 1e-12 and its f, M, u and S_E compared
-   with the oracle's converged run.
+1. Exact steps reach the oracle's fixed point.  Each step converges its
+   Ritz pairs to the form's rounding floor (as the benchmark's timed steps
+   do); at q = 20, T = 0.4398 with m = 32 and 64 (N = 640, 1280) the run is
+   taken to delta < 1e-12 in FP64 and in FP64 emulated on the tensor cores,
+   and its f, M, u and S_E compared with the oracle's converged run.  (An
+   inexact variant with two subspace iterations per step is not: its
+   per-step eigenvector errors of about 1e-3 break the corner's C3v symmetry,
+   and at m = 64 it settles on a fixed point 1.5e-7 off in f and 1e-3 in M.)
 2. Per-form errors at the benchmarked size: q = 20, m = 256, T = 0.4398, 20
    steps of Algorithm 3 from the fixed-boundary state in every precision form
    (converged subspace iterations each step), against the oracle's 20 steps:
@@ -49,15 +49,17 @@ def ctm():
 
 @pytest.mark.parametrize("m", [32, 64])
 @pytest.mark.parametrize("prec", ["fp64", "ozaki64"])
-def test_capped_subspace_regime_reaches_oracle_fixed_point(ctm, m, prec):
+def test_exact_steps_reach_oracle_fixed_point(ctm, m, prec):
     ref = _load(f"oracle_q20_m{m}_T0.4398_fixed_point.json")
-    g = ctm.CTMRG(W.dodecahedron(), m, ref["beta"], prec=prec, max_subspace_iters=2, tol_spectrum=1e-12)
+    tol = {"fp64": 1e-13, "ozaki64": 1e-11}[prec]
+    g = ctm.CTMRG(W.dodecahedron(), m, ref["beta"], prec=prec, max_subspace_iters=200, subspace_tol=tol,
+                  tol_spectrum=1e-12)
     done, info = g.run(20000)
     assert info["converged"], info
     ob = g.observables()
     r = ref["observables"]
     df = abs(ob["f"] - r["f"]) / abs(r["f"])
-    print(f"\n{prec} m={m}: {done} capped steps (oracle {ref['steps_run']}), |df|/|f| = {df:.2e}, "
+    print(f"\n{prec} m={m}: {done} steps (oracle {ref['steps_run']}), |df|/|f| = {df:.2e}, "
           f"|dM| = {abs(ob['M'] - r['M']):.2e}, |du| = {abs(ob['u'] - r['u']):.2e}, "
           f"|dS_E| = {abs(ob['S_E'] - r['S_E']):.2e}")
     assert df <= 1e-12
