@@ -751,6 +751,19 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
             // orthonormal to O(|E|^2) and needs no factorisation.
             ctm::ns_coeff_f64(h->st, b, h->G, b, h->Linv, b);
             prof_end(h, a, PC_CHOLQR, 1, 0.0, 8.0 * 2.0 * b * b);
+        } else if (passes == 3 && i == 1) {
+            // The second pass starts from the shifted factor's output, whose
+            // defect G - I is usually about the shift over the smallest
+            // eigenvalue of the first Gram matrix (1e-5 .. 1e-4): then two
+            // Newton-Schulz corrections (this pass and the last) reach FP64
+            // orthonormality (each squares the defect, 0.42 d^4 < 1e-16 for
+            // d <= 1e-4) and the factorisation is skipped on the device;
+            // otherwise (a defect near 1, where the corrections do not
+            // converge) the block is factorised again.
+            ctm::orth_check(h->st, b, h->G, b, 1e-4, h->Linv, b, h->ctl);
+            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, 0.0, h->ctl, h->lay.prec != CTM_FP64, &h->ctl->orth_ns));
+            ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1, &h->ctl->orth_ns);
+            prof_end(h, a, PC_CHOLQR, 4, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
         } else {
             double shift_rel =
                 (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;

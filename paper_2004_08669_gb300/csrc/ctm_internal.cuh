@@ -62,6 +62,10 @@ struct DevCtl {
     float rrc_hist_r[16];
     int rrc_hist_ne[16];
     int rrc_hist_cl[16];
+    // re-orthonormalisation: 1 when the block's defect max|G - I| was small
+    // enough for a Newton-Schulz correction in place of a factorisation
+    int orth_ns;
+    float orth_defect;   // that defect (the last check)
     // block 0's clock (ns) at the end of each phase of the last refinement's
     // first 16 iterations: after P1, P2, P3a, P3b, P3c, P3e, P4
     unsigned long long rrc_t0;

@@ -774,8 +774,12 @@ struct CDF {
 };
 
 template <class CA>
-__global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl) {
+__global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, double shift_rel, DevCtl* ctl,
+                                                    const int* skip) {
     using T = typename CA::T;
+    // a Newton-Schulz correction replaces this factorisation: every block
+    // leaves before the first barrier
+    if (skip && *(volatile const int*)skip) return;
     __shared__ T D[32][33];
     __shared__ T dinv[32];
     __shared__ T dinv2[32];
@@ -921,7 +925,8 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
 // and zero-padded.  One warp per block, one column of the inverse per lane
 // (forward substitution with the pivots' reciprocals taken once).
 __global__ void __launch_bounds__(32) k_trinv_diag(int n, const double* __restrict__ L, int ld,
-                                                   double* __restrict__ Dinv) {
+                                                   double* __restrict__ Dinv, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double Ls[32][33];
     __shared__ double rd[32];
     const int I = blockIdx.x, r0 = 32 * I, nbI = min(32, n - r0);
@@ -951,7 +956,8 @@ __global__ void __launch_bounds__(32) k_trinv_diag(int n, const double* __restri
 // the eight warps, with the next tile prefetched into registers.
 __global__ void __launch_bounds__(256) k_trinv_cols(int n, const double* __restrict__ L, int ld,
                                                     const double* __restrict__ Dinv, double* __restrict__ X,
-                                                    int ldx) {
+                                                    int ldx, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     extern __shared__ double tsh[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int npad = ((n + 31) / 32) * 32, nb = npad / 32;
@@ -1319,7 +1325,8 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
     return jacobi_launch<J64>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel, skip);
 }
 
-cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl, bool df) {
+cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl, bool df,
+                         const int* skip) {
     // shift is relative: the kernel adds shift * trace(G) to the diagonal.
     // ctl->chol_status is sticky (atomicMax): the caller clears it.
     cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), st);
@@ -1330,14 +1337,15 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
     if (grid > limit) grid = limit;
     if (grid > 2 * 152) grid = 2 * 152;
     if (grid < 1) grid = 1;
-    void* args[] = {&n, &G, &ld, &shift, &ctl};
+    void* args[] = {&n, &G, &ld, &shift, &ctl, &skip};
     return launch_coop(df ? (const void*)k_cholesky<CDF> : (const void*)k_cholesky<C64>, grid, 256, args, 0, st);
 }
 
-void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch) {
+void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch,
+               const int* skip) {
     // scratch: ceil(n / 32) * 1024 doubles (the diagonal blocks' inverses)
     const int nb = (n + 31) / 32;
-    k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch);
+    k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch, skip);
     const size_t smem = ((size_t)8 * nb * 32 + 3 * 32 * 33 + 8 * 32) * sizeof(double);
     static std::mutex mu;
     static size_t attr = 48 * 1024;
@@ -1348,7 +1356,7 @@ void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int l
             attr = smem;
         }
     }
-    k_trinv_cols<<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx);
+    k_trinv_cols<<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx, skip);
 }
 
 // X = (3 I - (G + G^t)/2) / 2.
@@ -1363,6 +1371,47 @@ __global__ void k_ns_coeff(int b, const double* __restrict__ G, int ldg, double*
 
 void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, int ldx) {
     k_ns_coeff<<<grid_for((size_t)b * b), 256, 0, st>>>(b, G, ldg, X, ldx);
+}
+
+// One block: the defect d = max|G - I| of a Gram matrix; when d <= thresh it
+// sets ctl->orth_ns and writes the Newton-Schulz coefficient X = (3I - G)/2
+// (the factorisation behind it is then skipped), else clears the flag.
+__global__ void __launch_bounds__(1024) k_orth_check(int b, const double* __restrict__ G, int ldg, double thresh,
+                                                     double* __restrict__ X, int ldx, DevCtl* ctl) {
+    __shared__ double red[32];
+    __shared__ int s_ns;
+    double d = 0.0;
+    const size_t tot = (size_t)b * b;
+    for (size_t e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int i = (int)(e % b), j = (int)(e / b);
+        const double g = G[i + (size_t)ldg * j];
+        const double v = fabs(g - (i == j ? 1.0 : 0.0));
+        d = (v > d || v != v) ? v : d;  // NaN propagates
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, d, o);
+        d = (t > d || t != t) ? t : d;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
+        s_ns = (m <= thresh) ? 1 : 0;
+        ctl->orth_ns = s_ns;
+        ctl->orth_defect = (float)m;
+    }
+    __syncthreads();
+    if (!s_ns) return;
+    for (size_t e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int i = (int)(e % b), j = (int)(e / b);
+        const double g = 0.5 * (G[i + (size_t)ldg * j] + G[j + (size_t)ldg * i]);
+        X[i + (size_t)ldx * j] = (i == j ? 1.5 : 0.0) - 0.5 * g;
+    }
+}
+
+void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl) {
+    k_orth_check<<<1, 1024, 0, st>>>(b, G, ldg, thresh, X, ldx, ctl);
 }
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,

@@ -92,15 +92,24 @@ cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 // df: double-float arithmetic on the FP32 pipe (mixed-precision forms).
-cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl, bool df = false);
+// skip (device, may be NULL): when *skip != 0 at run time the factorisation
+// is left out (orth_check chose a Newton-Schulz correction).
+cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift_rel, DevCtl* ctl, bool df = false,
+                         const int* skip = nullptr);
 
 // X = (3 I - (G + G^t)/2) / 2: the Newton-Schulz orthogonality correction
 // of a block whose Gram matrix G is close to I.
 void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, int ldx);
 
 // X = L^{-1} for lower-triangular L (upper part of X zeroed); scratch:
-// ceil(n / 32) * 1024 doubles.
-void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch);
+// ceil(n / 32) * 1024 doubles.  skip as for cholesky_f64.
+void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch,
+               const int* skip = nullptr);
+
+// The defect max|G - I| of a Gram matrix; if it is at most thresh, sets
+// ctl->orth_ns and writes X = (3I - G)/2 (a Newton-Schulz correction),
+// otherwise clears ctl->orth_ns (pass it as skip to cholesky_f64/trinv_f64).
+void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl);
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
                const double* theta, double* res);
