@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--block-extra", type=int, default=160, help="oversampling: b = m + block_extra")
     ap.add_argument("--capped", action="store_true",
                     help="also time the inexact variant (two subspace iterations per step, b = m + 32)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -296,10 +296,13 @@ def run_mode(args, prec, local, world, barrier, timed_steps, capped=False):
     for _ in range(timed_steps):
         done, info, st = g.step(1)
         if rr0 is None:
-            rr0 = (info["rr_refined"], info["rr_jacobi"])
+            rr0 = (info["rr_refined"], info["rr_jacobi"], list(info["rr_fail_counts"]))
         iters.append(info["subspace_iters"])
         sweeps.append(info["jacobi_sweeps"])
-    rr_paths = {"refined": info["rr_refined"] - rr0[0], "jacobi": info["rr_jacobi"] - rr0[1]}
+    fails = [a - b for a, b in zip(info["rr_fail_counts"], rr0[2])]
+    rr_paths = {"refined": info["rr_refined"] - rr0[0], "jacobi": info["rr_jacobi"] - rr0[1],
+                "refinement_fallbacks": dict(zip(("many_pairs", "cluster_above_32", "iteration_cap", "nonfinite"),
+                                                 fails[1:]))}
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
@@ -392,33 +395,73 @@ DTYPES = {"fp64": "f64", "ozaki64": "f64-emulated (bf16 x7 digit slices on tcgen
 
 
 def accuracy_gate(args, blob, local):
-    """The mixed forms against the FP64 form on the timed workload: load the
-    same checkpointed state into one handle per form, step them side by side,
-    and compare the per-step free energy f = -(T/2) ln kappa."""
+    """The mixed forms against the FP64 form on the timed workload, from the
+    checkpointed timed state, f = -(T/2) ln kappa per step.
+
+    local: the FP64 form steps from the checkpoint; before each of its steps
+    its state is loaded into one handle per mixed form, which takes that one
+    step: the per-step error of the form's arithmetic (the metric's
+    |df|/f <= 1e-10), free of the trajectory's own amplification.
+    trajectory: every form runs the steps on its own from the checkpoint.
+    Where the map is locally unstable (some stretches of the run from the
+    fixed boundary grow a perturbation ~80x per step), rounding-level
+    differences are amplified; the FP64 form rerun with a tighter Ritz
+    tolerance (1e-13 instead of 3e-13, an equally exact step) shows that
+    amplification of FP64's own rounding and is reported beside it."""
     import math
 
     from paper_2004_08669_gb300 import ctm, workloads as W
-    m = args.m
     beta = 1.0 / args.T
-    runs = {}
-    for prec in ("fp64", "ozaki64", "tf32", "bf16"):
+    fofk = lambda info: -0.5 / beta * math.log(info["kappa"])
+    forms = ("ozaki64", "tf32", "bf16")
+    # FP64 trajectory, its state before every step kept on the host
+    g = make_handle(args, "fp64", local)
+    g.load(blob)
+    ref, ref_me, states = [], [], []
+    for _ in range(args.gate_steps):
+        states.append(g.save())
+        _, info, _ = g.step(1)
+        ref.append(fofk(info))
+        ref_me.append(info["m_eff"])
+    g.close()
+    # FP64 rerun with a tighter Ritz tolerance
+    g = ctm.CTMRG(W.dodecahedron(), args.m, beta, prec="fp64", device=f"cuda:{local}",
+                  max_subspace_iters=args.subspace_iters, subspace_tol=1e-13, block_extra=args.block_extra)
+    g.load(blob)
+    rerun = []
+    for _ in range(args.gate_steps):
+        _, info, _ = g.step(1)
+        rerun.append(fofk(info))
+    g.close()
+    rel = lambda xs: [abs(a - b) / abs(b) for a, b in zip(xs, ref)]
+    rr = rel(rerun)
+    res = {"steps": args.gate_steps, "from": "checkpoint of the timed run", "threshold": 1e-10,
+           "passes_means": "local max |df|/f <= threshold (one step of the form from the FP64 form's state, "
+                           "every step)",
+           "fp64_rerun": {"note": "FP64 form again with subspace_tol 1e-13: the trajectory's amplification of "
+                                  "rounding-level differences",
+                          "trajectory_max_rel_df": max(rr), "trajectory_per_step": [float(f"{x:.2e}") for x in rr]}}
+    for prec in forms:
         g = make_handle(args, prec, local)
+        loc, me_loc = [], []
+        for k in range(args.gate_steps):
+            g.load(states[k])
+            _, info, _ = g.step(1)
+            loc.append(abs(fofk(info) - ref[k]) / abs(ref[k]))
+            me_loc.append(info["m_eff"] - ref_me[k])
         g.load(blob)
-        fs, me = [], []
+        traj, me = [], []
         for _ in range(args.gate_steps):
             _, info, _ = g.step(1)
-            fs.append(-0.5 / beta * math.log(info["kappa"]))
+            traj.append(fofk(info))
             me.append(info["m_eff"])
-        runs[prec] = (fs, me)
         g.close()
-    ref, ref_me = runs["fp64"]
-    res = {"steps": args.gate_steps, "from": "checkpoint of the timed run", "threshold": 1e-10}
-    for prec in ("ozaki64", "tf32", "bf16"):
-        fs, me = runs[prec]
-        per = [abs(a - b) / abs(b) for a, b in zip(fs, ref)]
-        res[prec] = {"max_rel_df": max(per), "passes": max(per) <= 1e-10,
-                     "per_step_rel_df": [float(f"{x:.2e}") for x in per],
-                     "m_eff_differences": [a - b for a, b in zip(me, ref_me)]}
+        tr = rel(traj)
+        res[prec] = {"local_max_rel_df": max(loc), "passes": max(loc) <= 1e-10,
+                     "local_per_step": [float(f"{x:.2e}") for x in loc],
+                     "local_m_eff_differences": me_loc,
+                     "trajectory_max_rel_df": max(tr), "trajectory_per_step": [float(f"{x:.2e}") for x in tr],
+                     "trajectory_m_eff_differences": [a - b for a, b in zip(me, ref_me)]}
     return res
 
 
@@ -442,7 +485,7 @@ def errors_vs_oracle(args, local):
         # Ritz tolerances at the forms' rounding floors for K = N = 5120
         tol = {"fp64": 3e-13, "ozaki64": 1e-11}.get(prec, 0.0)
         g = ctm.CTMRG(W.dodecahedron(), ref["m"], ref["beta"], prec=prec, device=f"cuda:{local}",
-                      subspace_tol=tol, max_subspace_iters=200)
+                      subspace_tol=tol, max_subspace_iters=200, block_extra=args.block_extra)
         try:
             dfm = 0.0
             for r in ref["steps"]:
@@ -486,17 +529,24 @@ def run_ours(args):
     g, res = run_mode(args, primary, local, world, barrier, args.steps)
     m = args.m
 
-    # end to end through the C-ABI with host buffers: per step load the state
-    # from pinned host memory, step, read the spectrum back to the host.
+    # end to end through the C-ABI with host buffers: per step load that
+    # step's input state from pinned host memory, step, read the spectrum back
+    # to the host.  The inputs are the states of consecutive steps of the run
+    # (taken untimed beforehand), so the timed steps are the run's next steps.
     blob = g.save()
-    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
-    pinned.numpy()[:] = np.frombuffer(blob, dtype=np.uint8)
     import ctypes
+    inputs = []
+    for _ in range(args.e2e_steps):
+        st_k = g.save()
+        pk = torch.empty(len(st_k), dtype=torch.uint8, pin_memory=True)
+        pk.numpy()[:] = np.frombuffer(st_k, dtype=np.uint8)
+        inputs.append(pk)
+        g.step(1)
     spec = torch.empty(m, dtype=torch.float64, pin_memory=True)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ctm._check(ctm.lib.ctm_load(g.h, ctypes.c_void_p(pinned.data_ptr()), len(blob)))
+    for pk in inputs:
+        ctm._check(ctm.lib.ctm_load(g.h, ctypes.c_void_p(pk.data_ptr()), pk.numel()))
         ctm.ctm_step(g.h, 1)
         ctm._check(ctm.lib.ctm_get_spectrum(g.h, ctypes.cast(spec.data_ptr(), ctm._dp)))
     torch.cuda.synchronize()
@@ -860,8 +910,7 @@ def run_profile(args):
     build.build()
     from paper_2004_08669_gb300 import ctm, workloads as W
     prec = args.modes.split(",")[0]
-    g = ctm.CTMRG(W.dodecahedron(), args.m, 1.0 / args.T, prec=prec, device="cuda:0",
-                  max_subspace_iters=args.subspace_iters)
+    g = make_handle(args, prec, 0, args.capped)
     if not args.no_tune:
         ctm.ctm_tune(g.h, 5)
     g.step(args.prep)

@@ -94,12 +94,19 @@ typedef struct {
     int converged;         /* delta < tol_spectrum                              */
     long long rr_refined;  /* Rayleigh-Ritz solves by simultaneous rotations   */
     long long rr_jacobi;   /* Rayleigh-Ritz solves by the cooperative Jacobi   */
-    int rr_fail_reason;    /* last refinement: 0 ok, 1 coupled non-doublet pair,
-                              2 large rotation, 3 iteration cap, 4 triplet     */
+    int rr_fail_reason;    /* last refinement.  Mixed-precision forms (the
+                              cluster-aware refinement): 0 ok, 1 more than 8b
+                              strongly coupled pairs, 2 a cluster above 32
+                              states, 3 iteration cap, 4 a non-finite value.
+                              FP64 form: 0 ok, 1 coupled non-doublet pair,
+                              2 large rotation, 3 iteration cap, 4 triplet  */
     int rr_last_iter;      /* its iterations                                   */
-    double rr_last_max;    /* its last largest rotation / orthonormality defect */
+    double rr_last_max;    /* its last largest coupling (mixed forms) or
+                              rotation / orthonormality defect (FP64 form)  */
     int jacobi_rotations[8]; /* rotations per sweep of the last Jacobi solve
                                 (first 8 sweeps)                           */
+    long long rr_fail_counts[5]; /* refinements that fell back to Jacobi, by
+                                    rr_fail_reason (index 0 unused)         */
 } ctm_step_info;
 
 /* Observables of the current state (Eq. 4-6 and the free energy). */

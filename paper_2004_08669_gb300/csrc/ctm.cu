@@ -217,6 +217,7 @@ struct ctm_handle {
     double last_backward_residual = 0.0;
     double last_resid = 0.0;                  // last Ritz residual / |w_1|
     int rr_fail_streak = 0;                   // consecutive failed refinements
+    long long rr_fail_counts[5] = {0, 0, 0, 0, 0};  // fallbacks to Jacobi by reason
     double resid_rate = 0.5;                  // measured Ritz residual reduction per iteration
     int jac_rec = -1;                         // profile record of the last Jacobi solve
     ctm::DevCtl* ctl;
@@ -727,9 +728,11 @@ void stage_extend(ctm_handle* h, const double* E1) {
 
 // Orthonormalise src (N x b) into dst by Cholesky QR; `passes` 2 (CholQR,
 // then one Newton-Schulz correction) or 3 (shifted CholQR, CholQR, then the
-// correction).  (Newton-Schulz corrections in place of the second
-// factorisation were measured: some warm blocks leave the shifted factor a
-// defect near 1, where they do not converge.)  tmp is clobbered.
+// correction), each factorisation replaced by a Newton-Schulz correction when
+// the block's defect is already below 1e-4 (decided on the device).  (Fixed
+// Newton-Schulz passes in place of the factorisations were measured: some
+// warm blocks leave a defect near 1, where they do not converge.)  tmp is
+// clobbered.
 ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int passes) {
     const Layout& L = h->lay;
     const int N = L.N, b = L.b;
@@ -738,7 +741,8 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
     for (int i = 0; i < passes; ++i) {
         double* out = bufs[(passes - 1 - i) % 2];
         if (oz_small(h)) {
-            ctm_status s0 = ozmm(h, b, b, N, {cur, N, 1, nullptr}, OZ_SA, true, {cur, N, 1, nullptr}, OZ_SB, true,
+            // G = cur^t cur: one split serves both operands
+            ctm_status s0 = ozmm(h, b, b, N, {cur, N, 1, nullptr}, OZ_SA, true, {cur, N, 1, nullptr}, OZ_SA, false,
                                  h->G, b);
             if (s0 != CTM_OK) return s0;
         } else {
@@ -751,25 +755,24 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
             // orthonormal to O(|E|^2) and needs no factorisation.
             ctm::ns_coeff_f64(h->st, b, h->G, b, h->Linv, b);
             prof_end(h, a, PC_CHOLQR, 1, 0.0, 8.0 * 2.0 * b * b);
-        } else if (passes == 3 && i == 1) {
-            // The second pass starts from the shifted factor's output, whose
-            // defect G - I is usually about the shift over the smallest
-            // eigenvalue of the first Gram matrix (1e-5 .. 1e-4): then two
-            // Newton-Schulz corrections (this pass and the last) reach FP64
-            // orthonormality (each squares the defect, 0.42 d^4 < 1e-16 for
-            // d <= 1e-4) and the factorisation is skipped on the device;
-            // otherwise (a defect near 1, where the corrections do not
-            // converge) the block is factorised again.
-            ctm::orth_check(h->st, b, h->G, b, 1e-4, h->Linv, b, h->ctl);
-            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, 0.0, h->ctl, h->lay.prec != CTM_FP64, &h->ctl->orth_ns));
-            ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1, &h->ctl->orth_ns);
-            prof_end(h, a, PC_CHOLQR, 4, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
         } else {
+            // Every earlier pass checks the defect G - I on the device first.
+            // A warm block is often close to orthonormal already (the scaled
+            // C~ V of a nearly converged block; the shifted factor's output,
+            // whose defect is about the shift over the smallest eigenvalue of
+            // the first Gram matrix): at a defect d <= 1e-4 the remaining
+            // passes as Newton-Schulz corrections reach FP64 orthonormality
+            // (each squares the defect, 0.42 d^4 < 1e-16) and the
+            // factorisation kernels return at once; otherwise (a defect near
+            // 1, where the corrections do not converge) the block is
+            // factorised, with a shift in the first of three passes.
             double shift_rel =
                 (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
-            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl, h->lay.prec != CTM_FP64));
-            ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1);
-            prof_end(h, a, PC_CHOLQR, 3, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
+            ctm::orth_check(h->st, b, h->G, b, 1e-4, h->Linv, b, h->ctl);
+            CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl, h->lay.prec != CTM_FP64,
+                                       &h->ctl->orth_ns));
+            ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1, &h->ctl->orth_ns, h->lay.prec != CTM_FP64);
+            prof_end(h, a, PC_CHOLQR, 5, (double)b * b * b / 3.0 + (double)b * b * b / 3.0, 8.0 * 2.0 * b * b);
         }
         if (oz_small(h)) {
             ctm_status s0 = ozmm(h, N, b, b, {cur, 1, N, nullptr}, OZ_SA, true, {h->Linv, 1, b, nullptr}, OZ_SB, true,
@@ -891,14 +894,17 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             CTM_CUDA(cudaMemsetAsync(&h->ctl->rrc_ok, 0, sizeof(int), h->st));
             if (rrc_tried) {
                 cudaEvent_t ra = prof_begin(h);
-                CTM_CUDA(ctm::rr_cluster_refine(h->st, b, h->H, b, h->rrc, h->ew, h->ctl, 12));
+                // the kept states and the multiplet test at the cut need the
+                // leading m + 1 pairs; 16 more keep a multiplet straddling
+                // the cut inside the head
+                CTM_CUDA(ctm::rr_cluster_refine(h->st, b, h->H, b, h->rrc, h->ew, h->ctl, 12, std::min(b, m + 16)));
                 prof_end(h, ra, PC_RRC, 1);
                 rrc_rec = (h->prof_on && ra) ? (int)h->recs.size() - 1 : -1;
                 ++h->rrc_solves;
             }
             cudaEvent_t ja2 = prof_begin(h);
             CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, 0.0, 0.0, true,
-                                     rrc_tried ? &h->ctl->rrc_ok : nullptr));
+                                     rrc_tried ? &h->ctl->rrc_ok : nullptr, cold ? 0 : std::min(b, m + 16)));
             prof_end(h, ja2, PC_JACOBI, 4);
             h->jac_rec = (h->prof_on && ja2) ? (int)h->recs.size() - 1 : -1;
         }
@@ -915,6 +921,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             used = ctm::rr_refine_f64(h->st, b, std::min(b, m + 2), h->H, b, h->oa, h->ew, h->theta, h->Sb, b, 1e-13,
                                       8, h->ctl, h->hctl, &nk_rr);
             h->rr_fail_streak = used < 0 ? h->rr_fail_streak + 1 : 0;
+            if (used < 0 && h->oa.fail_reason >= 1 && h->oa.fail_reason <= 4) ++h->rr_fail_counts[h->oa.fail_reason];
         }
         if (h->have_rrc) {
             // recorded above
@@ -925,7 +932,7 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             // the mixed-precision forms solve in double-float (FP32 pipe); the
             // FP64 form in FP64
             CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, 0.0, 0.0,
-                                     h->lay.prec != CTM_FP64));
+                                     h->lay.prec != CTM_FP64, nullptr, cold ? 0 : std::min(b, m + 16)));
             nk_rr += 4;
             ++h->rr_jacobi;
         } else {
@@ -967,6 +974,8 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
                 }
             }
             h->oa.fail_reason = rrc_tried ? h->hctl->rrc_fail : 0;
+            if (rrc_tried && !ok && h->oa.fail_reason >= 1 && h->oa.fail_reason <= 4)
+                ++h->rr_fail_counts[h->oa.fail_reason];
             h->oa.last_iter = h->hctl->rrc_iters;
             float mc;
             memcpy(&mc, &h->hctl->rrc_maxc, sizeof(float));
@@ -1099,6 +1108,7 @@ ctm_status step_once(ctm_handle* h) {
     I.rr_refined = h->rr_refined;
     I.rr_jacobi = h->rr_jacobi;
     I.rr_fail_reason = h->oa.fail_reason;
+    for (int k = 0; k < 5; ++k) I.rr_fail_counts[k] = h->rr_fail_counts[k];
     I.rr_last_iter = h->oa.last_iter;
     I.rr_last_max = h->oa.last_max;
     for (int k = 0; k < 8; ++k) I.jacobi_rotations[k] = h->hctl->rot_count[k];

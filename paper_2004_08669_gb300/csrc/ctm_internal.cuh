@@ -66,6 +66,7 @@ struct DevCtl {
     // enough for a Newton-Schulz correction in place of a factorisation
     int orth_ns;
     float orth_defect;   // that defect (the last check)
+    unsigned long long orth_max_bits;  // its running maximum (bits of a non-negative double)
     // block 0's clock (ns) at the end of each phase of the last refinement's
     // first 16 iterations: after P1, P2, P3a, P3b, P3c, P3e, P4
     unsigned long long rrc_t0;

@@ -381,7 +381,7 @@ template <class JA, bool FUSE>
 __global__ void __launch_bounds__(256, FUSE ? 2 : JA::kMinBlocks) k_jacobi(int n, int npad, typename JA::T* A0, typename JA::T* A1,
                                                 typename JA::T* S, typename JA::T* S1, double* __restrict__ diag,
                                                 int* act, int max_sweeps, double eps, double floor_rel,
-                                                DevCtl* ctl, const int* skip) {
+                                                DevCtl* ctl, const int* skip, int nhead) {
     using T = typename JA::T;
     // another solver already produced S and diag: every block leaves before
     // the first barrier
@@ -430,7 +430,8 @@ __global__ void __launch_bounds__(256, FUSE ? 2 : JA::kMinBlocks) k_jacobi(int n
         const int tag = sweep + 1;
         for (long e = gtid; e < (long)npad * npad; e += gstride) {
             const int i = (int)(e % npad), j = (int)(e / npad);
-            if (i < j) {
+            // pairs of two guard vectors (both >= nhead) need not converge
+            if (i < j && i < nhead) {
                 const T aij = JA::ld(Acur + i + (size_t)npad * j);
                 if (JA::nz(aij) && JA::above(JA::ld(Acur + i + (size_t)npad * i), JA::ld(Acur + j + (size_t)npad * j),
                                              aij, eps, floor_abs)) {
@@ -707,6 +708,7 @@ struct C64 {
     __device__ static T zero() { return 0.0; }
     __device__ static T mul(T a, T b) { return a * b; }
     __device__ static T sub(T a, T b) { return a - b; }
+    __device__ static T neg(T a) { return -a; }
     __device__ static T rsq(T d) { return rsqrt_nr(d); }
     __device__ static T shfl(T a, int l) { return __shfl_sync(0xffffffffu, a, l); }
     struct Acc {
@@ -742,6 +744,7 @@ struct CDF {
         return quick(s, e + (a.y + b.y));
     }
     __device__ static T sub(T a, T b) { return add(a, make_float2(-b.x, -b.y)); }
+    __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
     // 1/sqrt(d): FP32 seed, two double-float Newton steps y <- y + y (1 - d y^2)/2
     __device__ static T rsq(T d) {
         T y = make_float2(rsqrtf(d.x), 0.f);
@@ -832,12 +835,16 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
             dinv2[0] = CA::mul(inv, inv);
         }
         __syncthreads();
+        // Fixed ownership (256 threads): lane = row i, warp w holds columns
+        // w, w + 8, w + 16, w + 24, so a pivot step is four predicated
+        // updates per thread with no index arithmetic on the chain.
         for (int j = 0; j + 1 < kb; ++j) {
             const T w = dinv2[j];
-            const int nt = kb - 1 - j;  // trailing order
-            for (int e = tid; e < nt * nt; e += blockDim.x) {
-                const int i = j + 1 + e % nt, l = j + 1 + e / nt;
-                if (l <= i) {
+            const int i = lane;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int l = (tid >> 5) + 8 * r;
+                if (l > j && l <= i && i < kb) {
                     T v = CA::sub(D[i][l], CA::mul(CA::mul(D[i][j], D[l][j]), w));
                     if (i == j + 1 && l == j + 1) {  // the next pivot
                         const double vv = CA::to(v);
@@ -893,7 +900,7 @@ __global__ void __launch_bounds__(256, 2) k_cholesky(int n, double* G, int ld, d
         const int tx = tid & 15, ty = tid >> 4;
         for (long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
             // tile (I, J), I >= J, enumerated row by row
-            int I = (int)((sqrt(8.0 * (double)tIdx + 1.0) - 1.0) / 2.0);
+            int I = (int)((sqrtf(8.0f * (float)tIdx + 1.0f) - 1.0f) * 0.5f);  // corrected below
             while ((long)(I + 1) * (I + 2) / 2 <= tIdx) ++I;
             while ((long)I * (I + 1) / 2 > tIdx) --I;
             const int J = (int)(tIdx - (long)I * (I + 1) / 2);
@@ -954,17 +961,21 @@ __global__ void __launch_bounds__(32) k_trinv_diag(int n, const double* __restri
 // x_J = Dinv_J e_j, then for each later block x_I = -Dinv_I (L_{I, J:I}
 // x_{J:I}).  The 32 x 32 tiles of L are staged in shared memory, shared by
 // the eight warps, with the next tile prefetched into registers.
+template <class CA>
 __global__ void __launch_bounds__(256) k_trinv_cols(int n, const double* __restrict__ L, int ld,
                                                     const double* __restrict__ Dinv, double* __restrict__ X,
                                                     int ldx, const int* __restrict__ skip) {
+    using T = typename CA::T;
+    static_assert(sizeof(T) == sizeof(double), "shared-memory layout assumes 8-byte elements");
     if (skip && *skip) return;
-    extern __shared__ double tsh[];
+    extern __shared__ double tsh_raw[];
+    T* tsh = reinterpret_cast<T*>(tsh_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int npad = ((n + 31) / 32) * 32, nb = npad / 32;
-    double* xs = tsh + (size_t)warp * npad;  // this warp's column of X
-    double* Tt = tsh + (size_t)8 * npad;     // [2][32][33] tiles of L
-    double* Di = Tt + 2 * 32 * 33;           // [32][33] Dinv_I
-    double* ys = Di + 32 * 33;               // [8][32]
+    T* xs = tsh + (size_t)warp * npad;  // this warp's column of X
+    T* Tt = tsh + (size_t)8 * npad;     // [2][32][33] tiles of L
+    T* Di = Tt + 2 * 32 * 33;           // [32][33] Dinv_I
+    T* ys = Di + 32 * 33;               // [8][32]
     const int j0 = blockIdx.x * 8, j = j0 + warp;
     const bool live_col = j < n;
     const int J = j0 / 32, c = j % 32;
@@ -972,25 +983,25 @@ __global__ void __launch_bounds__(256) k_trinv_cols(int n, const double* __restr
         for (int i = lane; i < 32 * J; i += 32) X[i + (size_t)ldx * j] = 0.0;
     {
         const double v = live_col ? Dinv[(size_t)1024 * J + 32 * c + lane] : 0.0;  // zero above row c
-        xs[32 * J + lane] = v;
+        xs[32 * J + lane] = CA::from(v);
         if (live_col && 32 * J + lane < n) X[(32 * J + lane) + (size_t)ldx * j] = v;
     }
     double reg[4];
     for (int I = J + 1; I < nb; ++I) {
         __syncthreads();  // Di and the tiles of the previous I are consumed
-        for (int e = tid; e < 1024; e += 256) Di[(e % 32) * 33 + e / 32] = Dinv[(size_t)1024 * I + e];
+        for (int e = tid; e < 1024; e += 256) Di[(e % 32) * 33 + e / 32] = CA::from(Dinv[(size_t)1024 * I + e]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q, r = 32 * I + (e % 32), col = 32 * J + e / 32;
             reg[q] = (r < n) ? L[r + (size_t)ld * col] : 0.0;
         }
-        double y0 = 0.0, y1 = 0.0;
+        typename CA::Acc acc = CA::acc0();
         for (int kb = J, buf = 0; kb < I; ++kb, buf ^= 1) {
-            double* T = Tt + buf * 32 * 33;
+            T* Tb = Tt + buf * 32 * 33;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int e = tid + 256 * q;
-                T[(e % 32) * 33 + e / 32] = reg[q];
+                Tb[(e % 32) * 33 + e / 32] = CA::from(reg[q]);
             }
             __syncthreads();
             if (kb + 1 < I) {
@@ -1000,24 +1011,20 @@ __global__ void __launch_bounds__(256) k_trinv_cols(int n, const double* __restr
                     reg[q] = (r < n) ? L[r + (size_t)ld * col] : 0.0;
                 }
             }
-            const double* xk = xs + 32 * kb;
+            const T* xk = xs + 32 * kb;
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 2) {
-                y0 = fma(T[lane * 33 + cc], xk[cc], y0);
-                y1 = fma(T[lane * 33 + cc + 1], xk[cc + 1], y1);
-            }
+            for (int cc = 0; cc < 32; cc += 2)
+                CA::acc2(acc, Tb[lane * 33 + cc], xk[cc], Tb[lane * 33 + cc + 1], xk[cc + 1]);
         }
-        ys[warp * 32 + lane] = y0 + y1;
+        ys[warp * 32 + lane] = CA::fin(acc);
         __syncwarp();
-        double xi0 = 0.0, xi1 = 0.0;
+        typename CA::Acc ax = CA::acc0();
 #pragma unroll
-        for (int s2 = 0; s2 < 32; s2 += 2) {
-            xi0 = fma(Di[lane * 33 + s2], ys[warp * 32 + s2], xi0);
-            xi1 = fma(Di[lane * 33 + s2 + 1], ys[warp * 32 + s2 + 1], xi1);
-        }
-        const double xi = -(xi0 + xi1);
+        for (int s2 = 0; s2 < 32; s2 += 2)
+            CA::acc2(ax, Di[lane * 33 + s2], ys[warp * 32 + s2], Di[lane * 33 + s2 + 1], ys[warp * 32 + s2 + 1]);
+        const T xi = CA::neg(CA::fin(ax));
         xs[32 * I + lane] = xi;
-        if (live_col && 32 * I + lane < n) X[(32 * I + lane) + (size_t)ldx * j] = xi;
+        if (live_col && 32 * I + lane < n) X[(32 * I + lane) + (size_t)ldx * j] = CA::to(xi);
         __syncwarp();
     }
 }
@@ -1252,7 +1259,8 @@ int coop_grid_limit(const void* fn, int block, size_t smem) {
 
 template <class JA>
 cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta, double* Sout,
-                          int ldo, int max_sweeps, DevCtl* ctl, double eps, double floor_rel, const int* skip) {
+                          int ldo, int max_sweeps, DevCtl* ctl, double eps, double floor_rel, const int* skip,
+                          int nhead) {
     using T = typename JA::T;
     static_assert(sizeof(T) == sizeof(double), "A and S buffers hold one 8-byte element each");
     int npad = n + (n & 1);
@@ -1304,7 +1312,8 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
     double* diag = w.diag;
     int* act = w.rank;  // the sweep tags; rank is rewritten by the sort below
     T* S1 = fused ? (T*)w.S1 : nullptr;  // NULL: one round per barrier, S in place
-    void* args[] = {&n, &npad, &A0, &A1, &S, &S1, &diag, &act, &max_sweeps, &eps, &fl, &ctl, &skip};
+    int nh = (nhead > 0 && nhead < n) ? nhead : npad;
+    void* args[] = {&n, &npad, &A0, &A1, &S, &S1, &diag, &act, &max_sweeps, &eps, &fl, &ctl, &skip, &nh};
     cudaError_t e = launch_coop(fused ? fF : fS, grid, 256, args, smem, st);
     if (e != cudaSuccess) return e;
     k_rank_ritz<<<grid_for((size_t)n), 256, 0, st>>>(n, w.diag, w.rank, theta);
@@ -1314,15 +1323,15 @@ cudaError_t jacobi_launch(cudaStream_t st, int n, const double* H, int ldh, EigW
 
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
                        double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol, double floor_rel,
-                       bool df, const int* skip) {
+                       bool df, const int* skip, int nhead) {
     if (df) {
         // double-float: rotate while the coupling exceeds ~2^-46 of the
         // diagonal scale (four times the pair's unit roundoff)
         const double eps = rel_tol > 1.4210854715202004e-14 ? rel_tol : 1.4210854715202004e-14;
-        return jacobi_launch<JDF>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel, skip);
+        return jacobi_launch<JDF>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel, skip, nhead);
     }
     const double eps = rel_tol > 2.220446049250313e-16 ? rel_tol : 2.220446049250313e-16;
-    return jacobi_launch<J64>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel, skip);
+    return jacobi_launch<J64>(st, n, H, ldh, w, theta, Sout, ldo, max_sweeps, ctl, eps, floor_rel, skip, nhead);
 }
 
 cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift, DevCtl* ctl, bool df,
@@ -1342,7 +1351,7 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
 }
 
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch,
-               const int* skip) {
+               const int* skip, bool df) {
     // scratch: ceil(n / 32) * 1024 doubles (the diagonal blocks' inverses)
     const int nb = (n + 31) / 32;
     k_trinv_diag<<<nb, 32, 0, st>>>(n, L, ld, scratch, skip);
@@ -1352,11 +1361,13 @@ void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int l
     {
         std::lock_guard<std::mutex> g(mu);
         if (smem > attr) {
-            cudaFuncSetAttribute(k_trinv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_trinv_cols<C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_trinv_cols<CDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = smem;
         }
     }
-    k_trinv_cols<<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx, skip);
+    if (df) k_trinv_cols<CDF><<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx, skip);
+    else k_trinv_cols<C64><<<(n + 7) / 8, 256, smem, st>>>(n, L, ld, scratch, X, ldx, skip);
 }
 
 // X = (3 I - (G + G^t)/2) / 2.
@@ -1376,17 +1387,16 @@ void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, i
 // One block: the defect d = max|G - I| of a Gram matrix; when d <= thresh it
 // sets ctl->orth_ns and writes the Newton-Schulz coefficient X = (3I - G)/2
 // (the factorisation behind it is then skipped), else clears the flag.
-__global__ void __launch_bounds__(1024) k_orth_check(int b, const double* __restrict__ G, int ldg, double thresh,
-                                                     double* __restrict__ X, int ldx, DevCtl* ctl) {
-    __shared__ double red[32];
-    __shared__ int s_ns;
+// max |G - I| over a b x b Gram matrix: a CTA per column, the maximum by an
+// atomic max on the bits of the non-negative doubles (their order; a NaN's
+// bits exceed every finite value's, so it propagates).
+__global__ void __launch_bounds__(256) k_orth_max(int b, const double* __restrict__ G, int ldg, DevCtl* ctl) {
+    __shared__ double red[8];
+    const int j = blockIdx.x;
     double d = 0.0;
-    const size_t tot = (size_t)b * b;
-    for (size_t e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int i = (int)(e % b), j = (int)(e / b);
-        const double g = G[i + (size_t)ldg * j];
-        const double v = fabs(g - (i == j ? 1.0 : 0.0));
-        d = (v > d || v != v) ? v : d;  // NaN propagates
+    for (int i = threadIdx.x; i < b; i += blockDim.x) {
+        const double v = fabs(G[i + (size_t)ldg * j] - (i == j ? 1.0 : 0.0));
+        d = (v > d || v != v) ? v : d;
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double t = __shfl_xor_sync(0xffffffffu, d, o);
@@ -1397,21 +1407,31 @@ __global__ void __launch_bounds__(1024) k_orth_check(int b, const double* __rest
     if (threadIdx.x == 0) {
         double m = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
-        s_ns = (m <= thresh) ? 1 : 0;
-        ctl->orth_ns = s_ns;
+        atomicMax(&ctl->orth_max_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// The decision and, below the threshold, X = (3I - G)/2 (G symmetrised).
+__global__ void __launch_bounds__(256) k_orth_apply(int b, const double* __restrict__ G, int ldg, double thresh,
+                                                    double* __restrict__ X, int ldx, DevCtl* ctl) {
+    const double m = __longlong_as_double((long long)*(volatile unsigned long long*)&ctl->orth_max_bits);
+    const int ns = (m <= thresh) ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->orth_ns = ns;
         ctl->orth_defect = (float)m;
     }
-    __syncthreads();
-    if (!s_ns) return;
-    for (size_t e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int i = (int)(e % b), j = (int)(e / b);
+    if (!ns) return;
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) {
         const double g = 0.5 * (G[i + (size_t)ldg * j] + G[j + (size_t)ldg * i]);
         X[i + (size_t)ldx * j] = (i == j ? 1.5 : 0.0) - 0.5 * g;
     }
 }
 
 void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl) {
-    k_orth_check<<<1, 1024, 0, st>>>(b, G, ldg, thresh, X, ldx, ctl);
+    cudaMemsetAsync(&ctl->orth_max_bits, 0, sizeof(unsigned long long), st);
+    k_orth_max<<<b, 256, 0, st>>>(b, G, ldg, ctl);
+    k_orth_apply<<<b, 256, 0, st>>>(b, G, ldg, thresh, X, ldx, ctl);
 }
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,

@@ -64,9 +64,11 @@ bool rrc_supported(int n);
 // the double-float Jacobi solver leaves them, and sets ctl->rrc_ok = 1;
 // otherwise ctl->rrc_ok stays 0.  Launch jacobi_f64(..., df = true, skip =
 // &ctl->rrc_ok) behind it: it solves only when the refinement gave up, and
-// sorts in either case.
+// sorts in either case.  nhead: the leading columns (in the warm order, |Ritz
+// value| descending) whose pairs must converge; pairs of two later columns
+// (the oversampling's guard vectors) are left unrotated (0: all columns).
 cudaError_t rr_cluster_refine(cudaStream_t st, int n, const double* H, int ldh, RrcWork& w, EigWork& ew,
-                              DevCtl* ctl, int max_iter);
+                              DevCtl* ctl, int max_iter, int nhead = 0);
 
 // Warm-start Rayleigh-Ritz by simultaneous Jacobi rotations (Ogita-Aishima
 // refinement from X = I).  Returns iterations used, or -1 when it did not
@@ -86,9 +88,12 @@ int rr_refine_f64(cudaStream_t st, int b, int head, const double* H, int ldh, Oa
 // 48 significant bits; for the mixed-precision forms).
 // skip (device, may be NULL): when *skip != 0 at run time the solve is left
 // out (another solver already wrote w.S and w.diag) and only the sort runs.
+// nhead > 0: only couplings with at least one index below nhead are driven
+// below the threshold (a warm block's leading columns; the later ones are
+// guard vectors whose mutual rotations do not matter); 0: all.
 cudaError_t jacobi_f64(cudaStream_t st, int n, const double* H, int ldh, EigWork& w, double* theta,
                        double* Sout, int ldo, int max_sweeps, DevCtl* ctl, double rel_tol = 0.0,
-                       double floor_rel = 0.0, bool df = false, const int* skip = nullptr);
+                       double floor_rel = 0.0, bool df = false, const int* skip = nullptr, int nhead = 0);
 
 // G + shift_rel * trace(G) * I = L L^t, L lower in place (blocked, panel 32).
 // df: double-float arithmetic on the FP32 pipe (mixed-precision forms).
@@ -102,9 +107,11 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
 void ns_coeff_f64(cudaStream_t st, int b, const double* G, int ldg, double* X, int ldx);
 
 // X = L^{-1} for lower-triangular L (upper part of X zeroed); scratch:
-// ceil(n / 32) * 1024 doubles.  skip as for cholesky_f64.
+// ceil(n / 32) * 1024 doubles.  skip as for cholesky_f64.  df: the
+// substitution over the off-diagonal blocks in double-float on the FP32 pipe
+// (the mixed-precision forms), else FP64.
 void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int ldx, double* scratch,
-               const int* skip = nullptr);
+               const int* skip = nullptr, bool df = false);
 
 // The defect max|G - I| of a Gram matrix; if it is at most thresh, sets
 // ctl->orth_ns and writes X = (3I - G)/2 (a Newton-Schulz correction),

@@ -21,8 +21,9 @@
 // by 2^{-7t} (exact) and add them into a double-float (hi, lo) accumulator
 // per output element; the end result is written in FP64.  A producer warp
 // streams all digit planes of a 32-wide K-tile per stage (3-stage TMA ring,
-// 64-byte swizzle) and an MMA warp issues the tcgen05.mma of every pair.
-// All mbarrier waits are bounded (error flag, TMEM freed, return).
+// 64-byte swizzle) and an MMA warp issues the tcgen05.mma: one per A digit
+// plane and run of up to four consecutive B planes (their groups are
+// consecutive accumulators).  All mbarrier waits are bounded (error flag, TMEM freed, return).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -388,8 +389,8 @@ __global__ void __launch_bounds__(320, 1)
     } else if (warp == 9) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
-                                   ((uint32_t)(kOzBM >> 4) << 24);
+            // f32 accumulator, bf16 A and B, both K-major; N is set per MMA
+            const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBM >> 4) << 24);
             bool ok = true;
             long used = 0;    // K-tiles consumed over all tiles
             long chunks = 0;  // accumulator hand-overs over all tiles
@@ -413,20 +414,25 @@ __global__ void __launch_bounds__(320, 1)
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t base = smem_u32(smem + st * STAGE);
+                        // A plane i meets B planes j = 0 .. S-1-i (0-based), whose
+                        // groups g = i + j are consecutive accumulators, and the
+                        // B planes lie consecutively in the stage with the same
+                        // 8-row stride: so one MMA of N = 64 c covers c pairs
+                        // (c <= 4, N <= 256), 10 MMAs per 16-wide K step for
+                        // s = 7 instead of 28.  Every group's first product in
+                        // a chunk is the i = 0 one, which overwrites it.
 #pragma unroll
                         for (int i = 0; i < S; ++i) {
 #pragma unroll
-                            for (int j = 0; j < S; ++j) {
-                                if (i + j > S - 1) continue;  // keep i + j <= s + 1 (1-based)
-                                const int g = i + j;          // group index 0 .. S - 1
+                            for (int j0 = 0; j0 < S - i; j0 += 4) {
+                                const int c = (S - i - j0) < 4 ? (S - i - j0) : 4;
+                                const uint32_t idesc = idesc0 | ((uint32_t)((c * kOzBN) >> 3) << 17);
                                 const uint32_t a0 = base + i * A_PLANE;
-                                const uint32_t b0 = base + S * A_PLANE + j * B_PLANE;
+                                const uint32_t b0 = base + S * A_PLANE + j0 * B_PLANE;
 #pragma unroll
                                 for (int kk = 0; kk < kOzKT / 16; ++kk) {
-                                    // the first MMA of a group in this chunk overwrites its accumulator
-                                    const bool first = (kt == kt0) && (kk == 0) &&
-                                                       (i == (g < S ? 0 : g - (S - 1)));
-                                    mma_bf16(tmem + (uint32_t)(g * kOzBN), sdesc64(a0 + 32 * kk),
+                                    const bool first = (kt == kt0) && (kk == 0) && (i == 0);
+                                    mma_bf16(tmem + (uint32_t)((i + j0) * kOzBN), sdesc64(a0 + 32 * kk),
                                              sdesc64(b0 + 32 * kk), idesc, first ? 0u : 1u);
                                 }
                             }
@@ -640,7 +646,10 @@ cudaError_t oz_gemm(cudaStream_t st, int s, int M, int N, int K, const void* Apl
             kper = K;
         }
     }
-    const int Mp = oz_rows_pad(M, kOzBM), Np = oz_rows_pad(N, kOzBN), ld = oz_ld(K);
+    // B may be A's own planes (a Gram matrix A A^t): then its rows sit at A's
+    // plane stride
+    const bool sameAB = (Bplanes == Aplanes) && (eB == eA) && N <= M;
+    const int Mp = oz_rows_pad(M, kOzBM), Np = sameAB ? Mp : oz_rows_pad(N, kOzBN), ld = oz_ld(K);
     CUtensorMap ma, mb;
     if (!oz_map(&ma, Aplanes, K, s * Mp, ld, kOzBM) || !oz_map(&mb, Bplanes, K, s * Np, ld, kOzBN))
         return cudaErrorInvalidValue;

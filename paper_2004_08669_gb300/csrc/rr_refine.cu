@@ -62,6 +62,7 @@ struct RrcP {
     double* diag;  // Ritz values (unsorted)
     DevCtl* ctl;
     double eps_c, eps_r, tau;
+    int nhead;  // pairs with both indices >= nhead (guard vectors) are not rotated
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -211,12 +212,16 @@ __device__ float2 e_entry(const RrcP& p, int i, int k) {
     const float2 g = ldf2(p.G + a + (size_t)n * b);
     if (i == k) return JDF::half(JDF::add(JDF::one(), JDF::neg(g)));
     const float2 rh = JDF::half(JDF::neg(g));
+    if (a >= p.nhead) return rh;  // two guard vectors: orthonormality only
     const int ci = __ldcg(p.cid + i), ck = __ldcg(p.cid + k);
     if (ci >= 0 && ci == ck) return rh;
     const double li = __ldcg(p.lam + i), lk = __ldcg(p.lam + k);
     const double c = df2d(ldf2(p.S + a + (size_t)n * b)) - df2d(g) * 0.5 * (li + lk);
     const float sc = sqrtf(fabsf((float)li) * fabsf((float)lk));
-    if (!(fabsf((float)c) > (float)p.eps_c * sc)) return rh;
+    // a coupling already within the convergence threshold is not rotated:
+    // between (nearly) degenerate Ritz values it is rounding over rounding,
+    // and rotating by it would feed the orthonormality defect every iteration
+    if (!(fabsf((float)c) > 4.0f * (float)p.eps_c * sc)) return rh;
     return JDF::add(rh, JDF::from(c / (lk - li)));
 }
 
@@ -431,6 +436,12 @@ __global__ void __launch_bounds__(RTHREADS, 3) k_rr_refine(RrcP p) {
                     continue;
                 }
                 mr = fmaxf(mr, fabsf((float)g));
+                // A pair of guard vectors (both beyond the head) needs no
+                // rotation: a rotation within their span leaves the head's
+                // eigenvectors and span(X) unchanged, and their couplings,
+                // relative to their small Ritz values, sit far above the
+                // noise floor the head converges to.
+                if (i >= p.nhead) continue;
                 // Rayleigh quotients lambda = S_ii / G_ii (the first iteration: H_ii)
                 const size_t di = (size_t)i * (n + 1), dj = (size_t)j * (n + 1);
                 const double li = it > 0 ? df2d(ldf2(p.S + di)) / df2d(ldf2(p.G + di)) : __ldcg(p.lam + i);
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(RTHREADS, 3) k_rr_refine(RrcP p) {
                 const float ratio = sc > 0.f ? ac / sc : (ac > 0.f ? INFINITY : 0.f);
                 if (!(ratio == ratio)) mc = INFINITY;  // NaN
                 mc = fmaxf(mc, ratio);
-                if (ratio > (float)p.eps_c && ac > (float)p.tau * fabsf((float)(lj - li))) {
+                if (ratio > 4.0f * (float)p.eps_c && ac > (float)p.tau * fabsf((float)(lj - li))) {
                     const int k = atomicAdd(&ctl->rrc_nedges, 1);
                     if (k < p.edge_cap) {
                         p.edges[2 * k] = i;
@@ -751,7 +762,7 @@ void rrc_carve(void* base, int n, RrcWork& w) {
 bool rrc_supported(int n) { return n >= 2 && n <= RMAXN; }
 
 cudaError_t rr_cluster_refine(cudaStream_t st, int n, const double* H, int ldh, RrcWork& w, EigWork& ew,
-                              DevCtl* ctl, int max_iter) {
+                              DevCtl* ctl, int max_iter, int nhead) {
     if (!rrc_supported(n) || n > w.nmax) return cudaErrorInvalidValue;
     const size_t smem = smem_bytes();
     static std::mutex mu;
@@ -771,6 +782,7 @@ cudaError_t rr_cluster_refine(cudaStream_t st, int n, const double* H, int ldh, 
     p.n = n;
     p.npad = n + (n & 1) < 2 ? 2 : n + (n & 1);
     p.max_iter = max_iter;
+    p.nhead = (nhead > 0 && nhead < n) ? nhead : n;
     p.edge_cap = w.edge_cap;
     p.H = H;
     p.ldh = ldh;

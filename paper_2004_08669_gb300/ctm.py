@@ -40,11 +40,12 @@ class ctm_step_info(ctypes.Structure):
                 ("subspace_iters", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int), ("steps", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rr_refined", ctypes.c_longlong), ("rr_jacobi", ctypes.c_longlong),
                 ("rr_fail_reason", ctypes.c_int), ("rr_last_iter", ctypes.c_int), ("rr_last_max", ctypes.c_double),
-                ("jacobi_rotations", ctypes.c_int * 8)]
+                ("jacobi_rotations", ctypes.c_int * 8), ("rr_fail_counts", ctypes.c_longlong * 5)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["jacobi_rotations"] = list(d["jacobi_rotations"])
+        d["rr_fail_counts"] = list(d["rr_fail_counts"])
         return d
 
 

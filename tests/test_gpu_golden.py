@@ -88,8 +88,10 @@ BOUNDS = {"fp64": (1e-12, 1e-12, 1e-10, 1e-10), "ozaki64": (1e-9, 1e-10, 1e-9, 1
 def test_m256_trajectory_errors_against_oracle(ctm, prec):
     ref = _load("oracle_q20_m256_T0.4398_20steps.json")
     beta, T = ref["beta"], ref["T"]
-    # Ritz tolerances at the forms' rounding floors for K = N = 5120
-    tol = {"fp64": 3e-13, "ozaki64": 1e-11}.get(prec, 0.0)
+    # Ritz tolerances at the forms' rounding floors for K = N = 5120 (TF32
+    # and BF16: the benchmark's, above their residual floors of ~1e-4 and
+    # ~1e-2, where a tighter tolerance only runs the iteration to its cap)
+    tol = {"fp64": 3e-13, "ozaki64": 1e-11, "tf32": 2e-4, "bf16": 3e-2}[prec]
     g = ctm.CTMRG(W.dodecahedron(), ref["m"], beta, prec=prec, subspace_tol=tol, max_subspace_iters=200)
     df_max = 0.0
     rows = []
