@@ -768,7 +768,7 @@ ctm_status stage_orth(ctm_handle* h, double* src, double* dst, double* tmp, int 
             // factorised, with a shift in the first of three passes.
             double shift_rel =
                 (passes == 3 && i == 0) ? 11.0 * ((double)N * b + (double)b * (b + 1)) * 2.22e-16 : 0.0;
-            ctm::orth_check(h->st, b, h->G, b, 1e-4, h->Linv, b, h->ctl);
+            ctm::orth_check(h->st, b, h->G, b, 1e-4, h->Linv, b, h->ctl, i);
             CTM_CUDA(ctm::cholesky_f64(h->st, b, h->G, b, shift_rel, h->ctl, h->lay.prec != CTM_FP64,
                                        &h->ctl->orth_ns));
             ctm::trinv_f64(h->st, b, h->G, b, h->Linv, b, h->oa.W1, &h->ctl->orth_ns, h->lay.prec != CTM_FP64);

@@ -67,6 +67,9 @@ struct DevCtl {
     int orth_ns;
     float orth_defect;   // that defect (the last check)
     unsigned long long orth_max_bits;  // its running maximum (bits of a non-negative double)
+    // checks so far by decade of the defect (bucket k: 10^-k <= d < 10^(1-k),
+    // bucket 0: d >= 1, bucket 9: d < 1e-8), for the first pass and the others
+    unsigned int orth_hist[2][10];
     // block 0's clock (ns) at the end of each phase of the last refinement's
     // first 16 iterations: after P1, P2, P3a, P3b, P3c, P3e, P4
     unsigned long long rrc_t0;

@@ -1413,12 +1413,15 @@ __global__ void __launch_bounds__(256) k_orth_max(int b, const double* __restric
 
 // The decision and, below the threshold, X = (3I - G)/2 (G symmetrised).
 __global__ void __launch_bounds__(256) k_orth_apply(int b, const double* __restrict__ G, int ldg, double thresh,
-                                                    double* __restrict__ X, int ldx, DevCtl* ctl) {
+                                                    double* __restrict__ X, int ldx, DevCtl* ctl, int slot) {
     const double m = __longlong_as_double((long long)*(volatile unsigned long long*)&ctl->orth_max_bits);
     const int ns = (m <= thresh) ? 1 : 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->orth_ns = ns;
         ctl->orth_defect = (float)m;
+        int k = 0;
+        for (double t = 1.0; k < 9 && !(m >= t); t *= 0.1) ++k;
+        atomicAdd(&ctl->orth_hist[slot ? 1 : 0][k], 1u);
     }
     if (!ns) return;
     const int j = blockIdx.x;
@@ -1428,10 +1431,11 @@ __global__ void __launch_bounds__(256) k_orth_apply(int b, const double* __restr
     }
 }
 
-void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl) {
+void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl,
+                int slot) {
     cudaMemsetAsync(&ctl->orth_max_bits, 0, sizeof(unsigned long long), st);
     k_orth_max<<<b, 256, 0, st>>>(b, G, ldg, ctl);
-    k_orth_apply<<<b, 256, 0, st>>>(b, G, ldg, thresh, X, ldx, ctl);
+    k_orth_apply<<<b, 256, 0, st>>>(b, G, ldg, thresh, X, ldx, ctl, slot);
 }
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,

@@ -116,7 +116,10 @@ void trinv_f64(cudaStream_t st, int n, const double* L, int ld, double* X, int l
 // The defect max|G - I| of a Gram matrix; if it is at most thresh, sets
 // ctl->orth_ns and writes X = (3I - G)/2 (a Newton-Schulz correction),
 // otherwise clears ctl->orth_ns (pass it as skip to cholesky_f64/trinv_f64).
-void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl);
+// slot: 0 for a block's first orthonormalisation pass, 1 for later ones
+// (the defect histogram ctl->orth_hist)
+void orth_check(cudaStream_t st, int b, const double* G, int ldg, double thresh, double* X, int ldx, DevCtl* ctl,
+                int slot = 1);
 
 void resid_f64(cudaStream_t st, int N, int ncol, const double* T, const double* Z, int ld,
                const double* theta, double* res);
