@@ -483,7 +483,7 @@ def errors_vs_oracle(args, local):
     o = ref["observables"]
     for prec in ("fp64", "ozaki64", "tf32", "bf16"):
         # Ritz tolerances at the forms' rounding floors for K = N = 5120
-        tol = {"fp64": 3e-13, "ozaki64": 1e-11}.get(prec, 0.0)
+        tol = SUBSPACE_TOL.get(prec, 0.0)
         g = ctm.CTMRG(W.dodecahedron(), ref["m"], ref["beta"], prec=prec, device=f"cuda:{local}",
                       subspace_tol=tol, max_subspace_iters=200, block_extra=args.block_extra)
         try:

@@ -827,6 +827,17 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
     int it_meas = -1;
     bool meas_here = false;
     if (L.esz) pconvert(h, N, N, h->C, N, nullptr, h->opC, L.ldN);  // C~ rows (symmetric)
+    // dst = C~ src (N x b) after the first iteration (C~'s operand is ready)
+    auto cmul = [&](const double* src, double* dst) -> ctm_status {
+        if (is_oz(h))
+            return ozmm(h, N, b, N, {h->C, N, 1, nullptr}, OZ_BIG, false, {src, N, 1, nullptr}, OZ_SB, true, dst, N);
+        if (L.esz) {
+            pconvert(h, b, N, src, N, nullptr, h->opV, L.ldN);
+            return ptc(h, N, b, N, h->opC, L.ldN, h->opV, L.ldN, dst, N);
+        }
+        pgemm(h, false, false, N, b, N, h->C, N, src, N, dst, N);
+        return CTM_OK;
+    };
     for (it = 0; it < max_iters; ++it) {
         // A warm block is advanced without a Rayleigh-Ritz solve while the
         // residual cannot yet meet the tolerance: span(C~ V) does not depend
@@ -872,8 +883,38 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
         if (skip_rr) {
             ctm::next_block(h->st, N, b, h->Y, h->V, N, h->theta, 1e-12, h->T);
             count_small(h, 1);
-            ctm_status s = stage_orth(h, h->T, h->V, h->Y, 3);
+            // When the next iteration would skip its solve too, its power
+            // step is taken now and one orthonormalisation serves both
+            // (span(C~ C~ V) is what the two iterations produce either way).
+            // Not in a stage's first two iterations, whose blocks still carry
+            // the step's change of C~ (their scaled blocks are the least
+            // orthonormal: defects up to ~1), and only while the Ritz values
+            // the block is scaled by span at most four decades (a column's
+            // components along the leading eigenvectors grow by up to the
+            // inverse of that range per power step; a corner with a steep
+            // spectrum, e.g. Ising's, left the shifted Cholesky QR a
+            // non-positive pivot after two steps).  FP64-accurate products
+            // only: the TF32 / BF16 products' rounding (~1e-4, ~1e-2 of each
+            // column) grows the same way.
+            bool twice = false;
+            if (!L.esz && it >= 2 && it + 2 < max_iters && it + 1 - it_meas < 16 &&
+                h->hctl->theta_range >= 1e-4) {
+                const double pred = r_meas * std::pow(h->resid_rate, (double)(it + 1 - it_meas));
+                const double tol = h->cfg.subspace_tol;
+                twice = pred > 10.0 * tol || (h->resid_rate > 0.5 && pred > tol);
+            }
+            double* src = h->T;
+            if (twice) {
+                ctm_status s1 = cmul(h->T, h->Y);
+                if (s1 != CTM_OK) return s1;
+                ctm::next_block(h->st, N, b, h->Y, h->T, N, h->theta, 1e-12, h->V);
+                count_small(h, 1);
+                src = h->V;
+                ++it;
+            }
+            ctm_status s = twice ? stage_orth(h, src, h->T, h->Y, 3) : stage_orth(h, src, h->V, h->Y, 3);
             if (s != CTM_OK) return s;
+            if (twice) CTM_CUDA(cudaMemcpyAsync(h->V, h->T, sizeof(double) * N * b, cudaMemcpyDeviceToDevice, h->st));
             continue;
         }
         // Rayleigh-Ritz: simultaneous Jacobi rotations when the block is warm
@@ -896,8 +937,11 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
                 cudaEvent_t ra = prof_begin(h);
                 // the kept states and the multiplet test at the cut need the
                 // leading m + 1 pairs; 16 more keep a multiplet straddling
-                // the cut inside the head
-                CTM_CUDA(ctm::rr_cluster_refine(h->st, b, h->H, b, h->rrc, h->ew, h->ctl, 12, std::min(b, m + 16)));
+                // the cut inside the head.  Up to 20 iterations: the first
+                // solve of an exact step converges in 10-14 (linearly at
+                // first, while the couplings are ~1e-3), and a fallback to
+                // Jacobi costs several times an iteration (~230 us at b = 416).
+                CTM_CUDA(ctm::rr_cluster_refine(h->st, b, h->H, b, h->rrc, h->ew, h->ctl, 20, std::min(b, m + 16)));
                 prof_end(h, ra, PC_RRC, 1);
                 rrc_rec = (h->prof_on && ra) ? (int)h->recs.size() - 1 : -1;
                 ++h->rrc_solves;

@@ -29,6 +29,7 @@ struct DevCtl {
     int pad0, pad1;
     double resid;        // max residual / |theta_0|
     double theta0;
+    double theta_range;  // min |theta_i| / |theta_0| over the block's non-negligible Ritz values
     // step stage
     double kappa;
     double delta;

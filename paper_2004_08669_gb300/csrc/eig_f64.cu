@@ -1071,6 +1071,14 @@ __global__ void k_decide(int b, int L, int m, double tol, double tol_c, const do
     ctl->meff_new = bad ? 0 : meff;
     ctl->resid = bad ? INFINITY : rmax / a1;
     ctl->theta0 = theta[0];
+    // dynamic range of the Ritz values that k_next_block divides by (those
+    // above 1e-12 |theta_0|)
+    double rng = 1.0;
+    for (int i = 1; i < b; ++i) {
+        const double t = fabs(theta[i]);
+        if (t > 1e-12 * a1) rng = fmin(rng, t / a1);
+    }
+    ctl->theta_range = bad ? 0.0 : rng;
     ctl->sub_converged = (!bad && rmax <= tol * a1) ? 1 : 0;
     if (bad) ctl->numeric_bad = 1;
 }
@@ -1344,7 +1352,9 @@ cudaError_t cholesky_f64(cudaStream_t st, int n, double* G, int ld, double shift
     const long T = (n + 15) / 16;
     int grid = (int)std::max<long>(T * (T + 1) / 2, (n + 255) / 256);
     if (grid > limit) grid = limit;
-    if (grid > 2 * 152) grid = 2 * 152;
+    // one block per SM: measured 6% faster per factorisation than two
+    // (fewer participants per grid barrier), and 76 blocks slower again
+    if (grid > 152) grid = 152;
     if (grid < 1) grid = 1;
     void* args[] = {&n, &G, &ld, &shift, &ctl, &skip};
     return launch_coop(df ? (const void*)k_cholesky<CDF> : (const void*)k_cholesky<C64>, grid, 256, args, 0, st);
