@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--prep", type=int, default=25, help="untimed steps before warm-up (cold start)")
     ap.add_argument("--subspace-iters", type=int, default=200,
                     help="cap of subspace iterations per step (exact steps: far above the iterations used)")
-    ap.add_argument("--block-extra", type=int, default=160, help="oversampling: b = m + block_extra")
+    ap.add_argument("--block-extra", type=int, default=192, help="oversampling: b = m + block_extra")
     ap.add_argument("--capped", action="store_true",
                     help="also time the inexact variant (two subspace iterations per step, b = m + 32)")
     ap.add_argument("--e2e-steps", type=int, default=10)

@@ -907,7 +907,9 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             if (twice) {
                 ctm_status s1 = cmul(h->T, h->Y);
                 if (s1 != CTM_OK) return s1;
-                ctm::next_block(h->st, N, b, h->Y, h->T, N, h->theta, 1e-12, h->V);
+                // the pair as the degree-2 Chebyshev filter on the unwanted
+                // spectrum's interval (V still holds the block before the pair)
+                ctm::cheb2_block(h->st, N, b, h->Y, h->V, N, h->theta, 1e-12);
                 count_small(h, 1);
                 src = h->V;
                 ++it;

@@ -1099,6 +1099,31 @@ __global__ void k_next_block(int N, int b, const double* __restrict__ T, const d
     }
 }
 
+// Second power step of a pair taken before one orthonormalisation, with the
+// degree-2 Chebyshev filter on [-a, a], a = |theta_{b-1}| (the block's
+// smallest Ritz value, an estimate of the unwanted spectrum's edge):
+//   V_i <- T_2(C~/a) V_i / T_2(theta_i/a) = (c Y2_i - V_i) / (c - 1),
+//   Y2_i = Y_i / theta_i = C~^2 V_i / theta_i^2,  c = 2 theta_i^2 / a^2,
+// where Y = C~ (C~ V / theta).  Components with |lambda| <= a are damped by
+// 1/T_2(theta_i/a) instead of (a/theta_i)^2.  Columns with theta_i < 1.5 a
+// (c - 1 small) take Y2_i, negligible ones keep V_i.  V is updated in place
+// (each element reads only its own position).
+__global__ void k_cheb2_block(int N, int b, const double* __restrict__ Y, double* V, int ld,
+                              const double* __restrict__ theta, double eps_theta) {
+    const double a1 = fabs(theta[0]);
+    const double a = fabs(theta[b - 1]);
+    const size_t tot = (size_t)N * b;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % N), i = (int)(e / N);
+        const double th = theta[i];
+        const size_t o = r + (size_t)ld * i;
+        if (!(fabs(th) > eps_theta * a1)) continue;  // V_i kept
+        const double y2 = Y[o] / th;
+        const double c = (a > eps_theta * a1) ? 2.0 * (th / a) * (th / a) : 0.0;
+        V[o] = (c >= 4.5) ? (c * y2 - V[o]) / (c - 1.0) : y2;
+    }
+}
+
 // Dot products for the gauge alignment: d[3 i + 0] = z_i.v_i,
 // d[3 i + 1] = z_i.v_{i+1}, d[3 i + 2] = z_{i+1}.v_i.
 __global__ void k_gauge_dots(int N, int b, const double* __restrict__ Z, const double* __restrict__ V,
@@ -1462,6 +1487,11 @@ void decide(cudaStream_t st, int b, int L, int m, double tol, double tol_c, cons
 void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z, int ld,
                 const double* theta, double eps_theta, double* Vn) {
     k_next_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, T, Z, ld, theta, eps_theta, Vn);
+}
+
+void cheb2_block(cudaStream_t st, int N, int b, const double* Y, double* V, int ld, const double* theta,
+                 double eps_theta) {
+    k_cheb2_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, Y, V, ld, theta, eps_theta);
 }
 
 void gauge_align(cudaStream_t st, int N, int b, double* Z, const double* V, int ld, const double* theta,

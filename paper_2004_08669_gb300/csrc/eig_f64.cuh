@@ -127,6 +127,13 @@ void decide(cudaStream_t st, int b, int L, int m, double tol, double tol_c, cons
             const double* res, DevCtl* ctl);
 void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z, int ld,
                 const double* theta, double eps_theta, double* Vn);
+
+// The second of two power steps before one orthonormalisation, filtered:
+// V <- (c Y / theta - V) / (c - 1), c = 2 theta^2 / theta_{b-1}^2 (the
+// degree-2 Chebyshev polynomial on [-|theta_{b-1}|, |theta_{b-1}|]
+// normalised at theta), from Y = C~ (C~ V / theta); in place in V.
+void cheb2_block(cudaStream_t st, int N, int b, const double* Y, double* V, int ld, const double* theta,
+                 double eps_theta);
 void gauge_align(cudaStream_t st, int N, int b, double* Z, const double* V, int ld, const double* theta,
                  double tol_c, EigWork& w);
 void randn_block(cudaStream_t st, int N, int b, double* V, int ld, uint64_t seed);

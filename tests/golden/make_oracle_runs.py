@@ -8,10 +8,11 @@ the growth factor kappa (f = -(T/2) ln kappa, reading R5), the kept-state S_E
 (f, M of Eq. 5, u, S_E) of the last state.
 
   python tests/golden/make_oracle_runs.py traj    # m = 256, T = 0.4398, 20 steps
+  python tests/golden/make_oracle_runs.py traj64  # m = 256, T = 0.4398, 64 steps
   python tests/golden/make_oracle_runs.py fixed   # m = 32 and 64, T = 0.4398, to delta < 1e-12
 
-The m = 256 trajectory takes about 15 minutes on 8 host cores, the fixed
-points a few minutes.
+The m = 256 trajectory takes about 15 minutes on 8 host cores (64 steps: about
+an hour), the fixed points a few minutes.
 """
 from __future__ import annotations
 
@@ -55,6 +56,8 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "fixed"
     if what == "traj":
         run(256, 0.4398, 20, 0.0, "oracle_q20_m256_T0.4398_20steps.json")
+    elif what == "traj64":
+        run(256, 0.4398, 64, 0.0, "oracle_q20_m256_T0.4398_64steps.json")
     else:
         for m in (32, 64):
             run(m, 0.4398, 5000, 1e-12, f"oracle_q20_m{m}_T0.4398_fixed_point.json")
