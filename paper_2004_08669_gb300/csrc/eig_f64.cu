@@ -1124,6 +1124,34 @@ __global__ void k_cheb2_block(int N, int b, const double* __restrict__ Y, double
     }
 }
 
+// Three power steps before one orthonormalisation, filtered by the degree-3
+// Chebyshev polynomial on [-a, a]: with Y1 = C~ V / theta (in T) and
+// Y = C~^3 V / theta^2, u = theta / a:
+//   V <- (4 u^3 Y / theta - 3 u Y1) / (4 u^3 - 3 u).
+__global__ void k_cheb3_block(int N, int b, const double* __restrict__ Y, const double* __restrict__ T,
+                              double* __restrict__ V, int ld, const double* __restrict__ theta, double eps_theta) {
+    const double a1 = fabs(theta[0]);
+    const double a = fabs(theta[b - 1]);
+    const size_t tot = (size_t)N * b;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % N), i = (int)(e / N);
+        const double th = theta[i];
+        const size_t o = r + (size_t)ld * i;
+        if (!(fabs(th) > eps_theta * a1)) {
+            V[o] = T[o];
+            continue;
+        }
+        const double y3 = Y[o] / th;
+        const double u = (a > eps_theta * a1) ? fabs(th) / a : 0.0;
+        if (u >= 1.5) {
+            const double u3 = 4.0 * u * u * u, u1 = 3.0 * u;
+            V[o] = (u3 * y3 - u1 * T[o]) / (u3 - u1);
+        } else {
+            V[o] = y3;
+        }
+    }
+}
+
 // Dot products for the gauge alignment: d[3 i + 0] = z_i.v_i,
 // d[3 i + 1] = z_i.v_{i+1}, d[3 i + 2] = z_{i+1}.v_i.
 __global__ void k_gauge_dots(int N, int b, const double* __restrict__ Z, const double* __restrict__ V,
@@ -1487,6 +1515,11 @@ void decide(cudaStream_t st, int b, int L, int m, double tol, double tol_c, cons
 void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z, int ld,
                 const double* theta, double eps_theta, double* Vn) {
     k_next_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, T, Z, ld, theta, eps_theta, Vn);
+}
+
+void cheb3_block(cudaStream_t st, int N, int b, const double* Y, const double* T, double* V, int ld,
+                 const double* theta, double eps_theta) {
+    k_cheb3_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, Y, T, V, ld, theta, eps_theta);
 }
 
 void cheb2_block(cudaStream_t st, int N, int b, const double* Y, double* V, int ld, const double* theta,

@@ -132,6 +132,12 @@ void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z,
 // V <- (c Y / theta - V) / (c - 1), c = 2 theta^2 / theta_{b-1}^2 (the
 // degree-2 Chebyshev polynomial on [-|theta_{b-1}|, |theta_{b-1}|]
 // normalised at theta), from Y = C~ (C~ V / theta); in place in V.
+// Three power steps before one orthonormalisation, filtered by the degree-3
+// Chebyshev polynomial on [-|theta_{b-1}|, |theta_{b-1}|] normalised at theta:
+// V <- (4u^3 Y/theta - 3u T)/(4u^3 - 3u), u = theta/|theta_{b-1}|, from
+// T = C~ V / theta and Y = C~^3 V / theta^2 (V, T, Y distinct).
+void cheb3_block(cudaStream_t st, int N, int b, const double* Y, const double* T, double* V, int ld,
+                 const double* theta, double eps_theta);
 void cheb2_block(cudaStream_t st, int N, int b, const double* Y, double* V, int ld, const double* theta,
                  double eps_theta);
 void gauge_align(cudaStream_t st, int N, int b, double* Z, const double* V, int ld, const double* theta,
