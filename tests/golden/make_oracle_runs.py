@@ -10,6 +10,7 @@ the growth factor kappa (f = -(T/2) ln kappa, reading R5), the kept-state S_E
   python tests/golden/make_oracle_runs.py traj    # m = 256, T = 0.4398, 20 steps
   python tests/golden/make_oracle_runs.py traj64  # m = 256, T = 0.4398, 64 steps
   python tests/golden/make_oracle_runs.py fixed   # m = 32 and 64, T = 0.4398, to delta < 1e-12
+  python tests/golden/make_oracle_runs.py m1024   # m = 1024, T = 0.4398, 3 steps (live block <= 8000)
 
 The m = 256 trajectory takes about 15 minutes on 8 host cores (64 steps: about
 an hour), the fixed points a few minutes.
@@ -56,6 +57,8 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "fixed"
     if what == "traj":
         run(256, 0.4398, 20, 0.0, "oracle_q20_m256_T0.4398_20steps.json")
+    elif what == "m1024":
+        run(1024, 0.4398, 3, 0.0, "oracle_q20_m1024_T0.4398_3steps.json")
     elif what == "traj64":
         run(256, 0.4398, 64, 0.0, "oracle_q20_m256_T0.4398_64steps.json")
     else:

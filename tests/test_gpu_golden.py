@@ -143,3 +143,30 @@ def test_m256_64_steps_follow_the_oracle_until_the_unstable_stretch(ctm, prec, t
           " ".join(f"{k + 1}:{x:.1e}" for k, x in enumerate(rel) if k >= 39))
     assert max(rel[:47]) <= tol
     assert rel[-1] <= 1e-5
+
+
+def test_m1024_first_steps_match_the_oracle(ctm):
+    """q = 20, m = 1024 (N = 20480) in the emulated form: the first three
+    exact steps (live blocks of 20, 400 and 8000 rows) against the oracle's
+    (kappa to 1e-10, m_eff, S_E to 1e-10), then two full-size steps checked for
+    their Ritz residual and the bound 0 <= S_E <= ln m_eff."""
+    path = os.path.join(GOLDEN, "oracle_q20_m1024_T0.4398_3steps.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/oracle_q20_m1024_T0.4398_3steps.json not written")
+    ref = _load("oracle_q20_m1024_T0.4398_3steps.json")
+    g = ctm.CTMRG(W.dodecahedron(), 1024, ref["beta"], prec="ozaki64", subspace_tol=1e-11, max_subspace_iters=200,
+                  block_extra=192)
+    for k, r in enumerate(ref["steps"]):
+        _, info, st = g.step(1)
+        assert st in (ctm.CTM_OK, ctm.CTM_ENOTCONVERGED)
+        print(f"\nm=1024 step {k + 1}: |dkappa|/kappa = {abs(info['kappa'] - r['kappa']) / r['kappa']:.2e}, "
+              f"m_eff {info['m_eff']} (oracle {int(r['m_eff'])}), iterations {info['subspace_iters']}")
+        assert info["m_eff"] == int(r["m_eff"])
+        assert info["kappa"] == pytest.approx(r["kappa"], rel=1e-10)
+        assert info["S_E"] == pytest.approx(r["S_E_kept"], abs=1e-10)
+    for _ in range(2):
+        _, info, st = g.step(1)
+        assert st == ctm.CTM_OK
+        assert info["residual"] <= 1e-10
+        assert 0.0 <= info["S_E"] <= math.log(info["m_eff"]) + 1e-12
+    g.close()
