@@ -1071,85 +1071,86 @@ __global__ void k_decide(int b, int L, int m, double tol, double tol_c, const do
     ctl->meff_new = bad ? 0 : meff;
     ctl->resid = bad ? INFINITY : rmax / a1;
     ctl->theta0 = theta[0];
-    // dynamic range of the Ritz values that k_next_block divides by (those
+    // dynamic range of the Ritz values the next block is divided by (those
     // above 1e-12 |theta_0|)
-    double rng = 1.0;
+    double tmin = a1;
     for (int i = 1; i < b; ++i) {
         const double t = fabs(theta[i]);
-        if (t > 1e-12 * a1) rng = fmin(rng, t / a1);
+        if (t > 1e-12 * a1) tmin = fmin(tmin, t);
     }
-    ctl->theta_range = bad ? 0.0 : rng;
+    ctl->theta_range = (bad || !(a1 > 0.0)) ? 0.0 : tmin / a1;
     ctl->sub_converged = (!bad && rmax <= tol * a1) ? 1 : 0;
     if (bad) ctl->numeric_bad = 1;
 }
 
-// Next block before re-orthonormalisation: T_i / theta_i, or Z_i when
-// |theta_i| is negligible (keeps the Gram matrix well conditioned).
-__global__ void k_next_block(int N, int b, const double* __restrict__ T, const double* __restrict__ Z,
-                             int ld, const double* __restrict__ theta, double eps_theta,
-                             double* __restrict__ Vn) {
-    double a1 = fabs(theta[0]);
-    size_t tot = (size_t)N * b;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(e % N), i = (int)(e / N);
-        double th = theta[i];
-        size_t o = r + (size_t)ld * i;
-        Vn[o] = (fabs(th) > eps_theta * a1) ? T[o] / th : Z[o];
+// Column-wise combinations of N x b blocks, out_i = alpha_i X_i + beta_i W_i,
+// with the coefficients of column i computed once per column (this part's
+// FP64 division is slow: one per element cost more than the memory traffic).
+enum BlockMode { BM_NEXT = 0, BM_CHEB2 = 1, BM_CHEB3 = 2 };
+
+// BM_NEXT: X = T = C~ V, W = Z: T_i / theta_i, or Z_i for a negligible
+//   theta_i (keeps the Gram matrix well conditioned).
+// BM_CHEB2: X = Y = C~ (C~ V / theta), W = V: the pair of power steps as the
+//   degree-2 Chebyshev polynomial on [-a, a], a = |theta_{b-1}| (the block's
+//   smallest Ritz value, an estimate of the unwanted spectrum's edge),
+//   normalised at theta_i: (c Y_i / theta_i - V_i) / (c - 1), c = 2 u^2,
+//   u = |theta_i| / a, when c >= 4.5; else Y_i / theta_i.
+// BM_CHEB3: X = Y = C~^3 V / theta^2, W = T = C~ V / theta: three steps as
+//   T_3: (4u^3 Y_i / theta_i - 3u T_i) / (4u^3 - 3u) when u >= 1.5; else
+//   Y_i / theta_i.  Components with |lambda| <= a shrink by 1/T_k(u) instead
+//   of u^-k.
+__device__ void block_coeffs(int mode, int i, int b, const double* __restrict__ theta, double eps_theta,
+                             double& al, double& be) {
+    const double a1 = fabs(theta[0]);
+    const double th = theta[i];
+    if (!(fabs(th) > eps_theta * a1)) {  // negligible Ritz value: keep W_i
+        al = 0.0;
+        be = 1.0;
+        return;
+    }
+    al = 1.0 / th;
+    be = 0.0;
+    if (mode == BM_NEXT) return;
+    const double a = fabs(theta[b - 1]);
+    if (!(a > eps_theta * a1)) return;
+    const double u = fabs(th) / a;
+    if (mode == BM_CHEB2) {
+        const double c = 2.0 * u * u;  // T_2(u) = c - 1
+        if (c >= 4.5) {
+            al = c / (th * (c - 1.0));
+            be = -1.0 / (c - 1.0);
+        }
+    } else if (u >= 1.5) {
+        const double u3 = 4.0 * u * u * u, u1 = 3.0 * u;  // T_3(u) = u3 - u1
+        al = u3 / (th * (u3 - u1));
+        be = -u1 / (u3 - u1);
     }
 }
 
-// Second power step of a pair taken before one orthonormalisation, with the
-// degree-2 Chebyshev filter on [-a, a], a = |theta_{b-1}| (the block's
-// smallest Ritz value, an estimate of the unwanted spectrum's edge):
-//   V_i <- T_2(C~/a) V_i / T_2(theta_i/a) = (c Y2_i - V_i) / (c - 1),
-//   Y2_i = Y_i / theta_i = C~^2 V_i / theta_i^2,  c = 2 theta_i^2 / a^2,
-// where Y = C~ (C~ V / theta).  Components with |lambda| <= a are damped by
-// 1/T_2(theta_i/a) instead of (a/theta_i)^2.  Columns with theta_i < 1.5 a
-// (c - 1 small) take Y2_i, negligible ones keep V_i.  V is updated in place
-// (each element reads only its own position).
-__global__ void k_cheb2_block(int N, int b, const double* __restrict__ Y, double* V, int ld,
-                              const double* __restrict__ theta, double eps_theta) {
-    const double a1 = fabs(theta[0]);
-    const double a = fabs(theta[b - 1]);
-    const size_t tot = (size_t)N * b;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e % N), i = (int)(e / N);
-        const double th = theta[i];
+// out may alias W (each element reads only its own position)
+__global__ void k_col_combine(int mode, int N, int b, const double* __restrict__ X, const double* W, double* out,
+                              int ld, const double* __restrict__ theta, double eps_theta) {
+    __shared__ double s_al, s_be;
+    const int i = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double al, be;
+        block_coeffs(mode, i, b, theta, eps_theta, al, be);
+        s_al = al;
+        s_be = be;
+    }
+    __syncthreads();
+    const double al = s_al, be = s_be;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
         const size_t o = r + (size_t)ld * i;
-        if (!(fabs(th) > eps_theta * a1)) continue;  // V_i kept
-        const double y2 = Y[o] / th;
-        const double c = (a > eps_theta * a1) ? 2.0 * (th / a) * (th / a) : 0.0;
-        V[o] = (c >= 4.5) ? (c * y2 - V[o]) / (c - 1.0) : y2;
+        out[o] = (be == 0.0) ? al * X[o] : (al == 0.0 ? be * W[o] : fma(al, X[o], be * W[o]));
     }
 }
 
-// Three power steps before one orthonormalisation, filtered by the degree-3
-// Chebyshev polynomial on [-a, a]: with Y1 = C~ V / theta (in T) and
-// Y = C~^3 V / theta^2, u = theta / a:
-//   V <- (4 u^3 Y / theta - 3 u Y1) / (4 u^3 - 3 u).
-__global__ void k_cheb3_block(int N, int b, const double* __restrict__ Y, const double* __restrict__ T,
-                              double* __restrict__ V, int ld, const double* __restrict__ theta, double eps_theta) {
-    const double a1 = fabs(theta[0]);
-    const double a = fabs(theta[b - 1]);
-    const size_t tot = (size_t)N * b;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e % N), i = (int)(e / N);
-        const double th = theta[i];
-        const size_t o = r + (size_t)ld * i;
-        if (!(fabs(th) > eps_theta * a1)) {
-            V[o] = T[o];
-            continue;
-        }
-        const double y3 = Y[o] / th;
-        const double u = (a > eps_theta * a1) ? fabs(th) / a : 0.0;
-        if (u >= 1.5) {
-            const double u3 = 4.0 * u * u * u, u1 = 3.0 * u;
-            V[o] = (u3 * y3 - u1 * T[o]) / (u3 - u1);
-        } else {
-            V[o] = y3;
-        }
-    }
+void col_combine(cudaStream_t st, int mode, int N, int b, const double* X, const double* W, double* out, int ld,
+                 const double* theta, double eps_theta) {
+    if (N <= 0 || b <= 0) return;
+    const dim3 grid((unsigned)std::min((N + 255) / 256, 16), (unsigned)b);
+    k_col_combine<<<grid, 256, 0, st>>>(mode, N, b, X, W, out, ld, theta, eps_theta);
 }
 
 // Dot products for the gauge alignment: d[3 i + 0] = z_i.v_i,
@@ -1514,17 +1515,17 @@ void decide(cudaStream_t st, int b, int L, int m, double tol, double tol_c, cons
 
 void next_block(cudaStream_t st, int N, int b, const double* T, const double* Z, int ld,
                 const double* theta, double eps_theta, double* Vn) {
-    k_next_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, T, Z, ld, theta, eps_theta, Vn);
+    col_combine(st, BM_NEXT, N, b, T, Z, Vn, ld, theta, eps_theta);
 }
 
 void cheb3_block(cudaStream_t st, int N, int b, const double* Y, const double* T, double* V, int ld,
                  const double* theta, double eps_theta) {
-    k_cheb3_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, Y, T, V, ld, theta, eps_theta);
+    col_combine(st, BM_CHEB3, N, b, Y, T, V, ld, theta, eps_theta);
 }
 
 void cheb2_block(cudaStream_t st, int N, int b, const double* Y, double* V, int ld, const double* theta,
                  double eps_theta) {
-    k_cheb2_block<<<grid_for((size_t)N * b), 256, 0, st>>>(N, b, Y, V, ld, theta, eps_theta);
+    col_combine(st, BM_CHEB2, N, b, Y, V, V, ld, theta, eps_theta);
 }
 
 void gauge_align(cudaStream_t st, int N, int b, double* Z, const double* V, int ld, const double* theta,
