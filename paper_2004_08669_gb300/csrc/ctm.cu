@@ -956,7 +956,12 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
             // strongly coupled pairs form a cluster above 32 states is
             // recognised at the refinement's first check (no product is
             // formed there), so it is tried at every warm solve.
-            rrc_tried = (!cold || it > 0);
+            // Not in the TF32 / BF16 forms: their products leave couplings
+            // near their rounding (~1e-4, ~1e-2 of the Ritz values), which
+            // the refinement cannot bring to its double-float threshold, so
+            // it only ran to its iteration cap before the Jacobi fallback
+            // (measured at m = 256: 8 ms of a 17 ms TF32 step).
+            rrc_tried = !L.esz && (!cold || it > 0);
             CTM_CUDA(cudaMemsetAsync(&h->ctl->rrc_ok, 0, sizeof(int), h->st));
             if (rrc_tried) {
                 cudaEvent_t ra = prof_begin(h);
@@ -972,7 +977,11 @@ ctm_status stage_eigen(ctm_handle* h, int max_iters, bool* sub_converged, int* i
                 ++h->rrc_solves;
             }
             cudaEvent_t ja2 = prof_begin(h);
-            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl, 0.0, 0.0, true,
+            // TF32 / BF16: rotate while a coupling exceeds 1e-9 of the
+            // diagonal scale, far below their products' rounding (the
+            // double-float threshold 2^-46 only adds sweeps there)
+            CTM_CUDA(ctm::jacobi_f64(h->st, b, h->H, b, h->ew, h->theta, h->Sb, b, 40, h->ctl,
+                                     L.esz ? 1e-9 : 0.0, 0.0, true,
                                      rrc_tried ? &h->ctl->rrc_ok : nullptr, cold ? 0 : std::min(b, m + 16)));
             prof_end(h, ja2, PC_JACOBI, 4);
             h->jac_rec = (h->prof_on && ja2) ? (int)h->recs.size() - 1 : -1;
